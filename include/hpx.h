@@ -1,0 +1,167 @@
+/*
+ * hpx.h -- C ABI of libhpx: spherical harmonic transforms on RING-ordered
+ * HEALPix grids, computed on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2510.01785 (cuHPX).  Every transform is a per-ring Fourier
+ * step over the variable-length rings followed by a Legendre step over the
+ * rings (Sec. III-D, Eq. 12-14):
+ *
+ *   synthesis  p = Y a          p_xy = sum_m sum_l a_lm lambda_lm(theta_y)
+ *                                      exp(i m phi_{0,y} + 2 pi i m x / N_y)
+ *                                                              (Eq. 24-25)
+ *   analysis   a = Y^dagger W p a_lm = sum_y sum_x p_xy w_y lambda_lm(theta_y)
+ *                                      exp(-i m phi_{0,y} - 2 pi i m x / N_y)
+ *                                                              (Eq. 26-27)
+ *   adjoints   adjoint of synthesis = Y^dagger,
+ *              adjoint of analysis  = W Y               (Sec. III-F)
+ *
+ * with lambda_lm the orthonormal associated Legendre functions including the
+ * Condon-Shortley phase (Eq. 8, 15), generated by the three-term recurrence
+ * in l (Eq. 16) in FP64, and equal-area weights w_y = 4 pi / Npix (Eq. 1).
+ *
+ * Data layout (all device buffers are owned by the caller):
+ *   map : [nbatch][12 nside^2] real, RING order (rings north to south,
+ *         pixels by increasing phi), contiguous.
+ *   alm : [nbatch][nalm] complex, interleaved (re, im), packed m-major:
+ *         index(l, m) = m (2 lmax + 1 - m) / 2 + l for 0 <= m <= mmax,
+ *         m <= l <= lmax; nalm = hpx_nalm(lmax, mmax).  Only m >= 0 is
+ *         stored: the fields are real, so a_{l,-m} = (-1)^m conj(a_lm).
+ *         Synthesis reads Re(a_l0) only; analysis writes Im(a_l0) = 0.
+ *   real type: double for HPX_F64, float for every other dtype.
+ * Pointers must be 16-byte aligned; map and alm must not overlap.
+ *
+ * Calls are asynchronous and ordered on the stream passed in (NULL = the
+ * legacy default stream).  A plan owns device workspace, so one plan serves
+ * one call at a time: calls on one plan from different streams must be
+ * ordered by the caller, or use one plan per stream.
+ *
+ * Errors: every call returns an hpx_status; on failure hpx_last_error()
+ * returns a message for the calling thread.  No exception crosses the ABI.
+ */
+#ifndef HPX_H
+#define HPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream); declared here so the header needs
+ * no CUDA include. */
+struct CUstream_st;
+typedef struct CUstream_st* hpx_stream_t;
+
+typedef struct hpx_plan_s* hpx_plan;
+
+/* I/O precision and contraction mode.
+ *   HPX_F64        double maps/coefficients, FP64 contraction.
+ *   HPX_F32        float maps/coefficients, FP32 contraction; lambda_lm still
+ *                  comes from the FP64 recurrence.
+ *   HPX_F32_BF16 / HPX_F32_FP16     float I/O, the ring x lambda contraction
+ *                  on tensor cores in BF16 / FP16 with FP32 accumulation.
+ *   HPX_F32_BF16X3 / HPX_F32_FP16X3 the same with split hi+lo products. */
+typedef enum {
+  HPX_F64 = 0,
+  HPX_F32 = 1,
+  HPX_F32_BF16 = 2,
+  HPX_F32_BF16X3 = 3,
+  HPX_F32_FP16 = 4,
+  HPX_F32_FP16X3 = 5
+} hpx_dtype;
+
+typedef enum {
+  HPX_OK = 0,
+  HPX_ERR_INVALID = 1,     /* bad argument (plan parameters, pointer, size) */
+  HPX_ERR_NOMEM = 2,       /* device allocation failed */
+  HPX_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  HPX_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
+  HPX_ERR_UNSUPPORTED = 5  /* valid request this build does not provide */
+} hpx_status;
+
+/* Plan flags for hpx_plan_create_ex. */
+#define HPX_PLAN_LAMBDA_RECOMPUTE 0u /* lambda_lm recomputed by the FP64
+                                        recurrence inside every transform */
+#define HPX_PLAN_LAMBDA_TABLE 1u     /* lambda_lm generated once at plan time
+                                        by the same FP64 recurrence and kept
+                                        in device memory (the precomputed
+                                        Legendre tensor of Sec. III-D/III-G) */
+
+/* Number of packed coefficients for (lmax, mmax). */
+int64_t hpx_nalm(int lmax, int mmax);
+
+/* Create a plan on the current CUDA device.
+ *   nside  : HEALPix resolution, a power of two, 1 <= nside <= 2048
+ *            (Sec. III-A: Npix = 12 nside^2, 4 nside - 1 rings).
+ *   lmax, mmax : band limits, 0 <= mmax <= lmax <= 16384.
+ *   nbatch : number of independent channels per call, 1 <= nbatch <= 65535.
+ *   dtype  : see hpx_dtype.
+ * Builds the ring-geometry table, the recurrence coefficients, the starting
+ * state of every (m, ring) recurrence chain and the FFT tables on the device;
+ * returns once they are complete.  *out receives the plan.
+ * Errors: HPX_ERR_INVALID, HPX_ERR_NOMEM, HPX_ERR_CUDA, HPX_ERR_UNSUPPORTED. */
+hpx_status hpx_plan_create(int nside, int lmax, int mmax, int nbatch,
+                           hpx_dtype dtype, hpx_plan* out);
+
+/* As hpx_plan_create, with HPX_PLAN_* flags. */
+hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch,
+                              hpx_dtype dtype, unsigned flags, hpx_plan* out);
+
+/* Release the plan and all device memory it owns (after synchronising its
+ * device).  NULL is accepted. */
+hpx_status hpx_plan_destroy(hpx_plan plan);
+
+/* a = Y^dagger W p: analysis, Eq. 26-27 with w_y = 4 pi / Npix (Eq. 1).
+ *   map : device, [nbatch][npix] real (input).
+ *   alm : device, [nbatch][nalm] complex (output, fully overwritten). */
+hpx_status hpx_map2alm(hpx_plan plan, const void* map, void* alm,
+                       hpx_stream_t stream);
+
+/* p = Y a: synthesis, Eq. 24-25.
+ *   alm : device, [nbatch][nalm] complex (input).
+ *   map : device, [nbatch][npix] real (output, fully overwritten). */
+hpx_status hpx_alm2map(hpx_plan plan, const void* alm, void* map,
+                       hpx_stream_t stream);
+
+/* p = W Y a: adjoint of the analysis (Sec. III-F), i.e. the synthesis with
+ * every ring scaled by its weight.  Adjoint with respect to the real inner
+ * product <a, b> = sum_l Re(conj a_l0 b_l0) + 2 sum_{m>=1} Re(conj a_lm b_lm)
+ * on coefficients and the plain dot product on maps.
+ *   alm : device input; map : device output. */
+hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map,
+                               hpx_stream_t stream);
+
+/* a = Y^dagger p: adjoint of the synthesis (Sec. III-F), i.e. the analysis
+ * sum with unit weights (same inner products as above).
+ *   map : device input; alm : device output. */
+hpx_status hpx_alm2map_adjoint(hpx_plan plan, const void* map, void* alm,
+                               hpx_stream_t stream);
+
+/* Host-buffer forms of the two transforms: copy the input from host memory
+ * (pinned or pageable) into plan-owned device buffers, run the transform on
+ * the stream, copy the result back and wait for the stream.  The device I/O
+ * buffers are allocated on the first such call and counted by
+ * hpx_plan_device_bytes. */
+hpx_status hpx_map2alm_host(hpx_plan plan, const void* host_map,
+                            void* host_alm, hpx_stream_t stream);
+hpx_status hpx_alm2map_host(hpx_plan plan, const void* host_alm,
+                            void* host_map, hpx_stream_t stream);
+
+/* Device bytes held by the plan (tables + workspace), for admission control. */
+size_t hpx_plan_device_bytes(hpx_plan plan);
+
+/* Copy the plan's ring-geometry table to host arrays of length 4 nside - 1:
+ * first pixel, pixel count N_y, z = cos(theta_y), sin(theta_y) and the
+ * half-pixel shift sigma_y (phi_{0,y} = sigma_y pi / N_y).  Synchronous. */
+hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi,
+                               double* z, double* sinth, int32_t* sigma);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* hpx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPX_H */

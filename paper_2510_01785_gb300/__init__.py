@@ -1,0 +1,207 @@
+"""Spherical harmonic transforms on RING-ordered HEALPix grids for NVIDIA GB300.
+
+Python face of libhpx (C ABI in ``include/hpx.h``; method of arXiv 2510.01785,
+cuHPX).  Tensors are PyTorch CUDA tensors; this module only checks shapes and
+passes ``data_ptr()`` and the current CUDA stream to the library, whose
+kernels do all of the work.
+
+* ``Plan``                    -- one (nside, lmax, mmax, nbatch, dtype) setup
+* ``Plan.map2alm``            -- a = Y^dagger W p          (Eq. 26-27)
+* ``Plan.alm2map``            -- p = Y a                   (Eq. 24-25)
+* ``Plan.map2alm_adjoint``    -- W Y a   (adjoint of analysis, Sec. III-F)
+* ``Plan.alm2map_adjoint``    -- Y^dagger p (adjoint of synthesis, Sec. III-F)
+
+Maps are real ``[nbatch, 12 nside^2]`` in RING order; coefficients are complex
+``[nbatch, nalm]`` packed m-major (index m (2 lmax + 1 - m)/2 + l, m >= 0).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+__all__ = ["Plan", "nalm", "get_plan", "DTYPES"]
+
+DTYPES = {
+    "f64": _lib.HPX_F64,
+    "f32": _lib.HPX_F32,
+    "bf16": _lib.HPX_F32_BF16,
+    "bf16x3": _lib.HPX_F32_BF16X3,
+    "fp16": _lib.HPX_F32_FP16,
+    "fp16x3": _lib.HPX_F32_FP16X3,
+}
+
+
+def nalm(lmax: int, mmax: int | None = None) -> int:
+    return int(lib().hpx_nalm(lmax, lmax if mmax is None else mmax))
+
+
+def _stream_handle(stream, device) -> int:
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Plan:
+    """A transform setup: ring geometry, recurrence tables and workspace on
+    one GPU.  One plan serves one call at a time (its workspace); use one
+    plan per concurrently used stream."""
+
+    def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,
+                 dtype: str = "f32", lambda_table: bool = False, device=None):
+        mmax = lmax if mmax is None else mmax
+        if dtype not in DTYPES:
+            raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+        self.nside, self.lmax, self.mmax, self.nbatch = nside, lmax, mmax, nbatch
+        self.dtype = dtype
+        self.real_dtype = torch.float64 if dtype == "f64" else torch.float32
+        self.complex_dtype = torch.complex128 if dtype == "f64" else torch.complex64
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        self.npix = 12 * nside * nside
+        self.nalm = nalm(lmax, mmax)
+        self._h = None
+        flags = _lib.HPX_PLAN_LAMBDA_TABLE if lambda_table else _lib.HPX_PLAN_LAMBDA_RECOMPUTE
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().hpx_plan_create_ex(nside, lmax, mmax, nbatch, DTYPES[dtype], flags,
+                                           ctypes.byref(h)), "hpx_plan_create_ex")
+        self._h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            lib().hpx_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().hpx_plan_device_bytes(self._h))
+
+    # -- argument checks ----------------------------------------------------
+    def _map(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device):
+            raise ValueError(f"{name} must be a CUDA tensor on {self.device}")
+        if t.dtype != self.real_dtype or tuple(t.shape) != (self.nbatch, self.npix):
+            raise ValueError(f"{name} must be {self.real_dtype} of shape {(self.nbatch, self.npix)}, "
+                             f"got {t.dtype} {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _alm(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device):
+            raise ValueError(f"{name} must be a CUDA tensor on {self.device}")
+        if t.dtype != self.complex_dtype or tuple(t.shape) != (self.nbatch, self.nalm):
+            raise ValueError(f"{name} must be {self.complex_dtype} of shape {(self.nbatch, self.nalm)}, "
+                             f"got {t.dtype} {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def empty_map(self) -> torch.Tensor:
+        return torch.empty((self.nbatch, self.npix), dtype=self.real_dtype, device=self.device)
+
+    def empty_alm(self) -> torch.Tensor:
+        return torch.empty((self.nbatch, self.nalm), dtype=self.complex_dtype, device=self.device)
+
+    # -- transforms ---------------------------------------------------------
+    def _call(self, fn, name, src, dst, stream):
+        check(fn(self._h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                 ctypes.c_void_p(_stream_handle(stream, self.device))), name)
+        return dst
+
+    def map2alm(self, maps: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """a = Y^dagger W p with w = 4 pi / Npix (Eq. 26-27)."""
+        src = self._map(maps, "maps")
+        dst = self._alm(out, "out") if out is not None else self.empty_alm()
+        return self._call(lib().hpx_map2alm, "hpx_map2alm", src, dst, stream)
+
+    def alm2map(self, alm: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """p = Y a (Eq. 24-25)."""
+        src = self._alm(alm, "alm")
+        dst = self._map(out, "out") if out is not None else self.empty_map()
+        return self._call(lib().hpx_alm2map, "hpx_alm2map", src, dst, stream)
+
+    def map2alm_adjoint(self, alm: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """W Y a: adjoint of map2alm (Sec. III-F)."""
+        src = self._alm(alm, "alm")
+        dst = self._map(out, "out") if out is not None else self.empty_map()
+        return self._call(lib().hpx_map2alm_adjoint, "hpx_map2alm_adjoint", src, dst, stream)
+
+    def alm2map_adjoint(self, maps: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Y^dagger p: adjoint of alm2map (Sec. III-F)."""
+        src = self._map(maps, "maps")
+        dst = self._alm(out, "out") if out is not None else self.empty_alm()
+        return self._call(lib().hpx_alm2map_adjoint, "hpx_alm2map_adjoint", src, dst, stream)
+
+    # -- host-buffer forms --------------------------------------------------
+    def map2alm_host(self, maps: np.ndarray | torch.Tensor, out=None, stream=None):
+        """Host map in, host coefficients out (copies inside the call)."""
+        src = maps if isinstance(maps, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(maps))
+        assert src.device.type == "cpu" and src.dtype == self.real_dtype and src.is_contiguous()
+        assert tuple(src.shape) == (self.nbatch, self.npix)
+        dst = out if out is not None else torch.empty((self.nbatch, self.nalm), dtype=self.complex_dtype)
+        check(lib().hpx_map2alm_host(self._h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                     ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_map2alm_host")
+        return dst
+
+    def alm2map_host(self, alm: np.ndarray | torch.Tensor, out=None, stream=None):
+        """Host coefficients in, host map out (copies inside the call)."""
+        src = alm if isinstance(alm, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(alm))
+        assert src.device.type == "cpu" and src.dtype == self.complex_dtype and src.is_contiguous()
+        assert tuple(src.shape) == (self.nbatch, self.nalm)
+        dst = out if out is not None else torch.empty((self.nbatch, self.npix), dtype=self.real_dtype)
+        check(lib().hpx_alm2map_host(self._h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                     ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_alm2map_host")
+        return dst
+
+    def ring_table(self) -> dict:
+        R = 4 * self.nside - 1
+        start = np.zeros(R, np.int64)
+        nphi = np.zeros(R, np.int32)
+        z = np.zeros(R, np.float64)
+        sinth = np.zeros(R, np.float64)
+        sigma = np.zeros(R, np.int32)
+        P = ctypes.c_void_p
+        check(lib().hpx_plan_ring_table(self._h, P(start.ctypes.data), P(nphi.ctypes.data), P(z.ctypes.data),
+                                        P(sinth.ctypes.data), P(sigma.ctypes.data)), "hpx_plan_ring_table")
+        return {"start": start, "nphi": nphi, "z": z, "sinth": sinth, "sigma": sigma}
+
+
+_plan_cache: dict = {}
+_plan_lock = threading.Lock()
+
+
+def get_plan(nside: int, lmax: int, mmax: int | None, nbatch: int, dtype: str, device=None,
+             lambda_table: bool = False) -> Plan:
+    """A cached plan per (geometry, batch, dtype, device)."""
+    mmax = lmax if mmax is None else mmax
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    key = (nside, lmax, mmax, nbatch, dtype, device, lambda_table)
+    with _plan_lock:
+        p = _plan_cache.get(key)
+        if p is None:
+            p = Plan(nside, lmax, mmax, nbatch, dtype, lambda_table, device)
+            _plan_cache[key] = p
+    return p

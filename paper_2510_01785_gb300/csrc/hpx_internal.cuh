@@ -1,0 +1,108 @@
+// Internal declarations shared by the libhpx translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "hpx.h"
+
+namespace hpx {
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 / double2)
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using C2 = typename Vec2<T>::type;
+
+template <typename V> __host__ __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) {
+  V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmk<V>(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// plan-resident tables
+// ---------------------------------------------------------------------------
+// One HEALPix ring (Sec. III-A).
+struct RingInfo {
+  long long start;    // first pixel in RING order
+  long long specoff;  // offset of its half spectrum (N/2 + 1 bins) in the spectrum workspace
+  long long etab;     // offset of its table E_N[r] = exp(-i pi r / N), r in [0, 2N)
+  long long btab;     // offset of its Bluestein kernel spectrum (2^logm bins), -1 if N/2 is a power of two
+  int nphi;           // N_y
+  int sigma;          // phi_0 = sigma pi / N_y
+  int logm;           // log2 of the FFT length used for the ring
+  int pad;
+  double z, sinth;    // cos(theta_y), sin(theta_y)
+  double w;           // quadrature weight of every pixel on the ring (4 pi / Npix)
+};
+
+}  // namespace hpx
+
+struct hpx_plan_s {
+  int nside, lmax, mmax, nbatch, dtype, device;
+  unsigned flags;
+  int nring, npair;
+  long long npix, nalm, nspec;
+  int logm_max;        // largest FFT length over the rings (log2)
+  int logtw;           // log2 of the twiddle table's FFT length
+  long long netab, nbtab;
+  hpx::RingInfo* d_ring;
+  void* d_etab;        // C2<T> per distinct ring length
+  void* d_btab;        // C2<T> Bluestein kernel spectra, DIF output order, scaled 1/M
+  void* d_tw;          // C2<T> tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1)
+  double* d_cmm;       // [mmax+1] lambda_mm / sin^m(theta) (sign included)
+  double* d_coef_c;    // [nalm] recurrence coefficient c_l of mu_l = c_l z mu_{l-1} - mu_{l-2}
+  double* d_coef_p;    // [nalm] P_l, lambda_l = P_l mu_l
+  float* d_coef_pf;    // [nalm] P_l rounded to float
+  int* d_lc;           // [mmax+1][npair] first significant l of chain (m, pair)
+  double* d_mu0;       // [mmax+1][npair] mu_{lc-1}
+  double* d_mu1;       // [mmax+1][npair] mu_{lc}
+  void* d_spec;        // workspace [nbatch][nspec] C2<T>
+  void* d_F;           // workspace [nbatch][nring][mmax+1] C2<T>
+  void* d_io_map;      // device I/O buffers of the host-buffer entry points (lazy)
+  void* d_io_alm;
+  size_t bytes;
+};
+
+namespace hpx {
+
+// Significance threshold of the recurrence chains: a chain contributes from
+// the first l at which |mu_l| >= 2^-kSigExp; earlier values are below
+// 2^-kSigExp (about 1.6e-60) and are dropped.
+constexpr int kSigExp = 200;
+
+// error reporting (thread-local message)
+void set_error(const char* fmt, ...);
+hpx_status cuda_fail(cudaError_t e, const char* what);
+
+__host__ __device__ inline long long alm_base(int lmax, int m) {  // index(l = 0, m); index(l, m) = alm_base + l
+  return (long long)m * (2 * lmax + 1 - m) / 2;
+}
+
+// launchers (defined in hpx_fft.cu / hpx_legendre.cu)
+template <typename T>
+cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s);
+template <typename T>
+cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s);
+template <typename T>
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_weight, cudaStream_t s);
+template <typename T>
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s);
+
+// plan-time table builders (hpx_fft.cu, hpx_legendre.cu)
+template <typename T>
+cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s);
+cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s);
+
+}  // namespace hpx

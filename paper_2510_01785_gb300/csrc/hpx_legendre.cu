@@ -1,0 +1,577 @@
+// Legendre stage of the HEALPix SHT (Sec. III-D Eq. 14-16, Eq. 24-27).
+//
+// lambda_lm(z) obeys the three-term recurrence of Eq. 16,
+//   lambda_l = alpha_l (z lambda_{l-1} - lambda_{l-2} / alpha_{l-1}),
+//   alpha_l = sqrt((4 l^2 - 1) / (l^2 - m^2)),
+// started from lambda_mm = (-1)^m sqrt(prod_{k<=m} (2k+1)/(2k) / 4 pi) sin^m.
+// It is run here in the rescaled variable mu_l = lambda_l / P_l with
+// P_m = P_{m+1} = 1 and P_l = (alpha_l / alpha_{l-1}) P_{l-2}, which turns it
+// into mu_l = c_l z mu_{l-1} - mu_{l-2} (c_l = alpha_l P_{l-1} / P_l): two
+// FP64 operations per step.  P_l does not depend on the ring, so it is
+// applied once per output coefficient (analysis) or once per input
+// coefficient (synthesis) instead of once per step.
+//
+// Exponent rescaling: a plan-time pass runs every (m, ring) chain in a
+// (mantissa, 2^(-512 k)) representation from lambda_mm until it first
+// reaches 2^-200 and records l_c and (mu_{l_c-1}, mu_{l_c}).  Values before
+// l_c are below 2^-193 and are dropped; after l_c they stay within the
+// double range, so the per-transform kernels run the plain recurrence from
+// the recorded state and skip the dropped part of every chain.
+//
+// Contraction with the rings (analysis) or coefficients (synthesis) uses the
+// north/south symmetry lambda_lm(-z) = (-1)^(l+m) lambda_lm(z): each chain
+// serves a mirrored ring pair, with S = G(y) + G(y') for even l - m and
+// A = G(y) - G(y') for odd l - m.
+#include <cooperative_groups.h>
+
+#include <climits>
+
+#include "hpx_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hpx {
+
+constexpr int LB = 32;  // l values per block of the recurrence
+
+// ---------------------------------------------------------------------------
+// plan-time tables
+// ---------------------------------------------------------------------------
+// lambda_mm / sin^m theta = (-1)^m sqrt(prod_{k=1..m} (2k+1)/(2k) / (4 pi)),
+// the product carried as an unevaluated double-double sum.
+__global__ void k_lambda_mm_prefactor(int mmax, double* cmm) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > mmax) return;
+  double hi = 1.0, lo = 0.0;
+  for (int k = 1; k <= m; ++k) {
+    const double num = 2.0 * k + 1.0, den = 2.0 * k;
+    const double qh = num / den;
+    const double ql = fma(-qh, den, num) / den;  // num/den = qh + ql
+    const double ph = hi * qh;
+    double pe = fma(hi, qh, -ph);
+    pe = fma(hi, ql, pe);
+    pe = fma(lo, qh, pe);
+    hi = ph + pe;
+    lo = pe - (hi - ph);
+  }
+  const double inv4pi = 0.079577471545947667884;  // 1 / (4 pi)
+  const double r = sqrt(hi * inv4pi) * (1.0 + 0.5 * lo / hi);
+  cmm[m] = (m & 1) ? -r : r;
+}
+
+// c_l and P_l of the rescaled recurrence for every (l, m); packed like alm.
+__global__ void k_recurrence_coefs(int lmax, int mmax, double* coef_c, double* coef_p,
+                                   float* coef_pf) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > mmax) return;
+  const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
+  coef_c[base + m] = 0.0;
+  coef_p[base + m] = 1.0;
+  coef_pf[base + m] = 1.0f;
+  double p1 = 1.0, p2 = 1.0, a_prev = 0.0;  // P_{l-1}, P_{l-2}, alpha_{l-1}
+  const double md = m;
+  for (int l = m + 1; l <= lmax; ++l) {
+    const double ld = l;
+    const double a = sqrt((4.0 * ld * ld - 1.0) / (ld * ld - md * md));
+    double P, c;
+    if (l == m + 1) {
+      P = 1.0;
+      c = a;
+    } else {
+      P = (a / a_prev) * p2;
+      c = a * p1 / P;
+    }
+    coef_c[base + l] = c;
+    coef_p[base + l] = P;
+    coef_pf[base + l] = (float)P;
+    p2 = p1;
+    p1 = P;
+    a_prev = a;
+  }
+}
+
+// Start of every chain (m, pair): the first l at which |mu_l| >= 2^-200,
+// with (mu_{l-1}, mu_l) there; l_c = lmax + 1 if the chain never gets there.
+__global__ void k_chain_scan(const RingInfo* __restrict__ rings, const double* __restrict__ cmm,
+                             const double* __restrict__ coef_c, int lmax, int npair, int* lc_tab,
+                             double* mu0_tab, double* mu1_tab) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (p >= npair) return;
+  const double z = rings[p].z, s = rings[p].sinth;
+  // sin^m by binary powering on (mantissa, exponent) pairs
+  int es;
+  const double fs = frexp(s, &es);
+  double rm = 1.0, bm = fs;
+  long long er = 0, eb = 0;
+  for (int n = m; n > 0; n >>= 1) {
+    int e;
+    if (n & 1) {
+      rm = frexp(rm * bm, &e);
+      er += eb + e;
+    }
+    if (n > 1) {
+      bm = frexp(bm * bm, &e);
+      eb = 2 * eb + e;
+    }
+  }
+  int e1;
+  const double v0 = frexp(cmm[m] * rm, &e1);
+  const long long E = er + (long long)m * es + e1;  // |lambda_mm| in [2^(E-1), 2^E)
+  long long k = 0;
+  if (E < -(kSigExp - 1)) k = (-(kSigExp - 1) - E + 511) / 512;
+  double mu1 = ldexp(v0, (int)(E + 512 * k)), mu2 = 0.0;
+  int l = m;
+  const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
+  while (k > 0 && l < lmax) {
+    ++l;
+    const double mu = fma(coef_c[base + l] * z, mu1, -mu2);
+    mu2 = mu1;
+    mu1 = mu;
+    if (fabs(mu1) >= 0x1p312) {
+      mu1 *= 0x1p-512;
+      mu2 *= 0x1p-512;
+      --k;
+    }
+  }
+  const long long ci = (long long)m * npair + p;
+  if (k > 0) {
+    lc_tab[ci] = lmax + 1;
+    mu0_tab[ci] = 0.0;
+    mu1_tab[ci] = 0.0;
+  } else {
+    lc_tab[ci] = l;
+    mu0_tab[ci] = mu2;
+    mu1_tab[ci] = mu1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// analysis
+// ---------------------------------------------------------------------------
+// G_m(y) = w_y exp(-i m phi_{0,y}) X_y[m mod N_y], with X_y[N - k] = conj X_y[k]
+// (the m-aliasing fold of Eq. 26 for m >= N_y / 2).
+template <typename T>
+__device__ __forceinline__ C2<T> ring_coef(const C2<T>* __restrict__ spec, const C2<T>* __restrict__ etab,
+                                           const RingInfo& R, int m, int b, long long nspec, int use_w) {
+  const int N = R.nphi, H = N >> 1;
+  const int k = m % N;
+  const C2<T>* X = spec + (long long)b * nspec + R.specoff;
+  const C2<T> x = (k <= H) ? X[k] : cconj(X[N - k]);
+  C2<T> g = cmul(x, etab[R.etab + ((long long)R.sigma * m) % (2LL * N)]);
+  if (use_w) g = cscale(g, (T)R.w);
+  return g;
+}
+
+// Lane tiling of the (LB x 2CP) output block of one warp: each lane owns LPL
+// consecutive l and CPL consecutive real components.
+template <int C2N> struct LaneTile;
+template <> struct LaneTile<2> { static constexpr int CPL = 2, LPL = 1; };
+template <> struct LaneTile<4> { static constexpr int CPL = 4, LPL = 1; };
+template <> struct LaneTile<8> { static constexpr int CPL = 4, LPL = 2; };
+template <> struct LaneTile<16> { static constexpr int CPL = 4, LPL = 4; };
+template <> struct LaneTile<32> { static constexpr int CPL = 8, LPL = 4; };
+
+template <typename T> struct MuStride { static constexpr int v = LB + 16 / (int)sizeof(T); };
+
+template <typename T, int CP>
+size_t analysis_smem(int nthr) {
+  constexpr int C2N = 2 * CP;
+  const int nwarp = nthr / 32;
+  return sizeof(T) * ((size_t)nthr * 2 * C2N + (size_t)nthr * MuStride<T>::v +
+                      (size_t)nwarp * LB * C2N + 2 * LB * C2N) +
+         sizeof(double) * LB;
+}
+
+// One cluster per m; CTA r of the cluster owns ring pairs [r nthr, (r+1) nthr),
+// one recurrence chain per thread.  Per block of LB l values: the chains
+// write mu into shared memory, each warp contracts its 32 chains with their
+// S/A ring coefficients, the warps' partial sums are added in shared memory,
+// and the cluster adds the CTAs' partials through distributed shared memory
+// (double-buffered, one cluster barrier per block).  Deterministic order.
+template <typename T, int CP>
+__global__ void __launch_bounds__(512)
+k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const RingInfo* __restrict__ rings,
+                    const C2<T>* __restrict__ etab, const double* __restrict__ coef_c,
+                    const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
+                    const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
+                    int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w) {
+  using V = C2<T>;
+  constexpr int C2N = 2 * CP;
+  constexpr int CPL = LaneTile<C2N>::CPL, LPL = LaneTile<C2N>::LPL, NCQ = C2N / CPL;
+  constexpr int MS = MuStride<T>::v;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank(), csize = (int)cluster.num_blocks();
+  const int nthr = blockDim.x, nwarp = nthr >> 5;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int m = blockIdx.y;
+  const int p = crank * nthr + t;
+  const bool active = p < npair;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sG = reinterpret_cast<T*>(smem_raw);      // [nthr][2][C2N]  S, A
+  T* sMu = sG + (size_t)nthr * 2 * C2N;        // [nthr][MS]
+  T* sW = sMu + (size_t)nthr * MS;             // [nwarp][LB][C2N]
+  T* sC = sW + (size_t)nwarp * LB * C2N;       // [2][LB][C2N]
+  double* sCz = reinterpret_cast<double*>(sC + 2 * LB * C2N);  // [LB]
+
+  double z = 0.0, s0 = 0.0, s1 = 0.0;
+  int lc = INT_MAX;
+  {
+    T* g = sG + (size_t)t * 2 * C2N;
+    if (active) {
+      const int ys = (p == npair - 1) ? -1 : nring - 1 - p;
+      const RingInfo Rn = rings[p];
+      z = Rn.z;
+      const long long ci = (long long)m * npair + p;
+      lc = lc_tab[ci];
+      s0 = mu0_tab[ci];
+      s1 = mu1_tab[ci];
+      if (lc > lmax) lc = INT_MAX;
+      for (int c = 0; c < CP; ++c) {
+        V gn = cmk<V>(0, 0), gs = cmk<V>(0, 0);
+        if (c < nb && lc != INT_MAX) {
+          gn = ring_coef<T>(spec, etab, Rn, m, b0 + c, nspec, use_w);
+          if (ys >= 0) gs = ring_coef<T>(spec, etab, rings[ys], m, b0 + c, nspec, use_w);
+        }
+        const V S = cadd(gn, gs), A = csub(gn, gs);
+        g[2 * c] = S.x;
+        g[2 * c + 1] = S.y;
+        g[C2N + 2 * c] = A.x;
+        g[C2N + 2 * c + 1] = A.y;
+      }
+    } else {
+      for (int c = 0; c < 2 * C2N; ++c) g[c] = (T)0;
+    }
+  }
+
+  const long long base = alm_base(lmax, m);
+  const int lq = lane / NCQ, cq = lane % NCQ;
+  const int l0 = lq * LPL, c0 = cq * CPL;
+  double mu1 = 0.0, mu2 = 0.0;
+  int buf = 0;
+  for (int lb0 = m; lb0 <= lmax; lb0 += LB) {
+    if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
+    __syncthreads();
+    // --- recurrence: LB steps of mu_l = c_l z mu_{l-1} - mu_{l-2} ---
+    T* myMu = sMu + (size_t)t * MS;
+    if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
+#pragma unroll
+      for (int i4 = 0; i4 < LB; i4 += 4) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int l = lb0 + i4 + u;
+          double mu = fma(sCz[i4 + u] * z, mu1, -mu2);
+          if (l == lc) {
+            mu = s1;
+            mu1 = s0;
+          }
+          mu2 = mu1;
+          mu1 = mu;
+          v[u] = (T)mu;
+        }
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+          *reinterpret_cast<double2*>(myMu + i4) = make_double2(v[0], v[1]);
+          *reinterpret_cast<double2*>(myMu + i4 + 2) = make_double2(v[2], v[3]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < LB; ++i) myMu[i] = (T)0;
+    }
+    const int any_active = __syncthreads_or(lc < lb0 + LB);
+    T* cpart = sC + buf * LB * C2N;
+    if (any_active) {
+      // --- contraction of this warp's 32 chains ---
+      T acc[LPL][CPL];
+#pragma unroll
+      for (int a = 0; a < LPL; ++a)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[a][c] = (T)0;
+      const T* muw = sMu + (size_t)(warp * 32) * MS + l0;
+      const T* gw = sG + (size_t)(warp * 32) * 2 * C2N + c0;
+#pragma unroll 4
+      for (int j = 0; j < 32; ++j) {
+        T mv[LPL], gsv[CPL], gav[CPL];
+#pragma unroll
+        for (int a = 0; a < LPL; ++a) mv[a] = muw[(size_t)j * MS + a];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          gsv[c] = gw[(size_t)j * 2 * C2N + c];
+          gav[c] = gw[(size_t)j * 2 * C2N + C2N + c];
+        }
+#pragma unroll
+        for (int a = 0; a < LPL; ++a) {
+          const bool odd = ((l0 + a) & 1) != 0;
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) acc[a][c] = fma(mv[a], odd ? gav[c] : gsv[c], acc[a][c]);
+        }
+      }
+      T* wp = sW + (size_t)warp * LB * C2N;
+#pragma unroll
+      for (int a = 0; a < LPL; ++a)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) wp[(l0 + a) * C2N + c0 + c] = acc[a][c];
+      __syncthreads();
+      for (int o = t; o < LB * C2N; o += nthr) {
+        T s = (T)0;
+        for (int w = 0; w < nwarp; ++w) s += sW[(size_t)w * LB * C2N + o];
+        cpart[o] = s;
+      }
+    } else {
+      for (int o = t; o < LB * C2N; o += nthr) cpart[o] = (T)0;
+    }
+    // --- cluster reduction; CTA r writes its share of the block ---
+    cluster.sync();
+    {
+      const int nout = LB * C2N;
+      const int per = (nout + csize - 1) / csize;
+      const int q_end = min(nout, (crank + 1) * per);
+      for (int q = crank * per + t; q < q_end; q += nthr) {
+        const int part = q & 1, li = (q >> 1) % LB, bb = (q >> 1) / LB;
+        const int l = lb0 + li;
+        if (l > lmax || bb >= nb) continue;
+        const int o = li * C2N + 2 * bb + part;
+        T s = (T)0;
+        for (int r = 0; r < csize; ++r) s += cluster.map_shared_rank(cpart, r)[o];
+        alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part] = (T)(coef_p[base + l] * (double)s);
+      }
+    }
+    buf ^= 1;
+  }
+  cluster.sync();  // peers may still read this CTA's partials
+}
+
+// ---------------------------------------------------------------------------
+// synthesis
+// ---------------------------------------------------------------------------
+// One thread per chain (m, pair): E_m = sum over even l - m of a_lm lambda_lm,
+// O_m = sum over odd l - m; F_m(y) = E + O on the northern ring and
+// F_m(y') = E - O on its mirror (Eq. 24 before the ring transform).  The
+// block's coefficients (pre-multiplied by P_l) are broadcast from shared
+// memory.
+template <typename T, int CP>
+__global__ void __launch_bounds__(128)
+k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const RingInfo* __restrict__ rings,
+                     const double* __restrict__ coef_c, const float* __restrict__ coef_pf,
+                     const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
+                     const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
+                     int mmax, int npair, int nring, long long nalm, int b0, int nb) {
+  using V = C2<T>;
+  constexpr int C2N = 2 * CP;
+  __shared__ __align__(16) T sA[LB][C2N];
+  __shared__ double sCz[LB];
+  __shared__ int sMinLc;
+  const int m = blockIdx.y, t = threadIdx.x, nthr = blockDim.x;
+  const int p = blockIdx.x * nthr + t;
+  const bool active = p < npair;
+  double z = 0.0, s0 = 0.0, s1 = 0.0;
+  int lc = INT_MAX;
+  if (active) {
+    z = rings[p].z;
+    const long long ci = (long long)m * npair + p;
+    lc = lc_tab[ci];
+    s0 = mu0_tab[ci];
+    s1 = mu1_tab[ci];
+    if (lc > lmax) lc = INT_MAX;
+  }
+  if (t == 0) sMinLc = INT_MAX;
+  __syncthreads();
+  atomicMin(&sMinLc, lc);
+  __syncthreads();
+  const int lstart = sMinLc;
+  T accE[C2N], accO[C2N];
+#pragma unroll
+  for (int c = 0; c < C2N; ++c) accE[c] = accO[c] = (T)0;
+  const long long base = alm_base(lmax, m);
+  double mu1 = 0.0, mu2 = 0.0;
+  if (lstart <= lmax) {
+    for (int lb0 = m + ((lstart - m) / LB) * LB; lb0 <= lmax; lb0 += LB) {
+      for (int q = t; q < LB * C2N; q += nthr) {
+        const int li = q / C2N, c = q % C2N, bb = c >> 1, part = c & 1;
+        const int l = lb0 + li;
+        T v = (T)0;
+        if (l <= lmax && bb < nb && !(m == 0 && part == 1)) {
+          const T a = alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part];
+          if constexpr (sizeof(T) == 4) v = coef_pf[base + l] * a;
+          else v = (T)(coef_p[base + l] * (double)a);
+        }
+        sA[li][c] = v;
+      }
+      if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
+      __syncthreads();
+#pragma unroll 4
+      for (int i = 0; i < LB; i += 2) {
+        {
+          double mu = fma(sCz[i] * z, mu1, -mu2);
+          if (lb0 + i == lc) {
+            mu = s1;
+            mu1 = s0;
+          }
+          mu2 = mu1;
+          mu1 = mu;
+          const T mf = (T)mu;
+#pragma unroll
+          for (int c = 0; c < C2N; ++c) accE[c] = fma(mf, sA[i][c], accE[c]);
+        }
+        {
+          double mu = fma(sCz[i + 1] * z, mu1, -mu2);
+          if (lb0 + i + 1 == lc) {
+            mu = s1;
+            mu1 = s0;
+          }
+          mu2 = mu1;
+          mu1 = mu;
+          const T mf = (T)mu;
+#pragma unroll
+          for (int c = 0; c < C2N; ++c) accO[c] = fma(mf, sA[i + 1][c], accO[c]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (active) {
+    const int ys = (p == npair - 1) ? -1 : nring - 1 - p;
+#pragma unroll
+    for (int bb = 0; bb < CP; ++bb) {
+      if (bb < nb) {
+        const V e = cmk<V>(accE[2 * bb], accE[2 * bb + 1]);
+        const V o = cmk<V>(accO[2 * bb], accO[2 * bb + 1]);
+        F[((long long)(b0 + bb) * nring + p) * (mmax + 1) + m] = cadd(e, o);
+        if (ys >= 0) F[((long long)(b0 + bb) * nring + ys) * (mmax + 1) + m] = csub(e, o);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static void analysis_shape(int npair, int* nthr, int* csize) {
+  if (npair <= 256) {
+    *nthr = ((npair + 31) / 32) * 32;
+    *csize = 1;
+  } else {
+    *nthr = npair / 8 > 256 ? npair / 8 : 256;
+    *csize = (npair + *nthr - 1) / *nthr;
+  }
+}
+
+template <typename T, int CP>
+static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s) {
+  using V = C2<T>;
+  int nthr, csize;
+  analysis_shape(p->npair, &nthr, &csize);
+  const size_t smem = analysis_smem<T, CP>(nthr);
+  cudaError_t e = cudaFuncSetAttribute(k_legendre_analysis<T, CP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize, p->mmax + 1, 1);
+  cfg.blockDim = dim3(nthr, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
+    const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
+    e = cudaLaunchKernelEx(&cfg, k_legendre_analysis<T, CP>, (const V*)p->d_spec, alm,
+                           (const RingInfo*)p->d_ring, (const V*)p->d_etab, (const double*)p->d_coef_c,
+                           (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
+                           (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
+                           use_w ? 1 : 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static int pick_cp(const hpx_plan_s* p) {
+  int nthr, csize;
+  analysis_shape(p->npair, &nthr, &csize);
+  const int cmax = sizeof(T) == 4 ? 16 : 8;
+  int cp = 1;
+  while (cp < p->nbatch && cp < cmax) cp *= 2;
+  auto fits = [&](int c) {
+    size_t sm = 0;
+    switch (c) {
+      case 1: sm = analysis_smem<T, 1>(nthr); break;
+      case 2: sm = analysis_smem<T, 2>(nthr); break;
+      case 4: sm = analysis_smem<T, 4>(nthr); break;
+      case 8: sm = analysis_smem<T, 8>(nthr); break;
+      default: sm = analysis_smem<T, 16>(nthr); break;
+    }
+    return sm <= 200 * 1024;
+  };
+  while (cp > 1 && !fits(cp)) cp /= 2;
+  return cp;
+}
+
+template <typename T>
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s) {
+  switch (pick_cp<T>(p)) {
+    case 1: return launch_analysis_cp<T, 1>(p, alm, use_w, s);
+    case 2: return launch_analysis_cp<T, 2>(p, alm, use_w, s);
+    case 4: return launch_analysis_cp<T, 4>(p, alm, use_w, s);
+    case 8: return launch_analysis_cp<T, 8>(p, alm, use_w, s);
+    default:
+      if constexpr (sizeof(T) == 4) return launch_analysis_cp<T, 16>(p, alm, use_w, s);
+      else return launch_analysis_cp<T, 8>(p, alm, use_w, s);
+  }
+}
+
+template <typename T, int CP>
+static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaStream_t s) {
+  using V = C2<T>;
+  const int nthr = 128;
+  dim3 grid((p->npair + nthr - 1) / nthr, p->mmax + 1);
+  for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
+    const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
+    k_legendre_synthesis<T, CP><<<grid, nthr, 0, s>>>(
+        alm, (V*)p->d_F, p->d_ring, p->d_coef_c, p->d_coef_pf, p->d_coef_p, p->d_lc, p->d_mu0, p->d_mu1,
+        p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s) {
+  int cp = 1;
+  const int cmax = sizeof(T) == 4 ? 16 : 8;
+  while (cp < p->nbatch && cp < cmax) cp *= 2;
+  switch (cp) {
+    case 1: return launch_synthesis_cp<T, 1>(p, alm, s);
+    case 2: return launch_synthesis_cp<T, 2>(p, alm, s);
+    case 4: return launch_synthesis_cp<T, 4>(p, alm, s);
+    case 8: return launch_synthesis_cp<T, 8>(p, alm, s);
+    default:
+      if constexpr (sizeof(T) == 4) return launch_synthesis_cp<T, 16>(p, alm, s);
+      else return launch_synthesis_cp<T, 8>(p, alm, s);
+  }
+}
+
+cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s) {
+  const int mb = (p->mmax + 1 + 127) / 128;
+  k_lambda_mm_prefactor<<<mb, 128, 0, s>>>(p->mmax, p->d_cmm);
+  k_recurrence_coefs<<<mb, 128, 0, s>>>(p->lmax, p->mmax, p->d_coef_c, p->d_coef_p, p->d_coef_pf);
+  k_chain_scan<<<dim3((p->npair + 127) / 128, p->mmax + 1), 128, 0, s>>>(
+      p->d_ring, p->d_cmm, p->d_coef_c, p->lmax, p->npair, p->d_lc, p->d_mu0, p->d_mu1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, cudaStream_t);
+template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, cudaStream_t);
+template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, cudaStream_t);
+template cudaError_t launch_synthesis<double>(const hpx_plan_s*, const double*, cudaStream_t);
+
+}  // namespace hpx

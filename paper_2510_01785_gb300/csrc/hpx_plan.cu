@@ -1,0 +1,378 @@
+// libhpx C ABI: plans, the device-built ring geometry, and the transform
+// entry points declared in hpx.h.
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "hpx_internal.cuh"
+
+namespace hpx {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+hpx_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HPX_ERR_NOMEM : HPX_ERR_CUDA;
+}
+
+static bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+__device__ __forceinline__ int dlog2(long long v) { return 63 - __clzll(v); }
+__device__ __forceinline__ long long dnextpow2(long long v) {
+  long long r = 1;
+  while (r < v) r <<= 1;
+  return r;
+}
+
+// Ring y of the HEALPix grid (Sec. III-A; pixel centres as defined by
+// Gorski et al. 2005).  With the 1-based ring index i = y + 1:
+//   polar cap, i < nside: N = 4i, z = 1 - i^2 / (3 nside^2), phi_0 = pi / N;
+//   belt, nside <= i <= 3 nside: N = 4 nside, z = (2 nside - i) 2 / (3 nside),
+//     phi_0 = s pi / N with s = (i - nside + 1) mod 2;
+//   south cap: mirror of the north cap.
+// sin(theta) comes from exact integer forms of (1 - z)(1 + z).  Also records
+// each ring's offsets into the half-spectrum workspace and the FFT tables.
+__global__ void k_ring_geometry(int nside, RingInfo* rings) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ns = nside, npix = 12 * ns * ns;
+  if (y >= 4 * nside - 1) return;
+  const long long i = (long long)y + 1;
+  const bool south = i > 2 * ns;
+  const long long ii = south ? 4 * ns - i : i;
+  RingInfo R;
+  R.pad = 0;
+  if (ii < ns) {
+    const double den = 3.0 * (double)(ns * ns);
+    R.nphi = (int)(4 * ii);
+    R.sigma = 1;
+    R.z = 1.0 - (double)(ii * ii) / den;
+    R.sinth = (double)ii * sqrt((double)(6 * ns * ns - ii * ii)) / den;
+    R.start = south ? npix - 2 * ii * (ii + 1) : 2 * ii * (ii - 1);
+    R.specoff = south ? (ns * ns - 1) + (2 * ns + 1) * (2 * ns + 1) + ns * ns - (ii + 1) * (ii + 1)
+                      : ii * ii - 1;
+    R.etab = 4 * ii * (ii - 1);
+    const long long H = 2 * ii;
+    if ((ii & (ii - 1)) == 0) {
+      R.logm = dlog2(H);
+      R.btab = -1;
+    } else {
+      R.logm = dlog2(dnextpow2(4 * ii - 1));
+      long long off = 0;
+      for (long long j = 1; j < ii; ++j)
+        if ((j & (j - 1)) != 0) off += dnextpow2(4 * j - 1);
+      R.btab = off;
+    }
+  } else {
+    R.nphi = (int)(4 * ns);
+    R.sigma = (int)((i - ns + 1) & 1);
+    R.z = (double)(2 * (2 * ns - ii)) / (double)(3 * ns);
+    R.sinth = sqrt((double)((2 * ii - ns) * (7 * ns - 2 * ii))) / (double)(3 * ns);
+    R.start = 2 * ns * (ns - 1) + 4 * ns * (i - ns);
+    R.specoff = (ns * ns - 1) + (i - ns) * (2 * ns + 1);
+    R.etab = 4 * ns * (ns - 1);
+    R.logm = dlog2(2 * ns);
+    R.btab = -1;
+  }
+  if (south) R.z = -R.z;
+  R.w = (4.0 * 3.14159265358979323846) / (double)npix;
+  rings[y] = R;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static void plan_free(hpx_plan_s* p) {
+  if (!p) return;
+  void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
+                  p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+static bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+static hpx_status check_call(const hpx_plan_s* p, const void* in, const void* out) {
+  if (!p) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  if (!in || !out) {
+    set_error("null data pointer");
+    return HPX_ERR_INVALID;
+  }
+  if (!aligned16(in) || !aligned16(out)) {
+    set_error("data pointers must be 16-byte aligned");
+    return HPX_ERR_INVALID;
+  }
+  return HPX_OK;
+}
+
+size_t real_size(const hpx_plan_s* p) { return p->dtype == HPX_F64 ? sizeof(double) : sizeof(float); }
+
+template <typename T>
+static cudaError_t run_analysis(const hpx_plan_s* p, const void* map, void* alm, bool weighted, cudaStream_t s) {
+  cudaError_t e = launch_r2c<T>(p, static_cast<const T*>(map), s);
+  if (e == cudaSuccess) e = launch_analysis<T>(p, static_cast<T*>(alm), weighted, s);
+  return e;
+}
+
+template <typename T>
+static cudaError_t run_synthesis(const hpx_plan_s* p, const void* alm, void* map, bool weighted, cudaStream_t s) {
+  cudaError_t e = launch_synthesis<T>(p, static_cast<const T*>(alm), s);
+  if (e == cudaSuccess) e = launch_c2r<T>(p, static_cast<T*>(map), weighted, s);
+  return e;
+}
+
+static hpx_status transform(hpx_plan p, const void* in, void* out, hpx_stream_t stream, bool analysis,
+                            bool weighted, const char* name) {
+  hpx_status st = check_call(p, in, out);
+  if (st != HPX_OK) return st;
+  DeviceGuard g(p->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (analysis)
+    e = p->dtype == HPX_F64 ? run_analysis<double>(p, in, out, weighted, s)
+                            : run_analysis<float>(p, in, out, weighted, s);
+  else
+    e = p->dtype == HPX_F64 ? run_synthesis<double>(p, in, out, weighted, s)
+                            : run_synthesis<float>(p, in, out, weighted, s);
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return HPX_OK;
+}
+
+}  // namespace hpx
+
+using namespace hpx;
+
+extern "C" {
+
+int64_t hpx_nalm(int lmax, int mmax) {
+  if (lmax < 0 || mmax < 0 || mmax > lmax) return 0;
+  return (int64_t)(mmax + 1) * (lmax + 1) - (int64_t)mmax * (mmax + 1) / 2;
+}
+
+const char* hpx_last_error(void) { return g_err.c_str(); }
+
+hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
+                              hpx_plan* out) {
+  if (!out) {
+    set_error("null output pointer");
+    return HPX_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (nside < 1 || nside > 2048 || !is_pow2(nside)) {
+    set_error("nside must be a power of two in [1, 2048], got %d", nside);
+    return HPX_ERR_INVALID;
+  }
+  if (lmax < 0 || lmax > 16384 || mmax < 0 || mmax > lmax) {
+    set_error("need 0 <= mmax <= lmax <= 16384, got lmax %d mmax %d", lmax, mmax);
+    return HPX_ERR_INVALID;
+  }
+  if (nbatch < 1 || nbatch > 65535) {
+    set_error("nbatch must be in [1, 65535], got %d", nbatch);
+    return HPX_ERR_INVALID;
+  }
+  if (dtype != HPX_F64 && dtype != HPX_F32) {
+    set_error("dtype %d is not provided by this build", (int)dtype);
+    return HPX_ERR_UNSUPPORTED;
+  }
+  if (flags & ~HPX_PLAN_LAMBDA_TABLE) {
+    set_error("unknown plan flags 0x%x", flags);
+    return HPX_ERR_INVALID;
+  }
+  if (flags & HPX_PLAN_LAMBDA_TABLE) {
+    set_error("HPX_PLAN_LAMBDA_TABLE is not provided by this build");
+    return HPX_ERR_UNSUPPORTED;
+  }
+  hpx_plan_s* p = new hpx_plan_s();
+  std::memset(p, 0, sizeof(*p));
+  cudaGetDevice(&p->device);
+  p->nside = nside;
+  p->lmax = lmax;
+  p->mmax = mmax;
+  p->nbatch = nbatch;
+  p->dtype = dtype;
+  p->flags = flags;
+  p->nring = 4 * nside - 1;
+  p->npair = 2 * nside;
+  p->npix = 12LL * nside * nside;
+  p->nalm = hpx_nalm(lmax, mmax);
+  p->nspec = 6LL * nside * nside + 4LL * nside - 1;
+  p->netab = 4LL * nside * (nside - 1) + 8LL * nside;
+  p->nbtab = 0;
+  p->logm_max = ilog2(2LL * nside);
+  for (long long i = 1; i < nside; ++i) {
+    if (is_pow2(i)) continue;
+    long long M = 1;
+    while (M < 4 * i - 1) M <<= 1;
+    p->nbtab += M;
+    if (ilog2(M) > p->logm_max) p->logm_max = ilog2(M);
+  }
+  p->logtw = p->logm_max;
+  const size_t rs = real_size(p), cs = 2 * rs;
+  const long long nchain = (long long)(mmax + 1) * p->npair;
+
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      cuda_fail(e, "cudaMalloc");
+      *ptr = nullptr;
+      return false;
+    }
+    p->bytes += bytes;
+    return true;
+  };
+  bool ok = alloc((void**)&p->d_ring, sizeof(RingInfo) * p->nring) &&
+            alloc(&p->d_etab, cs * p->netab) && alloc(&p->d_btab, cs * p->nbtab) &&
+            alloc(&p->d_tw, cs * ((size_t)1 << (p->logtw - 1))) &&
+            alloc((void**)&p->d_cmm, sizeof(double) * (mmax + 1)) &&
+            alloc((void**)&p->d_coef_c, sizeof(double) * p->nalm) &&
+            alloc((void**)&p->d_coef_p, sizeof(double) * p->nalm) &&
+            alloc((void**)&p->d_coef_pf, sizeof(float) * p->nalm) &&
+            alloc((void**)&p->d_lc, sizeof(int) * nchain) && alloc((void**)&p->d_mu0, sizeof(double) * nchain) &&
+            alloc((void**)&p->d_mu1, sizeof(double) * nchain) &&
+            alloc(&p->d_spec, cs * (size_t)nbatch * p->nspec) &&
+            alloc(&p->d_F, cs * (size_t)nbatch * p->nring * (mmax + 1));
+  if (!ok) {
+    plan_free(p);
+    return HPX_ERR_NOMEM;
+  }
+  cudaStream_t s;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    plan_free(p);
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  k_ring_geometry<<<(p->nring + 127) / 128, 128, 0, s>>>(nside, p->d_ring);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = build_recurrence_tables(p, s);
+  if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    plan_free(p);
+    return cuda_fail(e, "plan construction");
+  }
+  *out = p;
+  return HPX_OK;
+}
+
+hpx_status hpx_plan_create(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, hpx_plan* out) {
+  return hpx_plan_create_ex(nside, lmax, mmax, nbatch, dtype, HPX_PLAN_LAMBDA_RECOMPUTE, out);
+}
+
+hpx_status hpx_plan_destroy(hpx_plan plan) {
+  if (!plan) return HPX_OK;
+  DeviceGuard g(plan->device);
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  return HPX_OK;
+}
+
+size_t hpx_plan_device_bytes(hpx_plan plan) { return plan ? plan->bytes : 0; }
+
+hpx_status hpx_map2alm(hpx_plan plan, const void* map, void* alm, hpx_stream_t stream) {
+  return transform(plan, map, alm, stream, true, true, "hpx_map2alm");
+}
+
+hpx_status hpx_alm2map_adjoint(hpx_plan plan, const void* map, void* alm, hpx_stream_t stream) {
+  return transform(plan, map, alm, stream, true, false, "hpx_alm2map_adjoint");
+}
+
+hpx_status hpx_alm2map(hpx_plan plan, const void* alm, void* map, hpx_stream_t stream) {
+  return transform(plan, alm, map, stream, false, false, "hpx_alm2map");
+}
+
+hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map, hpx_stream_t stream) {
+  return transform(plan, alm, map, stream, false, true, "hpx_map2alm_adjoint");
+}
+
+static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_t stream, bool analysis) {
+  if (!p || !hin || !hout) {
+    set_error("null argument");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(p->device);
+  const size_t rs = real_size(p);
+  const size_t map_bytes = rs * (size_t)p->nbatch * p->npix;
+  const size_t alm_bytes = 2 * rs * (size_t)p->nbatch * p->nalm;
+  if (!p->d_io_map) {
+    cudaError_t e = cudaMalloc(&p->d_io_map, map_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (host I/O buffer)");
+    p->bytes += map_bytes;
+  }
+  if (!p->d_io_alm) {
+    cudaError_t e = cudaMalloc(&p->d_io_alm, alm_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (host I/O buffer)");
+    p->bytes += alm_bytes;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* din = analysis ? p->d_io_map : p->d_io_alm;
+  void* dout = analysis ? p->d_io_alm : p->d_io_map;
+  const size_t in_bytes = analysis ? map_bytes : alm_bytes, out_bytes = analysis ? alm_bytes : map_bytes;
+  cudaError_t e = cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  hpx_status st = analysis ? hpx_map2alm(p, din, dout, stream) : hpx_alm2map(p, din, dout, stream);
+  if (st != HPX_OK) return st;
+  e = cudaMemcpyAsync(hout, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  return HPX_OK;
+}
+
+hpx_status hpx_map2alm_host(hpx_plan plan, const void* host_map, void* host_alm, hpx_stream_t stream) {
+  return host_call(plan, host_map, host_alm, stream, true);
+}
+
+hpx_status hpx_alm2map_host(hpx_plan plan, const void* host_alm, void* host_map, hpx_stream_t stream) {
+  return host_call(plan, host_alm, host_map, stream, false);
+}
+
+hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi, double* z, double* sinth,
+                               int32_t* sigma) {
+  if (!plan || !start || !nphi || !z || !sinth || !sigma) {
+    set_error("null argument");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(plan->device);
+  std::vector<RingInfo> h(plan->nring);
+  cudaError_t e = cudaMemcpy(h.data(), plan->d_ring, sizeof(RingInfo) * plan->nring, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "ring table copy");
+  for (int y = 0; y < plan->nring; ++y) {
+    start[y] = h[y].start;
+    nphi[y] = h[y].nphi;
+    z[y] = h[y].z;
+    sinth[y] = h[y].sinth;
+    sigma[y] = h[y].sigma;
+  }
+  return HPX_OK;
+}
+
+}  // extern "C"

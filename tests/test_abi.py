@@ -1,0 +1,68 @@
+"""The C ABI library loads and exports every entry point include/hpx.h
+declares; host-only entry points and argument validation work without a GPU
+(no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hpx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hpx_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def hpxlib():
+    from paper_2510_01785_gb300 import build as b
+    b.build()
+    from paper_2510_01785_gb300 import _lib
+    return _lib
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["hpx_plan_create", "hpx_plan_destroy", "hpx_map2alm", "hpx_alm2map",
+                     "hpx_map2alm_adjoint", "hpx_alm2map_adjoint", "hpx_plan_device_bytes",
+                     "hpx_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(hpxlib):
+    L = hpxlib.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert name in hpxlib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_nalm(hpxlib):
+    L = hpxlib.lib()
+    assert L.hpx_nalm(95, 95) == 4656
+    assert L.hpx_nalm(3071, 3071) == 4720128
+    assert L.hpx_nalm(2047, 2047) == 2098176
+    assert L.hpx_nalm(767, 767) == 295296
+    assert L.hpx_nalm(10, 3) == 11 + 10 + 9 + 8
+    assert L.hpx_nalm(5, 7) == 0
+
+
+@pytest.mark.parametrize("args", [(3, 8, 8, 1, 1), (0, 8, 8, 1, 1), (16, 10, 11, 1, 1),
+                                  (16, 10, 10, 0, 1), (16, -1, 0, 1, 1)])
+def test_invalid_plan_arguments_are_rejected(hpxlib, args):
+    L = hpxlib.lib()
+    h = ctypes.c_void_p()
+    st = L.hpx_plan_create(*args, ctypes.byref(h))
+    assert st == 1  # HPX_ERR_INVALID, before any CUDA call
+    assert h.value is None
+    assert L.hpx_last_error()
+
+
+def test_null_plan_calls_are_rejected(hpxlib):
+    L = hpxlib.lib()
+    buf = ctypes.create_string_buffer(64)
+    assert L.hpx_map2alm(None, buf, buf, None) == 1
+    assert L.hpx_plan_destroy(None) == 0
+    assert L.hpx_plan_device_bytes(None) == 0
