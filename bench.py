@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput benchmark: HEALPix RING spherical harmonic analysis + synthesis.
+
+Workload (one step): map2alm followed by alm2map of one batch of 8 FP32
+channels at Nside 1024 (12,582,912 pixels, 4095 rings), lmax = mmax = 3071,
+lambda_lm from the FP64 recurrence.  Channels 0-3 are band-limited fields
+(a_lm ~ N(0, (l+1)^-2), synthesised), channels 4-7 white noise; all inputs
+are seeded and synthetic and already resident in HBM when timing starts
+(maps 403 MB, coefficients 302 MB: larger than the 129 MB L2, so no flush).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = channel analysis+synthesis pairs per second
+over all ranks (weak scaling: every rank runs the full workload on its own
+GPU; replicas only, no data-path collective).  --impl reference times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SHT analysis+synthesis per s at Nside 1024 vs roofline; serving p50/p99 latency"
+UNIT = "analysis+synthesis/s"
+NSIDE, LMAX, MMAX, NBATCH = 1024, 3071, 3071, 8
+WORKLOAD = "healpix-sht-nside1024-lmax3071-b8-f32"
+SEED = 2510017850 + 2
+
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x
+# 2 flop x 2.07 GHz (the published 1.25 TFLOP/s dense FP64 of a GB300).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiling only")
+    ap.add_argument("--lmax", type=int, default=None)
+    ap.add_argument("--nbatch", type=int, default=NBATCH)
+    a = ap.parse_args()
+    set_workload(a.nside, a.lmax if a.lmax is not None else 3 * a.nside - 1, a.nbatch)
+    return a
+
+
+def set_workload(nside: int, lmax: int, nbatch: int) -> None:
+    global NSIDE, LMAX, MMAX, NBATCH, WORKLOAD
+    NSIDE, LMAX, MMAX, NBATCH = nside, lmax, lmax, nbatch
+    WORKLOAD = f"healpix-sht-nside{nside}-lmax{lmax}-b{nbatch}-f32"
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# --------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29517")
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist.is_available() and dist.is_initialized():
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(dist, x: float, device) -> float:
+    """Largest x over ranks (x itself when not distributed)."""
+    import torch
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, steps: int, t_max_ms: float) -> float:
+    """channel analysis+synthesis pairs per second, all ranks together."""
+    return world * NBATCH * steps / (t_max_ms / 1e3)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"hpx_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.out)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample(step: int = 0, n_m: int = 2, n_r: int = 2):
+    """Time the FP64 oracle on a bounded sample of one step and extrapolate:
+    analysis of n_m whole m columns (all l, all 8 channels) and synthesis of
+    n_r whole rings (all 8 channels), spread over the workload and shifted by
+    `step`; the full step costs (mmax+1)/n_m and nring/n_r times as much."""
+    import numpy as np
+
+    import oracle
+    from paper_2510_01785_gb300 import synthetic as syn
+    R = 4 * NSIDE - 1
+    g = syn.rng(SEED + 1000 + step)
+    ms = np.sort(g.choice(MMAX + 1, n_m, replace=False)).astype(np.int32)
+    rings = np.sort(g.choice(R, n_r, replace=False)).astype(np.int32)
+    maps = syn.white_maps(SEED, NSIDE, NBATCH)
+    alm = syn.gaussian_alm(SEED + 1, LMAX, MMAX, NBATCH, power=2.0)
+    ls_all, ms_all = [], []
+    for m in ms:
+        ls_all.append(np.arange(m, LMAX + 1))
+        ms_all.append(np.full(LMAX + 1 - m, m))
+    ls_all = np.concatenate(ls_all).astype(np.int32)
+    ms_all = np.concatenate(ms_all).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.analysis_sep(maps, LMAX, ls_all, ms_all, weights="equal")
+    t1 = time.perf_counter()
+    oracle.synthesis_sep(alm, NSIDE, LMAX, MMAX, rings)
+    t2 = time.perf_counter()
+    t_step = (t1 - t0) * (MMAX + 1) / n_m + (t2 - t1) * R / n_r
+    return {"seconds_measured": t2 - t0, "seconds_per_step_extrapolated": t_step,
+            "value": NBATCH / t_step, "cores": oracle.max_threads(),
+            "sample": f"oracle tier B: analysis of m in {list(map(int, ms))} (all l, 8 ch) and synthesis "
+                      f"of rings {list(map(int, rings))} (8 ch), extrapolated x{(MMAX + 1) / n_m:.0f} "
+                      f"(m) and x{R / n_r:.0f} (rings)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    for w in range(args.warmup):
+        oracle_sample(step=-1 - w, n_m=8, n_r=8)
+    vals, secs = [], []
+    for k in range(args.steps):
+        r = oracle_sample(step=k, n_m=8, n_r=8)
+        vals.append(r["value"])
+        secs.append(r["seconds_per_step_extrapolated"])
+        last = r
+    value = len(vals) / sum(1.0 / v for v in vals)  # pairs per second over all sampled steps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX, "nbatch": NBATCH},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": "per step: " + last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured from the current source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2510_01785_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    for line in open(path):
+        kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if kv.get("kernel") == kernel and kv.get("source_sha") == sha and "dram_bytes_per_launch" in kv:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import synthetic as syn
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (the transforms have no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+
+    plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", device=dev)
+    alm_np = syn.gaussian_alm(SEED + 1, LMAX, MMAX, NBATCH, power=2.0).astype(np.complex64)
+    alm_in = torch.from_numpy(alm_np).to(dev)
+    maps = plan.alm2map(alm_in)  # first half band-limited, second half white noise
+    nbl = NBATCH // 2
+    maps[nbl:] = torch.from_numpy(syn.white_maps(SEED, NSIDE, NBATCH - nbl).astype(np.float32)).to(dev)
+    alm_out = plan.empty_alm()
+    map_out = plan.empty_map()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.map2alm(maps, out=alm_out)
+        plan.alm2map(alm_in, out=map_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.stage_times()  # clear
+
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    plan.set_timing(True)
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(dist, dev)
+    t_ms = e0.elapsed_time(e1)
+    plan.set_timing(False)
+    stages = plan.stage_times()
+    t_max = reduce_max(dist, t_ms, dev)
+    value = throughput(world, args.steps, t_max)
+
+    # the dominant kernel's roofline (FP64-pipe bound: the recurrence)
+    active, total = plan.chain_stats()
+    launches = sum(n for _, n in stages.values())
+    dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k][0])
+    ms_launch = stages[dom][0] / max(stages[dom][1], 1)
+    fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
+    achieved = fp64_flop / (ms_launch / 1e3) / 1e12
+    kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
+    traffic = kernel_traffic(kname)
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per launch "
+                        f"(of {total}; contributions below 2^-193 dropped)"}
+    stage_report = {}
+    for k, (ms, n) in stages.items():
+        stage_report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
+    map_bytes = 4 * NBATCH * 12 * NSIDE * NSIDE
+    alm_bytes = 8 * NBATCH * plan.nalm
+    spec_bytes = 8 * NBATCH * (6 * NSIDE * NSIDE + 4 * NSIDE - 1)
+    for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", map_bytes)):
+        s = stage_report[k]
+        s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
+    for k in ("legendre_analysis", "legendre_synthesis"):
+        s = stage_report[k]
+        s["fp64_tflops"] = fp64_flop / (s["ms_per_launch"] / 1e3) / 1e12
+        s["fp32_contraction_tflops"] = 4.0 * NBATCH * active / (s["ms_per_launch"] / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(plan, maps, alm_in, dist, dev, args.steps, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(step=0, n_m=64, n_r=64)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
+               "seconds": r["seconds_measured"]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX,
+                           "nbatch": NBATCH, "step": "map2alm + alm2map of the batch",
+                           "lambda": "FP64 recurrence recomputed in every transform",
+                           "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(plan, maps, alm_in, dist, dev, steps, world):
+    """The same step through the host-buffer C ABI calls: pinned host input,
+    host-to-device copy, transform, device-to-host copy, every step."""
+    import torch
+    map_bytes = maps.numel() * maps.element_size()
+    alm_bytes = alm_in.numel() * alm_in.element_size()
+    hmaps = maps.cpu().pin_memory()
+    halm = alm_in.cpu().pin_memory()
+    oalm = torch.empty_like(halm).pin_memory()
+    omap = torch.empty_like(hmaps).pin_memory()
+    plan.map2alm_host(hmaps, out=oalm)
+    plan.alm2map_host(halm, out=omap)
+    barrier(dist, dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.map2alm_host(hmaps, out=oalm)
+        plan.alm2map_host(halm, out=omap)
+    t_e2e = (time.perf_counter() - t0) * 1e3
+    t_e2e = reduce_max(dist, t_e2e, dev)
+    return {"value": throughput(world, steps, t_e2e), "unit": UNIT,
+            "h2d_bytes_per_step": map_bytes + alm_bytes, "d2h_bytes_per_step": alm_bytes + map_bytes}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

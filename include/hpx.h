@@ -157,6 +157,22 @@ size_t hpx_plan_device_bytes(hpx_plan plan);
 hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi,
                                double* z, double* sinth, int32_t* sigma);
 
+/* Stage timing.  While enabled, every transform on the plan records a pair of
+ * CUDA events on its stream around each stage: 0 ring analysis FFT, 1
+ * Legendre analysis, 2 Legendre synthesis, 3 ring synthesis FFT.
+ * hpx_plan_stage_times waits for the recorded events, adds their elapsed
+ * times (ms) and kernel launch counts into ms[4] and launches[4] (either may
+ * be NULL), and clears the record.  Measurement support, not part of the
+ * transform. */
+hpx_status hpx_plan_set_timing(hpx_plan plan, int enable);
+hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches);
+
+/* Work of the Legendre stage per channel: *total = number of (l, m, ring
+ * pair) triples, nalm * 2 nside; *active = triples from each chain's first
+ * significant l on (the recurrence steps the kernels execute per chain).
+ * Synchronous. */
+hpx_status hpx_plan_chain_stats(hpx_plan plan, int64_t* active, int64_t* total);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* hpx_last_error(void);
 

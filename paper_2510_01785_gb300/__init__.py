@@ -176,6 +176,28 @@ class Plan:
                                      ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_alm2map_host")
         return dst
 
+    # -- measurement support ------------------------------------------------
+    STAGES = ("ring_fft_analysis", "legendre_analysis", "legendre_synthesis", "ring_fft_synthesis")
+
+    def set_timing(self, enable: bool) -> None:
+        """Record CUDA events around each stage of every following transform."""
+        check(lib().hpx_plan_set_timing(self._h, 1 if enable else 0), "hpx_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, kernel launches)} since the last call; waits."""
+        ms = np.zeros(4, np.float64)
+        n = np.zeros(4, np.int64)
+        check(lib().hpx_plan_stage_times(self._h, ctypes.c_void_p(ms.ctypes.data),
+                                         ctypes.c_void_p(n.ctypes.data)), "hpx_plan_stage_times")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    def chain_stats(self) -> tuple[int, int]:
+        """(active, total) (l, m, ring pair) triples of the Legendre stage."""
+        a = ctypes.c_int64()
+        t = ctypes.c_int64()
+        check(lib().hpx_plan_chain_stats(self._h, ctypes.byref(a), ctypes.byref(t)), "hpx_plan_chain_stats")
+        return int(a.value), int(t.value)
+
     def ring_table(self) -> dict:
         R = 4 * self.nside - 1
         start = np.zeros(R, np.int64)

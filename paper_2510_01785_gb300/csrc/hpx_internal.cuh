@@ -72,6 +72,7 @@ struct hpx_plan_s {
   void* d_F;           // workspace [nbatch][nring][mmax+1] C2<T>
   void* d_io_map;      // device I/O buffers of the host-buffer entry points (lazy)
   void* d_io_alm;
+  void* timing;        // per-stage CUDA events while timing is enabled
   size_t bytes;
 };
 
@@ -96,9 +97,9 @@ cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s);
 template <typename T>
 cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s);
 template <typename T>
-cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_weight, cudaStream_t s);
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_weight, cudaStream_t s, int* nlaunch);
 template <typename T>
-cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s);
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch);
 
 // plan-time table builders (hpx_fft.cu, hpx_legendre.cu)
 template <typename T>

@@ -461,7 +461,7 @@ static void analysis_shape(int npair, int* nthr, int* csize) {
 }
 
 template <typename T, int CP>
-static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s) {
+static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
   using V = C2<T>;
   int nthr, csize;
   analysis_shape(p->npair, &nthr, &csize);
@@ -489,6 +489,7 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, c
                            (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
                            use_w ? 1 : 0);
     if (e != cudaSuccess) return e;
+    ++*nlaunch;
   }
   return cudaGetLastError();
 }
@@ -516,20 +517,20 @@ static int pick_cp(const hpx_plan_s* p) {
 }
 
 template <typename T>
-cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s) {
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
   switch (pick_cp<T>(p)) {
-    case 1: return launch_analysis_cp<T, 1>(p, alm, use_w, s);
-    case 2: return launch_analysis_cp<T, 2>(p, alm, use_w, s);
-    case 4: return launch_analysis_cp<T, 4>(p, alm, use_w, s);
-    case 8: return launch_analysis_cp<T, 8>(p, alm, use_w, s);
+    case 1: return launch_analysis_cp<T, 1>(p, alm, use_w, s, nlaunch);
+    case 2: return launch_analysis_cp<T, 2>(p, alm, use_w, s, nlaunch);
+    case 4: return launch_analysis_cp<T, 4>(p, alm, use_w, s, nlaunch);
+    case 8: return launch_analysis_cp<T, 8>(p, alm, use_w, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_analysis_cp<T, 16>(p, alm, use_w, s);
-      else return launch_analysis_cp<T, 8>(p, alm, use_w, s);
+      if constexpr (sizeof(T) == 4) return launch_analysis_cp<T, 16>(p, alm, use_w, s, nlaunch);
+      else return launch_analysis_cp<T, 8>(p, alm, use_w, s, nlaunch);
   }
 }
 
 template <typename T, int CP>
-static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaStream_t s) {
+static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
   using V = C2<T>;
   const int nthr = 128;
   dim3 grid((p->npair + nthr - 1) / nthr, p->mmax + 1);
@@ -540,23 +541,24 @@ static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaSt
         p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    ++*nlaunch;
   }
   return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s) {
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
   int cp = 1;
   const int cmax = sizeof(T) == 4 ? 16 : 8;
   while (cp < p->nbatch && cp < cmax) cp *= 2;
   switch (cp) {
-    case 1: return launch_synthesis_cp<T, 1>(p, alm, s);
-    case 2: return launch_synthesis_cp<T, 2>(p, alm, s);
-    case 4: return launch_synthesis_cp<T, 4>(p, alm, s);
-    case 8: return launch_synthesis_cp<T, 8>(p, alm, s);
+    case 1: return launch_synthesis_cp<T, 1>(p, alm, s, nlaunch);
+    case 2: return launch_synthesis_cp<T, 2>(p, alm, s, nlaunch);
+    case 4: return launch_synthesis_cp<T, 4>(p, alm, s, nlaunch);
+    case 8: return launch_synthesis_cp<T, 8>(p, alm, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_synthesis_cp<T, 16>(p, alm, s);
-      else return launch_synthesis_cp<T, 8>(p, alm, s);
+      if constexpr (sizeof(T) == 4) return launch_synthesis_cp<T, 16>(p, alm, s, nlaunch);
+      else return launch_synthesis_cp<T, 8>(p, alm, s, nlaunch);
   }
 }
 
@@ -569,9 +571,9 @@ cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, cudaStream_t);
-template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, cudaStream_t);
-template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, cudaStream_t);
-template cudaError_t launch_synthesis<double>(const hpx_plan_s*, const double*, cudaStream_t);
+template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, cudaStream_t, int*);
+template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, cudaStream_t, int*);
+template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, cudaStream_t, int*);
+template cudaError_t launch_synthesis<double>(const hpx_plan_s*, const double*, cudaStream_t, int*);
 
 }  // namespace hpx

@@ -104,12 +104,31 @@ struct DeviceGuard {
   }
 };
 
+// Optional per-stage CUDA events (hpx_plan_set_timing).
+struct TimingRec {
+  int stage;
+  cudaEvent_t a, b;
+  int n;
+};
+struct TimingState {
+  bool on = false;
+  std::vector<TimingRec> recs;
+};
+
 static void plan_free(hpx_plan_s* p) {
   if (!p) return;
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p->timing) {
+    TimingState* ts = static_cast<TimingState*>(p->timing);
+    for (auto& r : ts->recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    delete ts;
+  }
   delete p;
 }
 
@@ -133,17 +152,42 @@ static hpx_status check_call(const hpx_plan_s* p, const void* in, const void* ou
 
 size_t real_size(const hpx_plan_s* p) { return p->dtype == HPX_F64 ? sizeof(double) : sizeof(float); }
 
+template <class F>
+static cudaError_t staged(hpx_plan_s* p, int stage, cudaStream_t s, F&& f) {
+  TimingState* ts = static_cast<TimingState*>(p->timing);
+  int n = 0;
+  if (!ts || !ts->on) return f(&n);
+  TimingRec r{stage, nullptr, nullptr, 0};
+  cudaError_t e = cudaEventCreate(&r.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&r.b);
+  if (e == cudaSuccess) e = cudaEventRecord(r.a, s);
+  if (e != cudaSuccess) return e;
+  e = f(&r.n);
+  cudaError_t e2 = cudaEventRecord(r.b, s);
+  ts->recs.push_back(r);
+  return e != cudaSuccess ? e : e2;
+}
+
 template <typename T>
-static cudaError_t run_analysis(const hpx_plan_s* p, const void* map, void* alm, bool weighted, cudaStream_t s) {
-  cudaError_t e = launch_r2c<T>(p, static_cast<const T*>(map), s);
-  if (e == cudaSuccess) e = launch_analysis<T>(p, static_cast<T*>(alm), weighted, s);
+static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool weighted, cudaStream_t s) {
+  cudaError_t e = staged(p, 0, s, [&](int* n) {
+    *n = 1;
+    return launch_r2c<T>(p, static_cast<const T*>(map), s);
+  });
+  if (e == cudaSuccess)
+    e = staged(p, 1, s, [&](int* n) { return launch_analysis<T>(p, static_cast<T*>(alm), weighted, s, n); });
   return e;
 }
 
 template <typename T>
-static cudaError_t run_synthesis(const hpx_plan_s* p, const void* alm, void* map, bool weighted, cudaStream_t s) {
-  cudaError_t e = launch_synthesis<T>(p, static_cast<const T*>(alm), s);
-  if (e == cudaSuccess) e = launch_c2r<T>(p, static_cast<T*>(map), weighted, s);
+static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, cudaStream_t s) {
+  cudaError_t e =
+      staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), s, n); });
+  if (e == cudaSuccess)
+    e = staged(p, 3, s, [&](int* n) {
+      *n = 1;
+      return launch_c2r<T>(p, static_cast<T*>(map), weighted, s);
+    });
   return e;
 }
 
@@ -372,6 +416,62 @@ hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi, dou
     sinth[y] = h[y].sinth;
     sigma[y] = h[y].sigma;
   }
+  return HPX_OK;
+}
+
+hpx_status hpx_plan_set_timing(hpx_plan plan, int enable) {
+  if (!plan) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  if (!plan->timing) plan->timing = new TimingState();
+  static_cast<TimingState*>(plan->timing)->on = enable != 0;
+  return HPX_OK;
+}
+
+hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches) {
+  if (!plan) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+  if (launches)
+    for (int k = 0; k < 4; ++k) launches[k] = 0;
+  TimingState* ts = static_cast<TimingState*>(plan->timing);
+  if (!ts) return HPX_OK;
+  DeviceGuard g(plan->device);
+  cudaError_t first = cudaSuccess;
+  for (auto& r : ts->recs) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+    if (ms) ms[r.stage] += t;
+    if (launches) launches[r.stage] += r.n;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ts->recs.clear();
+  if (first != cudaSuccess) return cuda_fail(first, "hpx_plan_stage_times");
+  return HPX_OK;
+}
+
+hpx_status hpx_plan_chain_stats(hpx_plan plan, int64_t* active, int64_t* total) {
+  if (!plan || !active || !total) {
+    set_error("null argument");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(plan->device);
+  const size_t nchain = (size_t)(plan->mmax + 1) * plan->npair;
+  std::vector<int> lc(nchain);
+  cudaError_t e = cudaMemcpy(lc.data(), plan->d_lc, sizeof(int) * nchain, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "chain table copy");
+  long long a = 0;
+  for (size_t c = 0; c < nchain; ++c)
+    if (lc[c] <= plan->lmax) a += plan->lmax + 1 - lc[c];
+  *active = a;
+  *total = plan->nalm * (long long)plan->npair;
   return HPX_OK;
 }
 
