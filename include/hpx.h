@@ -148,6 +148,25 @@ hpx_status hpx_map2alm_host(hpx_plan plan, const void* host_map,
 hpx_status hpx_alm2map_host(hpx_plan plan, const void* host_alm,
                             void* host_map, hpx_stream_t stream);
 
+/* a = Y^dagger W p, like hpx_map2alm, for callers that must not allocate
+ * device memory when they transform (their device memory is owned by another
+ * allocator or pool, or their loop cannot risk the device-wide
+ * synchronisation that cudaMalloc / cudaFree may cause).  The paper has no
+ * counterpart: this is a deployment variant of the same kernels.
+ *   The intermediate ring spectra live in one fixed 16 MiB device array
+ *   compiled into the library (held on every GPU that loads it until the
+ *   process exits) instead of the plan's workspace; the call allocates
+ *   nothing.  Plans needing more than 16 MiB of spectra (nbatch *
+ *   (6 nside^2 + 4 nside - 1) complex values) get HPX_ERR_INVALID.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the array: calls whose work overlaps on the GPU race and
+ *   must be ordered by the caller.  Nothing in it needs to start at zero.
+ *   map : device input [nbatch][npix]; alm : device output [nbatch][nalm]. */
+hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* alm,
+                               hpx_stream_t stream);
+
 /* Device bytes held by the plan (tables + workspace), for admission control. */
 size_t hpx_plan_device_bytes(hpx_plan plan);
 
