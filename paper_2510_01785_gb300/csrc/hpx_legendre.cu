@@ -174,21 +174,39 @@ template <> struct LaneTile<32> { static constexpr int CPL = 8, LPL = 4; };
 
 template <typename T> struct MuStride { static constexpr int v = LB + 16 / (int)sizeof(T); };
 
+// A recurrence value in the contraction's type.  The float case avoids the
+// double-to-float conversion instruction, which on this GPU issues to the same
+// scarce FP64 pipe as the recurrence: sign, exponent and top 24 significand
+// bits are moved with integer operations (rounded half up in magnitude), and
+// |x| < 2^-126 becomes 0.  |x| here is far below 2^128.
+template <typename T> __device__ __forceinline__ T to_real(double x);
+template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_real<float>(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = __funnelshift_l(lo, ahi, 3) + 0x40000000u + ((lo >> 28) & 1u);
+  f = (ahi < (897u << 20)) ? 0u : (f | (hi & 0x80000000u));
+  return __uint_as_float(f);
+}
+
 template <typename T, int CP>
 size_t analysis_smem(int nthr) {
   constexpr int C2N = 2 * CP;
   const int nwarp = nthr / 32;
   return sizeof(T) * ((size_t)nthr * 2 * C2N + (size_t)nthr * MuStride<T>::v +
                       (size_t)nwarp * LB * C2N + 2 * LB * C2N) +
-         sizeof(double) * LB;
+         sizeof(double) * 2 * LB;
 }
 
-// One cluster per m; CTA r of the cluster owns ring pairs [r nthr, (r+1) nthr),
-// one recurrence chain per thread.  Per block of LB l values: the chains
-// write mu into shared memory, each warp contracts its 32 chains with their
-// S/A ring coefficients, the warps' partial sums are added in shared memory,
-// and the cluster adds the CTAs' partials through distributed shared memory
-// (double-buffered, one cluster barrier per block).  Deterministic order.
+// One cluster per m, one recurrence chain per thread.  Warps take 32
+// consecutive ring pairs (similar start l, so few idle lanes) and are dealt
+// round-robin over the cluster's CTAs, so every CTA holds polar and
+// equatorial chains alike and none idles at the cluster barrier.  Per block
+// of LB l values: the chains write mu into shared memory, each warp contracts
+// its 32 chains with their S/A ring coefficients, the warps' partial sums are
+// added in shared memory, and the cluster adds the CTAs' partials through
+// distributed shared memory (double-buffered, one cluster barrier per block).
+// Deterministic order.
 template <typename T, int CP>
 __global__ void __launch_bounds__(512)
 k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const RingInfo* __restrict__ rings,
@@ -205,7 +223,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   const int nthr = blockDim.x, nwarp = nthr >> 5;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int m = blockIdx.y;
-  const int p = crank * nthr + t;
+  const int p = (warp * csize + crank) * 32 + lane;
   const bool active = p < npair;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -213,7 +231,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   T* sMu = sG + (size_t)nthr * 2 * C2N;        // [nthr][MS]
   T* sW = sMu + (size_t)nthr * MS;             // [nwarp][LB][C2N]
   T* sC = sW + (size_t)nwarp * LB * C2N;       // [2][LB][C2N]
-  double* sCz = reinterpret_cast<double*>(sC + 2 * LB * C2N);  // [LB]
+  double* sCz = reinterpret_cast<double*>(sC + 2 * LB * C2N);  // [2][LB] c_l of this and the next block
 
   double z = 0.0, s0 = 0.0, s1 = 0.0;
   int lc = INT_MAX;
@@ -250,9 +268,10 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   const int l0 = lq * LPL, c0 = cq * CPL;
   double mu1 = 0.0, mu2 = 0.0;
   int buf = 0;
+  if (t < LB) sCz[t] = (m + t <= lmax) ? coef_c[base + m + t] : 0.0;
+  __syncthreads();
   for (int lb0 = m; lb0 <= lmax; lb0 += LB) {
-    if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
-    __syncthreads();
+    const double* cz = sCz + buf * LB;
     // --- recurrence: LB steps of mu_l = c_l z mu_{l-1} - mu_{l-2} ---
     T* myMu = sMu + (size_t)t * MS;
     if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
@@ -262,14 +281,14 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int l = lb0 + i4 + u;
-          double mu = fma(sCz[i4 + u] * z, mu1, -mu2);
+          double mu = fma(cz[i4 + u] * z, mu1, -mu2);
           if (l == lc) {
             mu = s1;
             mu1 = s0;
           }
           mu2 = mu1;
           mu1 = mu;
-          v[u] = (T)mu;
+          v[u] = to_real<T>(mu);
         }
         if constexpr (sizeof(T) == 4) {
           *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
@@ -323,6 +342,11 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
       }
     } else {
       for (int o = t; o < LB * C2N; o += nthr) cpart[o] = (T)0;
+    }
+    // c_l of the next block, into the other half of the double buffer
+    if (t < LB) {
+      const int l = lb0 + LB + t;
+      sCz[(buf ^ 1) * LB + t] = (l <= lmax) ? coef_c[base + l] : 0.0;
     }
     // --- cluster reduction; CTA r writes its share of the block ---
     cluster.sync();
@@ -403,31 +427,34 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
       }
       if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
       __syncthreads();
+      // a warp whose chains all start after this block has nothing to add
+      if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
 #pragma unroll 4
-      for (int i = 0; i < LB; i += 2) {
-        {
-          double mu = fma(sCz[i] * z, mu1, -mu2);
-          if (lb0 + i == lc) {
-            mu = s1;
-            mu1 = s0;
-          }
-          mu2 = mu1;
-          mu1 = mu;
-          const T mf = (T)mu;
+        for (int i = 0; i < LB; i += 2) {
+          {
+            double mu = fma(sCz[i] * z, mu1, -mu2);
+            if (lb0 + i == lc) {
+              mu = s1;
+              mu1 = s0;
+            }
+            mu2 = mu1;
+            mu1 = mu;
+            const T mf = to_real<T>(mu);
 #pragma unroll
-          for (int c = 0; c < C2N; ++c) accE[c] = fma(mf, sA[i][c], accE[c]);
-        }
-        {
-          double mu = fma(sCz[i + 1] * z, mu1, -mu2);
-          if (lb0 + i + 1 == lc) {
-            mu = s1;
-            mu1 = s0;
+            for (int c = 0; c < C2N; ++c) accE[c] = fma(mf, sA[i][c], accE[c]);
           }
-          mu2 = mu1;
-          mu1 = mu;
-          const T mf = (T)mu;
+          {
+            double mu = fma(sCz[i + 1] * z, mu1, -mu2);
+            if (lb0 + i + 1 == lc) {
+              mu = s1;
+              mu1 = s0;
+            }
+            mu2 = mu1;
+            mu1 = mu;
+            const T mf = to_real<T>(mu);
 #pragma unroll
-          for (int c = 0; c < C2N; ++c) accO[c] = fma(mf, sA[i + 1][c], accO[c]);
+            for (int c = 0; c < C2N; ++c) accO[c] = fma(mf, sA[i + 1][c], accO[c]);
+          }
         }
       }
       __syncthreads();
