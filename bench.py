@@ -42,6 +42,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def _hbm_peak():
+    """Measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,73 +268,30 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     dist = dist_init("nccl")
 
-    plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", device=dev)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local
+
+    # recomputing plan first (also synthesises the band-limited inputs)
+    plan_r = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", device=dev)
     alm_np = syn.gaussian_alm(SEED + 1, LMAX, MMAX, NBATCH, power=2.0).astype(np.complex64)
     alm_in = torch.from_numpy(alm_np).to(dev)
-    maps = plan.alm2map(alm_in)  # first half band-limited, second half white noise
+    maps = plan_r.alm2map(alm_in)  # first half band-limited, second half white noise
     nbl = NBATCH // 2
     maps[nbl:] = torch.from_numpy(syn.white_maps(SEED, NSIDE, NBATCH - nbl).astype(np.float32)).to(dev)
-    alm_out = plan.empty_alm()
-    map_out = plan.empty_map()
-    stream = torch.cuda.current_stream(dev)
+    rec = timed_steps(plan_r, maps, alm_in, args, dist, dev, world, gpu_index)
+    rec["roofline"] = legendre_roofline(plan_r, rec["stages"], table=False)
+    active, total = plan_r.chain_stats()
+    plan_r.close()
 
-    def step():
-        plan.map2alm(maps, out=alm_out)
-        plan.alm2map(alm_in, out=map_out)
-
-    for _ in range(args.warmup):
-        step()
+    # plan-resident lambda table (built by the same FP64 recurrence at plan time)
+    t0 = time.perf_counter()
+    plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
     torch.cuda.synchronize(dev)
-    plan.stage_times()  # clear
-
-    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
-    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
-    plan.set_timing(True)
-    barrier(dist, dev)
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    barrier(dist, dev)
-    t_ms = e0.elapsed_time(e1)
-    plan.set_timing(False)
-    stages = plan.stage_times()
-    t_max = reduce_max(dist, t_ms, dev)
-    value = throughput(world, args.steps, t_max)
-
-    # the dominant kernel's roofline (FP64-pipe bound: the recurrence)
-    active, total = plan.chain_stats()
-    launches = sum(n for _, n in stages.values())
-    dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k][0])
-    ms_launch = stages[dom][0] / max(stages[dom][1], 1)
-    fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
-    achieved = fp64_flop / (ms_launch / 1e3) / 1e12
-    kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
-    traffic = kernel_traffic(kname)
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per launch "
-                        f"(of {total}; contributions below 2^-193 dropped)"}
-    stage_report = {}
-    for k, (ms, n) in stages.items():
-        stage_report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
-    map_bytes = 4 * NBATCH * 12 * NSIDE * NSIDE
-    alm_bytes = 8 * NBATCH * plan.nalm
-    spec_bytes = 8 * NBATCH * (6 * NSIDE * NSIDE + 4 * NSIDE - 1)
-    for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", map_bytes)):
-        s = stage_report[k]
-        s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
-    for k in ("legendre_analysis", "legendre_synthesis"):
-        s = stage_report[k]
-        s["fp64_tflops"] = fp64_flop / (s["ms_per_launch"] / 1e3) / 1e12
-        s["fp32_contraction_tflops"] = 4.0 * NBATCH * active / (s["ms_per_launch"] / 1e3) / 1e12
+    plan_s = time.perf_counter() - t0
+    tab = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
+    roofline = legendre_roofline(plan, tab["stages"], table=True)
+    t_max, value, stage_report, clk = tab["t_max"], tab["value"], tab["stages"], tab["clocks"]
+    launches = tab["launches"]
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
@@ -341,16 +310,106 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX,
                            "nbatch": NBATCH, "step": "map2alm + alm2map of the batch",
-                           "lambda": "FP64 recurrence recomputed in every transform",
+                           "lambda": "plan-resident table generated once by the FP64 recurrence "
+                                     "(bit-identical results to recomputing it per transform)",
                            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk,
+                "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan.device_bytes,
+                         "significant_triples": active, "all_triples": total},
+                "lambda_recompute": {"value": rec["value"], "ms_per_step": rec["t_max"] / args.steps,
+                                     "roofline": rec["roofline"], "stages": rec["stages"],
+                                     "clocks": rec["clocks"]}}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist.is_available() and dist.is_initialized():
         dist.destroy_process_group()
     return 0
+
+
+def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
+    """W warm-up steps, then K steps between CUDA events on the launch stream
+    (barrier + synchronize on both sides), with the library's per-stage events
+    and nvidia-smi clock samples over the same region."""
+    import torch
+    alm_out = plan.empty_alm()
+    map_out = plan.empty_map()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.map2alm(maps, out=alm_out)
+        plan.alm2map(alm_in, out=map_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.stage_times()  # clear
+    clocks = ClockSampler(gpu_index)
+    plan.set_timing(True)
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(dist, dev)
+    t_ms = e0.elapsed_time(e1)
+    plan.set_timing(False)
+    stages = plan.stage_times()
+    t_max = reduce_max(dist, t_ms, dev)
+    report = {}
+    for k, (ms, n) in stages.items():
+        report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
+    return {"t_max": t_max, "value": throughput(world, args.steps, t_max), "stages": report,
+            "clocks": clk, "launches": sum(n for _, n in stages.values())}
+
+
+def legendre_roofline(plan, stages, table: bool):
+    """Roofline of the slower Legendre kernel, with per-stage figures added
+    to `stages` in place.  Recomputing: FP64 pipe (3 flop per significant
+    (l, m, ring-pair) triple).  Table: HBM (the table's bytes plus the
+    kernel's compulsory inputs and outputs)."""
+    active, total = plan.chain_stats()
+    map_bytes = 4 * NBATCH * 12 * NSIDE * NSIDE
+    alm_bytes = 8 * NBATCH * plan.nalm
+    spec_bytes = 8 * NBATCH * (6 * NSIDE * NSIDE + 4 * NSIDE - 1)
+    f_bytes = 8 * NBATCH * (4 * NSIDE - 1) * (MMAX + 1)
+    tab_bytes = plan.table_bytes if table else 0
+    for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes)):
+        s = stages[k]
+        s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
+    fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
+    leg_bytes = {"legendre_analysis": tab_bytes + spec_bytes + alm_bytes,
+                 "legendre_synthesis": tab_bytes + alm_bytes + f_bytes}
+    for k in ("legendre_analysis", "legendre_synthesis"):
+        s = stages[k]
+        sec = s["ms_per_launch"] / 1e3
+        s["fp32_contraction_tflops"] = 4.0 * NBATCH * active / sec / 1e12
+        if table:
+            s["hbm_gbs_algorithmic"] = leg_bytes[k] / sec / 1e9
+        else:
+            s["fp64_tflops"] = fp64_flop / sec / 1e12
+    dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k]["ms_per_launch"])
+    kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
+    if table:
+        achieved = stages[dom]["hbm_gbs_algorithmic"]
+        return {"bound": "hbm", "kernel": kname + "<table>", "achieved": achieved, "peak": HBM_PEAK_GBS,
+                "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": kernel_traffic(kname + "<table>"),
+                "peak_source": HBM_PEAK_SOURCE,
+                "work": f"lambda table {tab_bytes} B + compulsory inputs/outputs {leg_bytes[dom] - tab_bytes} B "
+                        f"per launch"}
+    achieved = stages[dom]["fp64_tflops"]
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(kname),
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+            "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per launch "
+                    f"(of {total}; contributions below 2^-193 dropped)"}
 
 
 def measure_e2e(plan, maps, alm_in, dist, dev, steps, world):

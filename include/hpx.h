@@ -86,7 +86,12 @@ typedef enum {
 #define HPX_PLAN_LAMBDA_TABLE 1u     /* lambda_lm generated once at plan time
                                         by the same FP64 recurrence and kept
                                         in device memory (the precomputed
-                                        Legendre tensor of Sec. III-D/III-G) */
+                                        Legendre tensor of Sec. III-D/III-G);
+                                        results are identical to the
+                                        recomputing plan.  Costs one value of
+                                        the real type per significant
+                                        (l, m, ring pair), about 30 GB in
+                                        float at nside 1024, lmax 3071. */
 
 /* Number of packed coefficients for (lmax, mmax). */
 int64_t hpx_nalm(int lmax, int mmax);
@@ -191,6 +196,9 @@ hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches);
  * significant l on (the recurrence steps the kernels execute per chain).
  * Synchronous. */
 hpx_status hpx_plan_chain_stats(hpx_plan plan, int64_t* active, int64_t* total);
+
+/* Bytes of the plan-resident lambda table (0 without HPX_PLAN_LAMBDA_TABLE). */
+size_t hpx_plan_table_bytes(hpx_plan plan);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* hpx_last_error(void);

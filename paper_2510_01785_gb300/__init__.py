@@ -98,6 +98,11 @@ class Plan:
     def device_bytes(self) -> int:
         return int(lib().hpx_plan_device_bytes(self._h))
 
+    @property
+    def table_bytes(self) -> int:
+        """Bytes of the plan-resident lambda table (0 when recomputing)."""
+        return int(lib().hpx_plan_table_bytes(self._h))
+
     # -- argument checks ----------------------------------------------------
     def _map(self, t: torch.Tensor, name: str) -> torch.Tensor:
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device):

@@ -37,6 +37,7 @@ SIGNATURES = {
     "hpx_plan_set_timing": (_I, [_P, _I]),
     "hpx_plan_stage_times": (_I, [_P, _P, _P]),
     "hpx_plan_chain_stats": (_I, [_P, _P, _P]),
+    "hpx_plan_table_bytes": (_SZ, [_P]),
     "hpx_last_error": (ctypes.c_char_p, []),
 }
 

@@ -73,6 +73,11 @@ struct hpx_plan_s {
   void* d_io_map;      // device I/O buffers of the host-buffer entry points (lazy)
   void* d_io_alm;
   void* timing;        // per-stage CUDA events while timing is enabled
+  void* d_tab;         // plan-resident lambda table (HPX_PLAN_LAMBDA_TABLE), C2<T>'s real type
+  long long* d_tab_off;  // [mmax+1][ngroup] first element of each (m, 32-pair group)
+  int* d_tab_lstart;   // [mmax+1][ngroup] first l stored for the group
+  int ngroup;
+  long long tab_elems;
   size_t bytes;
 };
 
@@ -105,5 +110,7 @@ cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, 
 template <typename T>
 cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s);
 cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s);
+template <typename T>
+cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 
 }  // namespace hpx

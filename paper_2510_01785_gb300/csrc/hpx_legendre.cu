@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <vector>
 
 #include "hpx_internal.cuh"
 
@@ -198,22 +199,36 @@ size_t analysis_smem(int nthr) {
          sizeof(double) * 2 * LB;
 }
 
+// The plan-resident lambda table (HPX_PLAN_LAMBDA_TABLE): for every m and
+// every group g of 32 consecutive ring pairs, rows l = lstart(m,g)..lmax of 32
+// values mu_l (one per pair of the group), lstart = the group's earliest chain
+// start; row r of (m, g) at tab[off(m,g) + 32 r].  Written once at plan time
+// by the same FP64 recurrence and conversion as the recomputing kernels.
+template <typename T> struct LamTab {
+  const T* tab;
+  const long long* off;
+  const int* lstart;
+  int ngroup;
+};
+
 // One cluster per m, one recurrence chain per thread.  Warps take 32
 // consecutive ring pairs (similar start l, so few idle lanes) and are dealt
 // round-robin over the cluster's CTAs, so every CTA holds polar and
 // equatorial chains alike and none idles at the cluster barrier.  Per block
-// of LB l values: the chains write mu into shared memory, each warp contracts
-// its 32 chains with their S/A ring coefficients, the warps' partial sums are
-// added in shared memory, and the cluster adds the CTAs' partials through
+// of LB l values: the chains write mu into shared memory (from the recurrence,
+// or streamed from the lambda table when TAB), each warp contracts its 32
+// chains with their S/A ring coefficients, the warps' partial sums are added
+// in shared memory, and the cluster adds the CTAs' partials through
 // distributed shared memory (double-buffered, one cluster barrier per block).
 // Deterministic order.
-template <typename T, int CP>
+template <typename T, int CP, bool TAB>
 __global__ void __launch_bounds__(512)
 k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const RingInfo* __restrict__ rings,
                     const C2<T>* __restrict__ etab, const double* __restrict__ coef_c,
                     const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                     const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
-                    int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w) {
+                    int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w,
+                    const LamTab<T> tb) {
   using V = C2<T>;
   constexpr int C2N = 2 * CP;
   constexpr int CPL = LaneTile<C2N>::CPL, LPL = LaneTile<C2N>::LPL, NCQ = C2N / CPL;
@@ -275,20 +290,34 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
     // --- recurrence: LB steps of mu_l = c_l z mu_{l-1} - mu_{l-2} ---
     T* myMu = sMu + (size_t)t * MS;
     if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
+      // table rows of this warp's group (TAB): 32 coalesced 128-byte rows
+      int ls = INT_MAX;
+      const T* tg = nullptr;
+      if constexpr (TAB) {
+        const int g = warp * csize + crank;
+        if (g < tb.ngroup) {
+          ls = tb.lstart[(long long)m * tb.ngroup + g];
+          tg = tb.tab + tb.off[(long long)m * tb.ngroup + g] + lane;
+        }
+      }
 #pragma unroll
       for (int i4 = 0; i4 < LB; i4 += 4) {
         T v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int l = lb0 + i4 + u;
-          double mu = fma(cz[i4 + u] * z, mu1, -mu2);
-          if (l == lc) {
-            mu = s1;
-            mu1 = s0;
+          if constexpr (TAB) {
+            v[u] = (l >= ls && l <= lmax) ? __ldcs(tg + (long long)(l - ls) * 32) : (T)0;
+          } else {
+            double mu = fma(cz[i4 + u] * z, mu1, -mu2);
+            if (l == lc) {
+              mu = s1;
+              mu1 = s0;
+            }
+            mu2 = mu1;
+            mu1 = mu;
+            v[u] = to_real<T>(mu);
           }
-          mu2 = mu1;
-          mu1 = mu;
-          v[u] = to_real<T>(mu);
         }
         if constexpr (sizeof(T) == 4) {
           *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
@@ -376,14 +405,14 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
 // O_m = sum over odd l - m; F_m(y) = E + O on the northern ring and
 // F_m(y') = E - O on its mirror (Eq. 24 before the ring transform).  The
 // block's coefficients (pre-multiplied by P_l) are broadcast from shared
-// memory.
-template <typename T, int CP>
+// memory; mu comes from the recurrence, or from the lambda table when TAB.
+template <typename T, int CP, bool TAB>
 __global__ void __launch_bounds__(128)
 k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const RingInfo* __restrict__ rings,
                      const double* __restrict__ coef_c, const float* __restrict__ coef_pf,
                      const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                      const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
-                     int mmax, int npair, int nring, long long nalm, int b0, int nb) {
+                     int mmax, int npair, int nring, long long nalm, int b0, int nb, const LamTab<T> tb) {
   using V = C2<T>;
   constexpr int C2N = 2 * CP;
   __shared__ __align__(16) T sA[LB][C2N];
@@ -428,7 +457,28 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
       if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
       __syncthreads();
       // a warp whose chains all start after this block has nothing to add
-      if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
+      if (TAB && __any_sync(0xffffffffu, lc < lb0 + LB)) {
+        const int g = p >> 5;
+        const bool gok = g < tb.ngroup;
+        const int ls = gok ? tb.lstart[(long long)m * tb.ngroup + g] : INT_MAX;
+        const T* tg = tb.tab + (gok ? tb.off[(long long)m * tb.ngroup + g] : 0) + (p & 31);
+#pragma unroll
+        for (int h = 0; h < LB; h += 16) {
+          T mv[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int l = lb0 + h + i;
+            mv[i] = (l >= ls && l <= lmax) ? __ldcs(tg + (long long)(l - ls) * 32) : (T)0;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+#pragma unroll
+            for (int c = 0; c < C2N; ++c) accE[c] = fma(mv[i], sA[h + i][c], accE[c]);
+#pragma unroll
+            for (int c = 0; c < C2N; ++c) accO[c] = fma(mv[i + 1], sA[h + i + 1][c], accO[c]);
+          }
+        }
+      } else if (!TAB && __any_sync(0xffffffffu, lc < lb0 + LB)) {
 #pragma unroll 4
         for (int i = 0; i < LB; i += 2) {
           {
@@ -487,13 +537,23 @@ static void analysis_shape(int npair, int* nthr, int* csize) {
   }
 }
 
-template <typename T, int CP>
+template <typename T>
+static LamTab<T> lam_tab(const hpx_plan_s* p) {
+  LamTab<T> tb;
+  tb.tab = static_cast<const T*>(p->d_tab);
+  tb.off = p->d_tab_off;
+  tb.lstart = p->d_tab_lstart;
+  tb.ngroup = p->ngroup;
+  return tb;
+}
+
+template <typename T, int CP, bool TAB>
 static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
   using V = C2<T>;
   int nthr, csize;
   analysis_shape(p->npair, &nthr, &csize);
   const size_t smem = analysis_smem<T, CP>(nthr);
-  cudaError_t e = cudaFuncSetAttribute(k_legendre_analysis<T, CP>,
+  cudaError_t e = cudaFuncSetAttribute(k_legendre_analysis<T, CP, TAB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -510,15 +570,21 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, c
   cfg.numAttrs = 1;
   for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
-    e = cudaLaunchKernelEx(&cfg, k_legendre_analysis<T, CP>, (const V*)p->d_spec, alm,
+    e = cudaLaunchKernelEx(&cfg, k_legendre_analysis<T, CP, TAB>, (const V*)p->d_spec, alm,
                            (const RingInfo*)p->d_ring, (const V*)p->d_etab, (const double*)p->d_coef_c,
                            (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
                            (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
-                           use_w ? 1 : 0);
+                           use_w ? 1 : 0, lam_tab<T>(p));
     if (e != cudaSuccess) return e;
     ++*nlaunch;
   }
   return cudaGetLastError();
+}
+
+template <typename T, int CP>
+static cudaError_t launch_analysis_sel(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
+  return p->d_tab ? launch_analysis_cp<T, CP, true>(p, alm, use_w, s, nlaunch)
+                  : launch_analysis_cp<T, CP, false>(p, alm, use_w, s, nlaunch);
 }
 
 template <typename T>
@@ -546,31 +612,37 @@ static int pick_cp(const hpx_plan_s* p) {
 template <typename T>
 cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
   switch (pick_cp<T>(p)) {
-    case 1: return launch_analysis_cp<T, 1>(p, alm, use_w, s, nlaunch);
-    case 2: return launch_analysis_cp<T, 2>(p, alm, use_w, s, nlaunch);
-    case 4: return launch_analysis_cp<T, 4>(p, alm, use_w, s, nlaunch);
-    case 8: return launch_analysis_cp<T, 8>(p, alm, use_w, s, nlaunch);
+    case 1: return launch_analysis_sel<T, 1>(p, alm, use_w, s, nlaunch);
+    case 2: return launch_analysis_sel<T, 2>(p, alm, use_w, s, nlaunch);
+    case 4: return launch_analysis_sel<T, 4>(p, alm, use_w, s, nlaunch);
+    case 8: return launch_analysis_sel<T, 8>(p, alm, use_w, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_analysis_cp<T, 16>(p, alm, use_w, s, nlaunch);
-      else return launch_analysis_cp<T, 8>(p, alm, use_w, s, nlaunch);
+      if constexpr (sizeof(T) == 4) return launch_analysis_sel<T, 16>(p, alm, use_w, s, nlaunch);
+      else return launch_analysis_sel<T, 8>(p, alm, use_w, s, nlaunch);
   }
 }
 
-template <typename T, int CP>
+template <typename T, int CP, bool TAB>
 static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
   using V = C2<T>;
   const int nthr = 128;
   dim3 grid((p->npair + nthr - 1) / nthr, p->mmax + 1);
   for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
-    k_legendre_synthesis<T, CP><<<grid, nthr, 0, s>>>(
+    k_legendre_synthesis<T, CP, TAB><<<grid, nthr, 0, s>>>(
         alm, (V*)p->d_F, p->d_ring, p->d_coef_c, p->d_coef_pf, p->d_coef_p, p->d_lc, p->d_mu0, p->d_mu1,
-        p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb);
+        p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb, lam_tab<T>(p));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*nlaunch;
   }
   return cudaSuccess;
+}
+
+template <typename T, int CP>
+static cudaError_t launch_synthesis_sel(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
+  return p->d_tab ? launch_synthesis_cp<T, CP, true>(p, alm, s, nlaunch)
+                  : launch_synthesis_cp<T, CP, false>(p, alm, s, nlaunch);
 }
 
 template <typename T>
@@ -579,13 +651,13 @@ cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, 
   const int cmax = sizeof(T) == 4 ? 16 : 8;
   while (cp < p->nbatch && cp < cmax) cp *= 2;
   switch (cp) {
-    case 1: return launch_synthesis_cp<T, 1>(p, alm, s, nlaunch);
-    case 2: return launch_synthesis_cp<T, 2>(p, alm, s, nlaunch);
-    case 4: return launch_synthesis_cp<T, 4>(p, alm, s, nlaunch);
-    case 8: return launch_synthesis_cp<T, 8>(p, alm, s, nlaunch);
+    case 1: return launch_synthesis_sel<T, 1>(p, alm, s, nlaunch);
+    case 2: return launch_synthesis_sel<T, 2>(p, alm, s, nlaunch);
+    case 4: return launch_synthesis_sel<T, 4>(p, alm, s, nlaunch);
+    case 8: return launch_synthesis_sel<T, 8>(p, alm, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_synthesis_cp<T, 16>(p, alm, s, nlaunch);
-      else return launch_synthesis_cp<T, 8>(p, alm, s, nlaunch);
+      if constexpr (sizeof(T) == 4) return launch_synthesis_sel<T, 16>(p, alm, s, nlaunch);
+      else return launch_synthesis_sel<T, 8>(p, alm, s, nlaunch);
   }
 }
 
@@ -598,6 +670,99 @@ cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// plan-resident lambda table
+// ---------------------------------------------------------------------------
+// Earliest chain start of each (m, 32-pair group) and its number of rows.
+__global__ void k_table_groups(const int* __restrict__ lc_tab, int lmax, int npair, int ngroup, int* lstart,
+                               long long* rows) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (g >= ngroup) return;
+  int ls = lmax + 1;
+  for (int j = 0; j < 32; ++j) {
+    const int p = g * 32 + j;
+    if (p < npair) ls = min(ls, lc_tab[(long long)m * npair + p]);
+  }
+  lstart[(long long)m * ngroup + g] = ls;
+  rows[(long long)m * ngroup + g] = lmax + 1 - ls;
+}
+
+// Rows of every group: the recurrence of the per-transform kernels (same
+// operations, same conversion), zero before a chain's start and for the
+// padding lanes of a group.
+template <typename T>
+__global__ void k_table_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
+                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
+                             const long long* __restrict__ off, int lmax, int npair, int ngroup, T* tab) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  const int g = p >> 5;
+  if (g >= ngroup) return;
+  const int ls = lstart[(long long)m * ngroup + g];
+  T* out = tab + off[(long long)m * ngroup + g] + (p & 31);
+  if (p >= npair) {
+    for (int l = ls; l <= lmax; ++l) out[(long long)(l - ls) * 32] = (T)0;
+    return;
+  }
+  const double z = rings[p].z;
+  const long long ci = (long long)m * npair + p;
+  const int lc = lc_tab[ci];
+  const double s0 = mu0_tab[ci], s1 = mu1_tab[ci];
+  const long long base = alm_base(lmax, m);
+  double mu1 = 0.0, mu2 = 0.0;
+  for (int l = ls; l <= lmax; ++l) {
+    double mu = fma(coef_c[base + l] * z, mu1, -mu2);
+    if (l == lc) {
+      mu = s1;
+      mu1 = s0;
+    }
+    mu2 = mu1;
+    mu1 = mu;
+    out[(long long)(l - ls) * 32] = to_real<T>(mu);
+  }
+}
+
+template <typename T>
+cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s) {
+  const int ng = (p->npair + 31) / 32;
+  p->ngroup = ng;
+  const long long nent = (long long)(p->mmax + 1) * ng;
+  cudaError_t e = cudaMalloc((void**)&p->d_tab_lstart, sizeof(int) * nent);
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(int) * nent;
+  e = cudaMalloc((void**)&p->d_tab_off, sizeof(long long) * nent);
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(long long) * nent;
+  k_table_groups<<<dim3((ng + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, ng,
+                                                                      p->d_tab_lstart, p->d_tab_off);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  std::vector<long long> rows(nent);
+  e = cudaMemcpy(rows.data(), p->d_tab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  long long acc = 0;
+  for (long long i = 0; i < nent; ++i) {
+    const long long r = rows[i];
+    rows[i] = acc;
+    acc += 32 * r;
+  }
+  p->tab_elems = acc;
+  e = cudaMemcpy(p->d_tab_off, rows.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&p->d_tab, sizeof(T) * (acc > 0 ? acc : 1));
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(T) * (acc > 0 ? acc : 1);
+  k_table_fill<T><<<dim3((ng * 32 + 127) / 128, p->mmax + 1), 128, 0, s>>>(
+      p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
+      ng, static_cast<T*>(p->d_tab));
+  return cudaGetLastError();
+}
+
+template cudaError_t build_lambda_table<float>(hpx_plan_s*, cudaStream_t);
+template cudaError_t build_lambda_table<double>(hpx_plan_s*, cudaStream_t);
 template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, cudaStream_t, int*);
 template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, cudaStream_t, int*);
 template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, cudaStream_t, int*);

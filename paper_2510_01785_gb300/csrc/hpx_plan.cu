@@ -118,7 +118,8 @@ struct TimingState {
 static void plan_free(hpx_plan_s* p) {
   if (!p) return;
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
-                  p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm};
+                  p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
+                  p->d_tab, p->d_tab_off, p->d_tab_lstart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->timing) {
@@ -248,10 +249,6 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("unknown plan flags 0x%x", flags);
     return HPX_ERR_INVALID;
   }
-  if (flags & HPX_PLAN_LAMBDA_TABLE) {
-    set_error("HPX_PLAN_LAMBDA_TABLE is not provided by this build");
-    return HPX_ERR_UNSUPPORTED;
-  }
   hpx_plan_s* p = new hpx_plan_s();
   std::memset(p, 0, sizeof(*p));
   cudaGetDevice(&p->device);
@@ -315,6 +312,8 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
   k_ring_geometry<<<(p->nring + 127) / 128, 128, 0, s>>>(nside, p->d_ring);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
+  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE))
+    e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -340,6 +339,11 @@ hpx_status hpx_plan_destroy(hpx_plan plan) {
 }
 
 size_t hpx_plan_device_bytes(hpx_plan plan) { return plan ? plan->bytes : 0; }
+
+size_t hpx_plan_table_bytes(hpx_plan plan) {
+  if (!plan || !plan->d_tab) return 0;
+  return (size_t)plan->tab_elems * (plan->dtype == HPX_F64 ? sizeof(double) : sizeof(float));
+}
 
 hpx_status hpx_map2alm(hpx_plan plan, const void* map, void* alm, hpx_stream_t stream) {
   return transform(plan, map, alm, stream, true, true, "hpx_map2alm");

@@ -237,3 +237,33 @@ def test_bad_arguments_raise():
             p.alm2map(torch.zeros((2, p.nalm), device="cuda", dtype=torch.complex128))
     with pytest.raises(RuntimeError):
         h.Plan(12, 10, 10, 1, "f32")
+
+
+# --------------------------------------------------------------------------
+# plan-resident lambda table: same recurrence values, so identical results
+# --------------------------------------------------------------------------
+TABLE_CASES = [(1, 2, 2, 1), (2, 5, 5, 3), (8, 40, 30, 2), (16, 47, 20, 3), (64, 191, 191, 3),
+               (256, 400, 380, 1), (512, 1535, 1535, 2)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", TABLE_CASES, ids=[f"ns{c[0]}-l{c[1]}-m{c[2]}-b{c[3]}" for c in TABLE_CASES])
+def test_table_mode_equals_recompute(case, dtype):
+    nside, lmax, mmax, nb = case
+    maps = to_dev(syn.white_maps(31, nside, nb), dtype)
+    alm = to_dev(syn.gaussian_alm(32, lmax, mmax, nb, power=1.0), dtype)
+    h = hpx()
+    with h.Plan(nside, lmax, mmax, nb, dtype) as pr, h.Plan(nside, lmax, mmax, nb, dtype, lambda_table=True) as pt:
+        assert pt.device_bytes > pr.device_bytes
+        for op, x in (("map2alm", maps), ("alm2map", alm), ("map2alm_adjoint", alm), ("alm2map_adjoint", maps)):
+            a = getattr(pr, op)(x)
+            b = getattr(pt, op)(x)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b), op
+
+
+def test_cfg2_table_mode_equals_recompute(big):
+    h = hpx()
+    with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True) as pt:
+        assert torch.equal(pt.map2alm(big["dmaps"]), big["a"])
+        assert torch.equal(pt.alm2map(big["dalm"]), big["s"])
