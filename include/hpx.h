@@ -143,6 +143,22 @@ hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map,
 hpx_status hpx_alm2map_adjoint(hpx_plan plan, const void* map, void* alm,
                                hpx_stream_t stream);
 
+/* Gradients for automatic differentiation (Sec. III-F, IV-C).  The
+ * coefficients are the real parameters (Re a_lm, Im a_lm) of a real field,
+ * and a coefficient gradient holds dL/dRe + i dL/dIm (PyTorch's convention
+ * for complex tensors).  With D = 1 for m = 0 and 2 for m >= 1:
+ *   hpx_alm2map_grad:  grad_alm = D Y^dagger grad_map   (backward of
+ *                      hpx_alm2map; Im of the m = 0 entries is 0, since the
+ *                      synthesis reads Re a_l0 only);
+ *   hpx_map2alm_grad:  grad_map = W Y D^-1 grad_alm     (backward of
+ *                      hpx_map2alm; reads Re of the m = 0 entries).
+ * lambda_lm is recomputed (or read from the plan's table), never stored by
+ * the forward call.  Same layouts and stream semantics as the transforms. */
+hpx_status hpx_alm2map_grad(hpx_plan plan, const void* grad_map, void* grad_alm,
+                            hpx_stream_t stream);
+hpx_status hpx_map2alm_grad(hpx_plan plan, const void* grad_alm, void* grad_map,
+                            hpx_stream_t stream);
+
 /* Host-buffer forms of the two transforms: copy the input from host memory
  * (pinned or pageable) into plan-owned device buffers, run the transform on
  * the stream, copy the result back and wait for the stream.  The device I/O

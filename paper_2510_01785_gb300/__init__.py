@@ -160,6 +160,18 @@ class Plan:
         dst = self._alm(out, "out") if out is not None else self.empty_alm()
         return self._call(lib().hpx_alm2map_adjoint, "hpx_alm2map_adjoint", src, dst, stream)
 
+    def alm2map_grad(self, grad_map: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Backward of alm2map: D Y^dagger g (dL/dRe + i dL/dIm per coefficient)."""
+        src = self._map(grad_map, "grad_map")
+        dst = self._alm(out, "out") if out is not None else self.empty_alm()
+        return self._call(lib().hpx_alm2map_grad, "hpx_alm2map_grad", src, dst, stream)
+
+    def map2alm_grad(self, grad_alm: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Backward of map2alm: W Y D^-1 g."""
+        src = self._alm(grad_alm, "grad_alm")
+        dst = self._map(out, "out") if out is not None else self.empty_map()
+        return self._call(lib().hpx_map2alm_grad, "hpx_map2alm_grad", src, dst, stream)
+
     # -- host-buffer forms --------------------------------------------------
     def map2alm_host(self, maps: np.ndarray | torch.Tensor, out=None, stream=None):
         """Host map in, host coefficients out (copies inside the call)."""

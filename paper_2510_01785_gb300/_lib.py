@@ -30,6 +30,8 @@ SIGNATURES = {
     "hpx_map2alm_adjoint": (_I, [_P, _P, _P, _P]),
     "hpx_alm2map_adjoint": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_noalloc": (_I, [_P, _P, _P, _P]),
+    "hpx_alm2map_grad": (_I, [_P, _P, _P, _P]),
+    "hpx_map2alm_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_host": (_I, [_P, _P, _P, _P]),
     "hpx_alm2map_host": (_I, [_P, _P, _P, _P]),
     "hpx_plan_device_bytes": (_SZ, [_P]),

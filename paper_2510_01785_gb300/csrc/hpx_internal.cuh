@@ -101,10 +101,13 @@ template <typename T>
 cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s);
 template <typename T>
 cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s);
+// mfac multiplies every coefficient with m > 0 on its way out (analysis) or
+// in (synthesis): 1 for the transforms, 2 and 1/2 for the gradients.
 template <typename T>
-cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_weight, cudaStream_t s, int* nlaunch);
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_weight, double mfac, cudaStream_t s,
+                            int* nlaunch);
 template <typename T>
-cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch);
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, double mfac, cudaStream_t s, int* nlaunch);
 
 // plan-time table builders (hpx_fft.cu, hpx_legendre.cu)
 template <typename T>

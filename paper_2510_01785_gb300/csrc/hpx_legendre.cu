@@ -228,7 +228,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
                     const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                     const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
                     int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w,
-                    const LamTab<T> tb) {
+                    const LamTab<T> tb, double mfac) {
   using V = C2<T>;
   constexpr int C2N = 2 * CP;
   constexpr int CPL = LaneTile<C2N>::CPL, LPL = LaneTile<C2N>::LPL, NCQ = C2N / CPL;
@@ -390,7 +390,8 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
         const int o = li * C2N + 2 * bb + part;
         T s = (T)0;
         for (int r = 0; r < csize; ++r) s += cluster.map_shared_rank(cpart, r)[o];
-        alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part] = (T)(coef_p[base + l] * (double)s);
+        alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part] =
+            (T)(coef_p[base + l] * (m > 0 ? mfac : 1.0) * (double)s);
       }
     }
     buf ^= 1;
@@ -412,7 +413,8 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
                      const double* __restrict__ coef_c, const float* __restrict__ coef_pf,
                      const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                      const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
-                     int mmax, int npair, int nring, long long nalm, int b0, int nb, const LamTab<T> tb) {
+                     int mmax, int npair, int nring, long long nalm, int b0, int nb, const LamTab<T> tb,
+                     double mfac) {
   using V = C2<T>;
   constexpr int C2N = 2 * CP;
   __shared__ __align__(16) T sA[LB][C2N];
@@ -449,8 +451,8 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
         T v = (T)0;
         if (l <= lmax && bb < nb && !(m == 0 && part == 1)) {
           const T a = alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part];
-          if constexpr (sizeof(T) == 4) v = coef_pf[base + l] * a;
-          else v = (T)(coef_p[base + l] * (double)a);
+          if constexpr (sizeof(T) == 4) v = coef_pf[base + l] * (m > 0 ? (float)mfac : 1.0f) * a;
+          else v = (T)(coef_p[base + l] * (m > 0 ? mfac : 1.0) * (double)a);
         }
         sA[li][c] = v;
       }
@@ -548,7 +550,8 @@ static LamTab<T> lam_tab(const hpx_plan_s* p) {
 }
 
 template <typename T, int CP, bool TAB>
-static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
+static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, double mfac, cudaStream_t s,
+                                      int* nlaunch) {
   using V = C2<T>;
   int nthr, csize;
   analysis_shape(p->npair, &nthr, &csize);
@@ -574,7 +577,7 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, c
                            (const RingInfo*)p->d_ring, (const V*)p->d_etab, (const double*)p->d_coef_c,
                            (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
                            (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
-                           use_w ? 1 : 0, lam_tab<T>(p));
+                           use_w ? 1 : 0, lam_tab<T>(p), mfac);
     if (e != cudaSuccess) return e;
     ++*nlaunch;
   }
@@ -582,9 +585,10 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, c
 }
 
 template <typename T, int CP>
-static cudaError_t launch_analysis_sel(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
-  return p->d_tab ? launch_analysis_cp<T, CP, true>(p, alm, use_w, s, nlaunch)
-                  : launch_analysis_cp<T, CP, false>(p, alm, use_w, s, nlaunch);
+static cudaError_t launch_analysis_sel(const hpx_plan_s* p, T* alm, bool use_w, double mfac, cudaStream_t s,
+                                       int* nlaunch) {
+  return p->d_tab ? launch_analysis_cp<T, CP, true>(p, alm, use_w, mfac, s, nlaunch)
+                  : launch_analysis_cp<T, CP, false>(p, alm, use_w, mfac, s, nlaunch);
 }
 
 template <typename T>
@@ -610,20 +614,21 @@ static int pick_cp(const hpx_plan_s* p) {
 }
 
 template <typename T>
-cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, cudaStream_t s, int* nlaunch) {
+cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, double mfac, cudaStream_t s, int* nlaunch) {
   switch (pick_cp<T>(p)) {
-    case 1: return launch_analysis_sel<T, 1>(p, alm, use_w, s, nlaunch);
-    case 2: return launch_analysis_sel<T, 2>(p, alm, use_w, s, nlaunch);
-    case 4: return launch_analysis_sel<T, 4>(p, alm, use_w, s, nlaunch);
-    case 8: return launch_analysis_sel<T, 8>(p, alm, use_w, s, nlaunch);
+    case 1: return launch_analysis_sel<T, 1>(p, alm, use_w, mfac, s, nlaunch);
+    case 2: return launch_analysis_sel<T, 2>(p, alm, use_w, mfac, s, nlaunch);
+    case 4: return launch_analysis_sel<T, 4>(p, alm, use_w, mfac, s, nlaunch);
+    case 8: return launch_analysis_sel<T, 8>(p, alm, use_w, mfac, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_analysis_sel<T, 16>(p, alm, use_w, s, nlaunch);
-      else return launch_analysis_sel<T, 8>(p, alm, use_w, s, nlaunch);
+      if constexpr (sizeof(T) == 4) return launch_analysis_sel<T, 16>(p, alm, use_w, mfac, s, nlaunch);
+      else return launch_analysis_sel<T, 8>(p, alm, use_w, mfac, s, nlaunch);
   }
 }
 
 template <typename T, int CP, bool TAB>
-static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
+static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, double mfac, cudaStream_t s,
+                                       int* nlaunch) {
   using V = C2<T>;
   const int nthr = 128;
   dim3 grid((p->npair + nthr - 1) / nthr, p->mmax + 1);
@@ -631,7 +636,7 @@ static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaSt
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
     k_legendre_synthesis<T, CP, TAB><<<grid, nthr, 0, s>>>(
         alm, (V*)p->d_F, p->d_ring, p->d_coef_c, p->d_coef_pf, p->d_coef_p, p->d_lc, p->d_mu0, p->d_mu1,
-        p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb, lam_tab<T>(p));
+        p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb, lam_tab<T>(p), mfac);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*nlaunch;
@@ -640,24 +645,25 @@ static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, cudaSt
 }
 
 template <typename T, int CP>
-static cudaError_t launch_synthesis_sel(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
-  return p->d_tab ? launch_synthesis_cp<T, CP, true>(p, alm, s, nlaunch)
-                  : launch_synthesis_cp<T, CP, false>(p, alm, s, nlaunch);
+static cudaError_t launch_synthesis_sel(const hpx_plan_s* p, const T* alm, double mfac, cudaStream_t s,
+                                        int* nlaunch) {
+  return p->d_tab ? launch_synthesis_cp<T, CP, true>(p, alm, mfac, s, nlaunch)
+                  : launch_synthesis_cp<T, CP, false>(p, alm, mfac, s, nlaunch);
 }
 
 template <typename T>
-cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, cudaStream_t s, int* nlaunch) {
+cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, double mfac, cudaStream_t s, int* nlaunch) {
   int cp = 1;
   const int cmax = sizeof(T) == 4 ? 16 : 8;
   while (cp < p->nbatch && cp < cmax) cp *= 2;
   switch (cp) {
-    case 1: return launch_synthesis_sel<T, 1>(p, alm, s, nlaunch);
-    case 2: return launch_synthesis_sel<T, 2>(p, alm, s, nlaunch);
-    case 4: return launch_synthesis_sel<T, 4>(p, alm, s, nlaunch);
-    case 8: return launch_synthesis_sel<T, 8>(p, alm, s, nlaunch);
+    case 1: return launch_synthesis_sel<T, 1>(p, alm, mfac, s, nlaunch);
+    case 2: return launch_synthesis_sel<T, 2>(p, alm, mfac, s, nlaunch);
+    case 4: return launch_synthesis_sel<T, 4>(p, alm, mfac, s, nlaunch);
+    case 8: return launch_synthesis_sel<T, 8>(p, alm, mfac, s, nlaunch);
     default:
-      if constexpr (sizeof(T) == 4) return launch_synthesis_sel<T, 16>(p, alm, s, nlaunch);
-      else return launch_synthesis_sel<T, 8>(p, alm, s, nlaunch);
+      if constexpr (sizeof(T) == 4) return launch_synthesis_sel<T, 16>(p, alm, mfac, s, nlaunch);
+      else return launch_synthesis_sel<T, 8>(p, alm, mfac, s, nlaunch);
   }
 }
 
@@ -763,9 +769,9 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s) {
 
 template cudaError_t build_lambda_table<float>(hpx_plan_s*, cudaStream_t);
 template cudaError_t build_lambda_table<double>(hpx_plan_s*, cudaStream_t);
-template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, cudaStream_t, int*);
-template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, cudaStream_t, int*);
-template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, cudaStream_t, int*);
-template cudaError_t launch_synthesis<double>(const hpx_plan_s*, const double*, cudaStream_t, int*);
+template cudaError_t launch_analysis<float>(const hpx_plan_s*, float*, bool, double, cudaStream_t, int*);
+template cudaError_t launch_analysis<double>(const hpx_plan_s*, double*, bool, double, cudaStream_t, int*);
+template cudaError_t launch_synthesis<float>(const hpx_plan_s*, const float*, double, cudaStream_t, int*);
+template cudaError_t launch_synthesis<double>(const hpx_plan_s*, const double*, double, cudaStream_t, int*);
 
 }  // namespace hpx

@@ -93,10 +93,10 @@ extern "C" hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* 
     cudaError_t e;
     if (plan->dtype == HPX_F64) {
       e = hpx::launch_r2c<double>(&view, static_cast<const double*>(map), s);
-      if (e == cudaSuccess) e = hpx::launch_analysis<double>(&view, static_cast<double*>(alm), true, s, &nlaunch);
+      if (e == cudaSuccess) e = hpx::launch_analysis<double>(&view, static_cast<double*>(alm), true, 1.0, s, &nlaunch);
     } else {
       e = hpx::launch_r2c<float>(&view, static_cast<const float*>(map), s);
-      if (e == cudaSuccess) e = hpx::launch_analysis<float>(&view, static_cast<float*>(alm), true, s, &nlaunch);
+      if (e == cudaSuccess) e = hpx::launch_analysis<float>(&view, static_cast<float*>(alm), true, 1.0, s, &nlaunch);
     }
     if (e != cudaSuccess) st = hpx::cuda_fail(e, "hpx_map2alm_noalloc");
   }

@@ -170,20 +170,23 @@ static cudaError_t staged(hpx_plan_s* p, int stage, cudaStream_t s, F&& f) {
 }
 
 template <typename T>
-static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool weighted, cudaStream_t s) {
+static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool weighted, double mfac,
+                                cudaStream_t s) {
   cudaError_t e = staged(p, 0, s, [&](int* n) {
     *n = 1;
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e == cudaSuccess)
-    e = staged(p, 1, s, [&](int* n) { return launch_analysis<T>(p, static_cast<T*>(alm), weighted, s, n); });
+    e = staged(p, 1, s,
+               [&](int* n) { return launch_analysis<T>(p, static_cast<T*>(alm), weighted, mfac, s, n); });
   return e;
 }
 
 template <typename T>
-static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, cudaStream_t s) {
+static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, double mfac,
+                                 cudaStream_t s) {
   cudaError_t e =
-      staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), s, n); });
+      staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), mfac, s, n); });
   if (e == cudaSuccess)
     e = staged(p, 3, s, [&](int* n) {
       *n = 1;
@@ -193,18 +196,18 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
 }
 
 static hpx_status transform(hpx_plan p, const void* in, void* out, hpx_stream_t stream, bool analysis,
-                            bool weighted, const char* name) {
+                            bool weighted, const char* name, double mfac = 1.0) {
   hpx_status st = check_call(p, in, out);
   if (st != HPX_OK) return st;
   DeviceGuard g(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (analysis)
-    e = p->dtype == HPX_F64 ? run_analysis<double>(p, in, out, weighted, s)
-                            : run_analysis<float>(p, in, out, weighted, s);
+    e = p->dtype == HPX_F64 ? run_analysis<double>(p, in, out, weighted, mfac, s)
+                            : run_analysis<float>(p, in, out, weighted, mfac, s);
   else
-    e = p->dtype == HPX_F64 ? run_synthesis<double>(p, in, out, weighted, s)
-                            : run_synthesis<float>(p, in, out, weighted, s);
+    e = p->dtype == HPX_F64 ? run_synthesis<double>(p, in, out, weighted, mfac, s)
+                            : run_synthesis<float>(p, in, out, weighted, mfac, s);
   if (e != cudaSuccess) return cuda_fail(e, name);
   return HPX_OK;
 }
@@ -359,6 +362,14 @@ hpx_status hpx_alm2map(hpx_plan plan, const void* alm, void* map, hpx_stream_t s
 
 hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map, hpx_stream_t stream) {
   return transform(plan, alm, map, stream, false, true, "hpx_map2alm_adjoint");
+}
+
+hpx_status hpx_alm2map_grad(hpx_plan plan, const void* grad_map, void* grad_alm, hpx_stream_t stream) {
+  return transform(plan, grad_map, grad_alm, stream, true, false, "hpx_alm2map_grad", 2.0);
+}
+
+hpx_status hpx_map2alm_grad(hpx_plan plan, const void* grad_alm, void* grad_map, hpx_stream_t stream) {
+  return transform(plan, grad_alm, grad_map, stream, false, true, "hpx_map2alm_grad", 0.5);
 }
 
 static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_t stream, bool analysis) {
