@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run (config 5)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-duration", type=float, default=10.0)
+    ap.add_argument("--serve-drain", type=float, default=15.0)
     ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiling only")
     ap.add_argument("--lmax", type=int, default=None)
     ap.add_argument("--nbatch", type=int, default=NBATCH)
@@ -288,6 +292,7 @@ def run_ours(args):
     plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
     torch.cuda.synchronize(dev)
     plan_s = time.perf_counter() - t0
+    plan_bytes = plan.device_bytes
     tab = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
     roofline = legendre_roofline(plan, tab["stages"], table=True)
     t_max, value, stage_report, clk = tab["t_max"], tab["value"], tab["stages"], tab["clocks"]
@@ -297,6 +302,12 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(plan, maps, alm_in, dist, dev, args.steps, world)
+
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        plan.close()
+        torch.cuda.empty_cache()
+        serving = run_serving(dev, args.serve_rate, args.serve_duration, args.serve_drain)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -315,8 +326,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
-                "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan.device_bytes,
+                "gpu_launches": launches, "clocks": clk, "serving": serving,
+                "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "significant_triples": active, "all_triples": total},
                 "lambda_recompute": {"value": rec["value"], "ms_per_step": rec["t_max"] / args.steps,
                                      "roofline": rec["roofline"], "stages": rec["stages"],
@@ -410,6 +421,89 @@ def legendre_roofline(plan, stages, table: bool):
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
             "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per launch "
                     f"(of {total}; contributions below 2^-193 dropped)"}
+
+
+SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
+
+
+def _serve_stream(dev, pools, rate, duration, drain_s, seed):
+    import torch
+
+    from paper_2510_01785_gb300.serve import GpuExecutor, Server, make_requests
+    reqs = make_requests(seed, rate, duration, SERVE_MIX, max_channels=32)
+    for r in reqs:
+        m, a = pools[r.nside]
+        r.x = m[: r.nch] if r.op == "map2alm" else a[: r.nch]
+    ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=(64, 128, 256, 512))
+    srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=2)
+    wall = srv.run(reqs, drain_s=drain_s)
+    torch.cuda.synchronize(dev)
+    for ss in srv.slots.values():
+        for s in ss:
+            ex.free_slot(s.handle)
+    torch.cuda.empty_cache()
+    return reqs, srv, wall
+
+
+def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_rate: float = 10.0) -> dict:
+    """Config 5: a seeded Poisson stream of map2alm/alm2map requests (50/50),
+    Nside from SERVE_MIX, lmax = 3 Nside - 1, 1-32 FP32 channels, served by
+    the continuously batching server under a 120 GB cap (requests still
+    queued drain_s after the last arrival are reported unserved).  The
+    requests it served are then run one at a time (one launch per request,
+    one stream, same plans) for the transforms/s comparison, and a second,
+    sustainable-rate stream gives the latency the server holds when it
+    keeps up."""
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import synthetic as syn
+    from paper_2510_01785_gb300.serve import latency_report
+
+    pools = {}
+    for ns in SERVE_MIX:  # band-limited input pools, 32 channels per Nside
+        lmax = 3 * ns - 1
+        with hpx.Plan(ns, lmax, lmax, 32, "f32", device=dev) as p:
+            a = torch.from_numpy(syn.gaussian_alm(SEED + ns, lmax, lmax, 32).astype(np.complex64)).to(dev)
+            pools[ns] = (p.alm2map(a), a)
+        torch.cuda.synchronize(dev)
+    reqs, srv, wall = _serve_stream(dev, pools, rate, duration, drain_s, SEED + 5)
+    rep = latency_report(reqs)
+    served = [r for r in reqs if r.t_done is not None and r.error is None]
+    served_ch = sum(r.nch for r in served)
+    out = {"offered_rps": len(reqs) / duration, "duration_s": duration, "drain_limit_s": drain_s,
+           "wall_s": wall, "served_rps": rep["served"] / wall, "transforms_per_s": served_ch / wall,
+           "unserved": len(reqs) - rep["served"] - rep["errors"], "batches": srv.batches,
+           "peak_slot_bytes": srv.peak_bytes, **rep,
+           "lambda": "tables for Nside <= 512, recomputed above"}
+    # the same served requests, one at a time
+    plans, outs = {}, {}
+    for r in served:
+        if r.nside not in plans:
+            plans[r.nside] = hpx.Plan(r.nside, r.lmax, r.lmax, 32, "f32", lambda_table=r.nside <= 512, device=dev)
+            outs[r.nside] = (plans[r.nside].empty_alm(), plans[r.nside].empty_map())
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for r in served:
+        p = plans[r.nside]
+        if r.op == "map2alm":
+            p.map2alm_n(r.nch, r.x, outs[r.nside][0])
+        else:
+            p.alm2map_n(r.nch, r.x, outs[r.nside][1])
+        torch.cuda.synchronize(dev)
+    t1 = time.perf_counter() - t0
+    for p in plans.values():
+        p.close()
+    torch.cuda.empty_cache()
+    out["one_at_a_time_same_requests"] = {"requests": len(served), "seconds": t1,
+                                          "transforms_per_s": served_ch / t1 if t1 > 0 else None}
+    sreqs, ssrv, swall = _serve_stream(dev, pools, sustainable_rate, duration, drain_s, SEED + 6)
+    srep = latency_report(sreqs)
+    out["sustainable_point"] = {"offered_rps": len(sreqs) / duration, "wall_s": swall, "batches": ssrv.batches,
+                                "transforms_per_s": sum(r.nch for r in sreqs if r.t_done is not None) / swall,
+                                **srep}
+    return out
 
 
 def measure_e2e(plan, maps, alm_in, dist, dev, steps, world):

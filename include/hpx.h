@@ -143,6 +143,14 @@ hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map,
 hpx_status hpx_alm2map_adjoint(hpx_plan plan, const void* map, void* alm,
                                hpx_stream_t stream);
 
+/* hpx_map2alm / hpx_alm2map on the first n channels only (1 <= n <= nbatch):
+ * buffers hold n channels in the same layout.  Lets one plan serve batches
+ * of varying size (continuous batching of requests). */
+hpx_status hpx_map2alm_n(hpx_plan plan, int n, const void* map, void* alm,
+                         hpx_stream_t stream);
+hpx_status hpx_alm2map_n(hpx_plan plan, int n, const void* alm, void* map,
+                         hpx_stream_t stream);
+
 /* Gradients for automatic differentiation (Sec. III-F, IV-C).  The
  * coefficients are the real parameters (Re a_lm, Im a_lm) of a real field,
  * and a coefficient gradient holds dL/dRe + i dL/dIm (PyTorch's convention
@@ -212,6 +220,12 @@ hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches);
  * significant l on (the recurrence steps the kernels execute per chain).
  * Synchronous. */
 hpx_status hpx_plan_chain_stats(hpx_plan plan, int64_t* active, int64_t* total);
+
+/* Device bytes hpx_plan_create_ex would allocate for these arguments (an
+ * upper bound for the lambda table), without allocating or touching the GPU;
+ * 0 for invalid arguments.  For admission control. */
+size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch,
+                               hpx_dtype dtype, unsigned flags);
 
 /* Bytes of the plan-resident lambda table (0 without HPX_PLAN_LAMBDA_TABLE). */
 size_t hpx_plan_table_bytes(hpx_plan plan);

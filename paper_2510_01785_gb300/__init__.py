@@ -160,6 +160,28 @@ class Plan:
         dst = self._alm(out, "out") if out is not None else self.empty_alm()
         return self._call(lib().hpx_alm2map_adjoint, "hpx_alm2map_adjoint", src, dst, stream)
 
+    def _first_n(self, t: torch.Tensor, n: int, cols: int, dtype, name: str) -> torch.Tensor:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device and t.dtype == dtype
+                and t.is_contiguous() and t.dim() == 2 and t.shape[0] >= n and t.shape[1] == cols):
+            raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor with >= {n} rows of {cols}")
+        return t
+
+    def map2alm_n(self, n: int, maps: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """map2alm of the first n (<= nbatch) rows of maps into out."""
+        src = self._first_n(maps, n, self.npix, self.real_dtype, "maps")
+        dst = self._first_n(out, n, self.nalm, self.complex_dtype, "out")
+        check(lib().hpx_map2alm_n(self._h, n, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                  ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_map2alm_n")
+        return dst
+
+    def alm2map_n(self, n: int, alm: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """alm2map of the first n (<= nbatch) rows of alm into out."""
+        src = self._first_n(alm, n, self.nalm, self.complex_dtype, "alm")
+        dst = self._first_n(out, n, self.npix, self.real_dtype, "out")
+        check(lib().hpx_alm2map_n(self._h, n, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                  ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_alm2map_n")
+        return dst
+
     def alm2map_grad(self, grad_map: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Backward of alm2map: D Y^dagger g (dL/dRe + i dL/dIm per coefficient)."""
         src = self._map(grad_map, "grad_map")

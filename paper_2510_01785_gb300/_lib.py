@@ -30,6 +30,8 @@ SIGNATURES = {
     "hpx_map2alm_adjoint": (_I, [_P, _P, _P, _P]),
     "hpx_alm2map_adjoint": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_noalloc": (_I, [_P, _P, _P, _P]),
+    "hpx_map2alm_n": (_I, [_P, _I, _P, _P, _P]),
+    "hpx_alm2map_n": (_I, [_P, _I, _P, _P, _P]),
     "hpx_alm2map_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_host": (_I, [_P, _P, _P, _P]),
@@ -40,6 +42,7 @@ SIGNATURES = {
     "hpx_plan_stage_times": (_I, [_P, _P, _P]),
     "hpx_plan_chain_stats": (_I, [_P, _P, _P]),
     "hpx_plan_table_bytes": (_SZ, [_P]),
+    "hpx_plan_estimate_bytes": (_SZ, [_I, _I, _I, _I, _I, _U]),
     "hpx_last_error": (ctypes.c_char_p, []),
 }
 

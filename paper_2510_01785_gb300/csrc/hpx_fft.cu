@@ -277,17 +277,13 @@ cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     k_build_twiddles<double><<<32, 256, 0, s>>>(p->logtw, tw64);
     const size_t smem = sizeof(double2) << p->logm_max;
-    e = cudaFuncSetAttribute(k_build_bluestein<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_smem(k_build_bluestein<T>);
     if (e != cudaSuccess) return e;
     k_build_bluestein<T><<<ns - 1, 256, smem, s>>>(p->d_ring, tw64, p->logtw, (V*)p->d_btab);
     e = cudaGetLastError();
     cudaFreeAsync(tw64, s);
     if (e != cudaSuccess) return e;
   }
-  const int smem = (int)(((size_t(1) << p->logm_max) + 1) * sizeof(V));
-  e = cudaFuncSetAttribute(k_ring_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ring_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
@@ -295,6 +291,8 @@ template <typename T>
 cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   using V = C2<T>;
   const size_t smem = ((size_t(1) << p->logm_max) + 1) * sizeof(V);
+  cudaError_t e = allow_max_smem(k_ring_r2c<T>);
+  if (e != cudaSuccess) return e;
   k_ring_r2c<T><<<dim3(p->nring, p->nbatch), 256, smem, s>>>(
       map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw,
       p->logtw, p->npix, p->nspec);
@@ -305,6 +303,8 @@ template <typename T>
 cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s) {
   using V = C2<T>;
   const size_t smem = ((size_t(1) << p->logm_max) + 1) * sizeof(V);
+  cudaError_t e = allow_max_smem(k_ring_c2r<T>);
+  if (e != cudaSuccess) return e;
   k_ring_c2r<T><<<dim3(p->nring, p->nbatch), 256, smem, s>>>(
       (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw,
       p->logtw, p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0);

@@ -92,6 +92,20 @@ constexpr int kSigExp = 200;
 void set_error(const char* fmt, ...);
 hpx_status cuda_fail(cudaError_t e, const char* what);
 
+// Let `func` launch with any dynamic shared memory size the current device
+// allows.  The attribute is global per function, so plans of different sizes
+// (and threads launching them) must not set it to their own sizes: one plan
+// could lower it below what another, still live, launches with.  The launch
+// size itself decides occupancy, not this limit.
+template <typename F>
+cudaError_t allow_max_smem(F* func) {
+  int dev = 0, maxopt = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt);
+  return e;
+}
+
 __host__ __device__ inline long long alm_base(int lmax, int m) {  // index(l = 0, m); index(l, m) = alm_base + l
   return (long long)m * (2 * lmax + 1 - m) / 2;
 }

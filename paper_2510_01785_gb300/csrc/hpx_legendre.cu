@@ -556,8 +556,7 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, d
   int nthr, csize;
   analysis_shape(p->npair, &nthr, &csize);
   const size_t smem = analysis_smem<T, CP>(nthr);
-  cudaError_t e = cudaFuncSetAttribute(k_legendre_analysis<T, CP, TAB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(k_legendre_analysis<T, CP, TAB>);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csize, p->mmax + 1, 1);

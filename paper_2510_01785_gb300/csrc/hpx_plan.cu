@@ -343,6 +343,32 @@ hpx_status hpx_plan_destroy(hpx_plan plan) {
 
 size_t hpx_plan_device_bytes(hpx_plan plan) { return plan ? plan->bytes : 0; }
 
+size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags) {
+  if (nside < 1 || nside > 2048 || !is_pow2(nside) || lmax < 0 || mmax < 0 || mmax > lmax || nbatch < 1)
+    return 0;
+  const size_t rs = dtype == HPX_F64 ? sizeof(double) : sizeof(float), cs = 2 * rs;
+  const size_t nring = 4 * (size_t)nside - 1, npair = 2 * (size_t)nside;
+  const size_t nalm = (size_t)hpx_nalm(lmax, mmax), nchain = (size_t)(mmax + 1) * npair;
+  const size_t nspec = 6 * (size_t)nside * nside + 4 * (size_t)nside - 1;
+  const size_t netab = 4 * (size_t)nside * (nside - 1) + 8 * (size_t)nside;
+  size_t nbtab = 0;
+  int logm_max = ilog2(2LL * nside);
+  for (long long i = 1; i < nside; ++i) {
+    if (is_pow2(i)) continue;
+    long long M = 1;
+    while (M < 4 * i - 1) M <<= 1;
+    nbtab += (size_t)M;
+    if (ilog2(M) > logm_max) logm_max = ilog2(M);
+  }
+  size_t b = sizeof(RingInfo) * nring + cs * netab + cs * (nbtab ? nbtab : 1) + cs * ((size_t)1 << (logm_max - 1)) +
+             sizeof(double) * (mmax + 1) + (2 * sizeof(double) + sizeof(float)) * nalm +
+             (sizeof(int) + 2 * sizeof(double)) * nchain + cs * (size_t)nbatch * nspec +
+             cs * (size_t)nbatch * nring * (mmax + 1);
+  if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
+    b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ((npair + 31) / 32);
+  return b;
+}
+
 size_t hpx_plan_table_bytes(hpx_plan plan) {
   if (!plan || !plan->d_tab) return 0;
   return (size_t)plan->tab_elems * (plan->dtype == HPX_F64 ? sizeof(double) : sizeof(float));
@@ -362,6 +388,31 @@ hpx_status hpx_alm2map(hpx_plan plan, const void* alm, void* map, hpx_stream_t s
 
 hpx_status hpx_map2alm_adjoint(hpx_plan plan, const void* alm, void* map, hpx_stream_t stream) {
   return transform(plan, alm, map, stream, false, true, "hpx_map2alm_adjoint");
+}
+
+// The first n channels of the plan's batch: a view of the plan with nbatch n
+// (the workspace is channel-major, so its first n channel slices serve).
+static hpx_status transform_n(hpx_plan plan, int n, const void* in, void* out, hpx_stream_t stream,
+                              bool analysis, const char* name) {
+  if (!plan) {
+    set_error("%s: null plan", name);
+    return HPX_ERR_INVALID;
+  }
+  if (n < 1 || n > plan->nbatch) {
+    set_error("%s: n = %d outside [1, %d]", name, n, plan->nbatch);
+    return HPX_ERR_INVALID;
+  }
+  hpx_plan_s view = *plan;
+  view.nbatch = n;
+  return transform(&view, in, out, stream, analysis, analysis, name);
+}
+
+hpx_status hpx_map2alm_n(hpx_plan plan, int n, const void* map, void* alm, hpx_stream_t stream) {
+  return transform_n(plan, n, map, alm, stream, true, "hpx_map2alm_n");
+}
+
+hpx_status hpx_alm2map_n(hpx_plan plan, int n, const void* alm, void* map, hpx_stream_t stream) {
+  return transform_n(plan, n, alm, map, stream, false, "hpx_alm2map_n");
 }
 
 hpx_status hpx_alm2map_grad(hpx_plan plan, const void* grad_map, void* grad_alm, hpx_stream_t stream) {

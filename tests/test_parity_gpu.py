@@ -267,3 +267,20 @@ def test_cfg2_table_mode_equals_recompute(big):
     with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True) as pt:
         assert torch.equal(pt.map2alm(big["dmaps"]), big["a"])
         assert torch.equal(pt.alm2map(big["dalm"]), big["s"])
+
+
+def test_plans_of_different_sizes_interleaved():
+    """A plan keeps working after a smaller one is created (per-function
+    launch limits are global and must not shrink under a live plan)."""
+    h = hpx()
+    big_p = h.Plan(64, 191, 191, 2, "f32")
+    x = to_dev(syn.white_maps(71, 64, 2), "f32")
+    ref = big_p.map2alm(x).clone()
+    small = h.Plan(4, 11, 11, 1, "f32")
+    small.map2alm(to_dev(syn.white_maps(72, 4, 1), "f32"))
+    again = big_p.map2alm(x)
+    m = big_p.alm2map(ref)
+    torch.cuda.synchronize()
+    assert torch.equal(again, ref) and torch.isfinite(m).all()
+    small.close()
+    big_p.close()

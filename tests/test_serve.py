@@ -1,0 +1,124 @@
+"""Host-side logic of the continuously batching server, with a fake executor
+(no GPU): batching, admission under the HBM cap with eviction of idle
+slots, and requests that fail on the host without blocking the others."""
+import itertools
+
+from paper_2510_01785_gb300.serve import Request, Server, latency_report, make_requests
+
+
+class FakeExecutor:
+    """A slot is busy for `work` pump calls after a launch."""
+
+    def __init__(self, bytes_per_slot=10, work=2):
+        self.bps, self.work = bytes_per_slot, work
+        self.ids = itertools.count()
+        self.live = {}
+        self.launches = []
+
+    def slot_bytes(self, nside, lmax, max_ch):
+        return self.bps * (2 if nside >= 1024 else 1)
+
+    def new_slot(self, nside, lmax, max_ch):
+        h = {"id": next(self.ids), "nside": nside, "left": 0, "batch": [], "bytes": self.slot_bytes(nside, lmax, max_ch)}
+        self.live[h["id"]] = h
+        return h
+
+    def handle_bytes(self, h):
+        return h["bytes"]
+
+    def free_slot(self, h):
+        assert h["left"] == 0
+        del self.live[h["id"]]
+
+    def launch(self, h, op, batch):
+        assert sum(r.nch for r in batch) <= 32 and len({(r.nside, r.op) for r in batch}) == 1
+        h["left"], h["batch"] = self.work, batch
+        self.launches.append((h["id"], op, [r.rid for r in batch]))
+
+    def done(self, h):
+        h["left"] -= 1
+        return h["left"] <= 0
+
+    def finish(self, h):
+        return [f"out{r.rid}" for r in h["batch"]]
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-3
+        return self.t
+
+
+def drain(srv, limit=10000):
+    for _ in range(limit):
+        srv.pump()
+        if not srv.pending() and not srv.busy():
+            return
+    raise AssertionError("server did not drain")
+
+
+def test_requests_arriving_together_are_packed_into_batches():
+    ex = FakeExecutor()
+    srv = Server(ex, hbm_cap_bytes=100, max_channels=32, max_slots_per_key=1, clock=Clock())
+    reqs = [Request(rid=i, op="map2alm", nside=64, nch=5) for i in range(20)]
+    for r in reqs:
+        srv.submit(r)
+    drain(srv)
+    assert all(r.y == f"out{r.rid}" and r.error is None for r in reqs)
+    # 20 x 5 channels in batches of at most 6 requests (30 channels)
+    assert len(ex.launches) == 4 and max(len(b) for _, _, b in ex.launches) == 6
+    served = [rid for _, _, b in ex.launches for rid in b]
+    assert served == list(range(20))  # arrival order kept
+
+
+def test_late_arrivals_join_the_next_batch_while_a_batch_runs():
+    ex = FakeExecutor(work=3)
+    srv = Server(ex, hbm_cap_bytes=100, max_channels=32, max_slots_per_key=1, clock=Clock())
+    srv.submit(Request(rid=0, op="alm2map", nside=16, nch=4))
+    srv.pump()  # launches rid 0
+    for i in range(1, 5):
+        srv.submit(Request(rid=i, op="alm2map", nside=16, nch=4))
+    drain(srv)
+    assert [b for _, _, b in ex.launches] == [[0], [1, 2, 3, 4]]
+
+
+def test_admission_never_exceeds_the_cap_and_evicts_idle_slots():
+    ex = FakeExecutor(bytes_per_slot=10, work=2)
+    srv = Server(ex, hbm_cap_bytes=25, max_channels=32, max_slots_per_key=2, clock=Clock())
+    reqs = [Request(rid=i, op="map2alm" if i % 2 else "alm2map", nside=[16, 32, 64][i % 3], nch=20)
+            for i in range(30)]
+    for r in reqs:
+        srv.submit(r)
+        srv.pump()
+        assert srv.bytes <= 25
+    drain(srv)
+    assert srv.peak_bytes <= 25
+    assert all(r.y is not None for r in reqs)
+    assert len(ex.live) <= 2
+
+
+def test_bad_requests_fail_on_the_host_and_do_not_block_others():
+    ex = FakeExecutor()
+    srv = Server(ex, hbm_cap_bytes=15, max_channels=32, clock=Clock())
+    bad = [Request(rid=100, op="map2alm", nside=12, nch=1), Request(rid=101, op="map2alm", nside=16, nch=40),
+           Request(rid=102, op="fft", nside=16, nch=1), Request(rid=103, op="map2alm", nside=1024, nch=1)]
+    good = [Request(rid=i, op="map2alm", nside=16, nch=2) for i in range(3)]
+    for r in bad + good:
+        srv.submit(r)
+    drain(srv)
+    assert all(r.error for r in bad) and "cap" in bad[3].error
+    assert all(r.error is None and r.y == f"out{r.rid}" for r in good)
+    rep = latency_report(bad + good)
+    assert rep["errors"] == 4 and rep["served"] == 3
+
+
+def test_make_requests_is_seeded_and_follows_the_mix():
+    a = make_requests(7, 500.0, 2.0, {64: 0.5, 1024: 0.5})
+    b = make_requests(7, 500.0, 2.0, {64: 0.5, 1024: 0.5})
+    assert [(r.op, r.nside, r.nch, r.t_arrival) for r in a] == [(r.op, r.nside, r.nch, r.t_arrival) for r in b]
+    assert 800 < len(a) < 1200
+    assert all(1 <= r.nch <= 32 and r.lmax == 3 * r.nside - 1 for r in a)
+    assert 0.4 < sum(r.op == "map2alm" for r in a) / len(a) < 0.6
