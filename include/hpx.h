@@ -92,6 +92,16 @@ typedef enum {
                                         the real type per significant
                                         (l, m, ring pair), about 30 GB in
                                         float at nside 1024, lmax 3071. */
+#define HPX_PLAN_TENSOR_CORES 2u     /* with HPX_PLAN_LAMBDA_TABLE on an
+                                        HPX_F32 plan: the Legendre analysis
+                                        (Eq. 26-27) runs as a tensor-core
+                                        matrix product (tcgen05, three TF32
+                                        split products per term, "3xTF32"),
+                                        fed by TMA from the table.  Results
+                                        agree with the CUDA-core path to FP32
+                                        rounding, not bit for bit.  Other
+                                        dtypes or a missing table flag:
+                                        HPX_ERR_INVALID. */
 
 /* Number of packed coefficients for (lmax, mmax). */
 int64_t hpx_nalm(int lmax, int mmax);
@@ -229,6 +239,13 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch,
 
 /* Bytes of the plan-resident lambda table (0 without HPX_PLAN_LAMBDA_TABLE). */
 size_t hpx_plan_table_bytes(hpx_plan plan);
+
+/* Status of the plan's device-side waits.  Synchronises the plan's device,
+ * returns HPX_ERR_TIMEOUT if a bounded wait inside one of the plan's kernels
+ * expired since the last call (that transform's output is incomplete) and
+ * clears the record; HPX_OK otherwise.  The host-buffer entry points check
+ * it themselves. */
+hpx_status hpx_plan_device_status(hpx_plan plan);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* hpx_last_error(void);

@@ -55,7 +55,8 @@ class Plan:
     plan per concurrently used stream."""
 
     def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,
-                 dtype: str = "f32", lambda_table: bool = False, device=None):
+                 dtype: str = "f32", lambda_table: bool = False, device=None,
+                 tensor_cores: bool = False):
         mmax = lmax if mmax is None else mmax
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
@@ -69,7 +70,10 @@ class Plan:
         self.npix = 12 * nside * nside
         self.nalm = nalm(lmax, mmax)
         self._h = None
+        self.lambda_table, self.tensor_cores = lambda_table, tensor_cores
         flags = _lib.HPX_PLAN_LAMBDA_TABLE if lambda_table else _lib.HPX_PLAN_LAMBDA_RECOMPUTE
+        if tensor_cores:
+            flags |= _lib.HPX_PLAN_TENSOR_CORES
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib().hpx_plan_create_ex(nside, lmax, mmax, nbatch, DTYPES[dtype], flags,
@@ -97,6 +101,11 @@ class Plan:
     @property
     def device_bytes(self) -> int:
         return int(lib().hpx_plan_device_bytes(self._h))
+
+    def device_status(self) -> None:
+        """Synchronise and raise HpxError(HPX_ERR_TIMEOUT) if a bounded
+        device-side wait of this plan's kernels expired since the last check."""
+        check(lib().hpx_plan_device_status(self._h), "hpx_plan_device_status")
 
     @property
     def table_bytes(self) -> int:
@@ -255,14 +264,14 @@ _plan_lock = threading.Lock()
 
 
 def get_plan(nside: int, lmax: int, mmax: int | None, nbatch: int, dtype: str, device=None,
-             lambda_table: bool = False) -> Plan:
-    """A cached plan per (geometry, batch, dtype, device)."""
+             lambda_table: bool = False, tensor_cores: bool = False) -> Plan:
+    """A cached plan per (geometry, batch, dtype, device, options)."""
     mmax = lmax if mmax is None else mmax
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    key = (nside, lmax, mmax, nbatch, dtype, device, lambda_table)
+    key = (nside, lmax, mmax, nbatch, dtype, device, lambda_table, tensor_cores)
     with _plan_lock:
         p = _plan_cache.get(key)
         if p is None:
-            p = Plan(nside, lmax, mmax, nbatch, dtype, lambda_table, device)
+            p = Plan(nside, lmax, mmax, nbatch, dtype, lambda_table, device, tensor_cores)
             _plan_cache[key] = p
     return p

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libhpx.so")
 
 HPX_F64, HPX_F32, HPX_F32_BF16, HPX_F32_BF16X3, HPX_F32_FP16, HPX_F32_FP16X3 = range(6)
-HPX_PLAN_LAMBDA_RECOMPUTE, HPX_PLAN_LAMBDA_TABLE = 0, 1
+HPX_PLAN_LAMBDA_RECOMPUTE, HPX_PLAN_LAMBDA_TABLE, HPX_PLAN_TENSOR_CORES = 0, 1, 2
 STATUS = {0: "HPX_OK", 1: "HPX_ERR_INVALID", 2: "HPX_ERR_NOMEM", 3: "HPX_ERR_CUDA",
           4: "HPX_ERR_TIMEOUT", 5: "HPX_ERR_UNSUPPORTED"}
 
@@ -43,6 +43,7 @@ SIGNATURES = {
     "hpx_plan_chain_stats": (_I, [_P, _P, _P]),
     "hpx_plan_table_bytes": (_SZ, [_P]),
     "hpx_plan_estimate_bytes": (_SZ, [_I, _I, _I, _I, _I, _U]),
+    "hpx_plan_device_status": (_I, [_P]),
     "hpx_last_error": (ctypes.c_char_p, []),
 }
 

@@ -70,14 +70,15 @@ __device__ void fft_dit(V* buf, int logm, const V* __restrict__ tw, int logtw, b
 template <typename V>
 __device__ void ring_dft(V* buf, int H, int logm, bool bluestein, const V* __restrict__ E,
                          const V* __restrict__ Bk, const V* __restrict__ tw, int logtw) {
-  const long long twoN = 4LL * H;
+  // chirp index 2 n^2 mod 2N: n < H <= 8192, so 32-bit unsigned arithmetic is exact
+  const unsigned twoN = 4u * (unsigned)H;
   if (!bluestein) {
     fft_dif(buf, logm, tw, logtw, false);
     return;
   }
   const int M = 1 << logm;
   for (int n = threadIdx.x; n < M; n += blockDim.x) {
-    if (n < H) buf[n] = cmul(buf[n], E[(2LL * n * n) % twoN]);
+    if (n < H) buf[n] = cmul(buf[n], E[(2u * (unsigned)n * (unsigned)n) % twoN]);
     else buf[n] = cmk<V>(0, 0);
   }
   __syncthreads();
@@ -85,7 +86,7 @@ __device__ void ring_dft(V* buf, int H, int logm, bool bluestein, const V* __res
   for (int j = threadIdx.x; j < M; j += blockDim.x) buf[j] = cmul(buf[j], Bk[j]);
   __syncthreads();
   fft_dit(buf, logm, tw, logtw, true);
-  for (int k = threadIdx.x; k < H; k += blockDim.x) buf[k] = cmul(buf[k], E[(2LL * k * k) % twoN]);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) buf[k] = cmul(buf[k], E[(2u * (unsigned)k * (unsigned)k) % twoN]);
   __syncthreads();
 }
 
@@ -142,7 +143,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   const int y = blockIdx.x, b = blockIdx.y;
   const RingInfo R = rings[y];
   const int N = R.nphi, H = N >> 1, logm = R.logm, sig = R.sigma;
-  const long long twoN = 2LL * N;
+  const unsigned twoN = 2u * (unsigned)N;  // sigma m < 2^15: 32-bit arithmetic is exact
   const bool blue = R.btab >= 0;
   const V* E = etab + R.etab;
   const V* Fy = F + ((long long)b * nring + y) * (mmax + 1);
@@ -150,7 +151,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   auto term = [&](int m) -> V {  // F_m exp(+i pi sigma m / N)
     V f = Fy[m];
     if (m == 0) f.y = 0;
-    return cmul(f, cconj(E[((long long)sig * m) % twoN]));
+    return cmul(f, cconj(E[((unsigned)sig * (unsigned)m) % twoN]));
   };
   const int per_bin = (mmax + N) / N;
   if (per_bin > 8) {  // few bins, many aliases: one warp per bin

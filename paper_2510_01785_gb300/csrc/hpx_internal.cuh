@@ -78,6 +78,13 @@ struct hpx_plan_s {
   int* d_tab_lstart;   // [mmax+1][ngroup] first l stored for the group
   int ngroup;
   long long tab_elems;
+  // tensor-core analysis (HPX_PLAN_TENSOR_CORES): per-transform operand
+  // Gt[m][g][n][32] and the TMA descriptors of it and of the table
+  int tc_nn;           // N columns of the tensor-core tile (0: not used)
+  void* d_gt;
+  alignas(64) unsigned char tm_tab[128];
+  alignas(64) unsigned char tm_gt[128];
+  int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
   size_t bytes;
 };
 
@@ -87,6 +94,10 @@ namespace hpx {
 // the first l at which |mu_l| >= 2^-kSigExp; earlier values are below
 // 2^-kSigExp (about 1.6e-60) and are dropped.
 constexpr int kSigExp = 200;
+
+// Rows (l values) per tensor-core tile of the Legendre analysis; the lambda
+// table's group starts are aligned to this grid relative to m.
+constexpr int kTcTile = 128;
 
 // error reporting (thread-local message)
 void set_error(const char* fmt, ...);
@@ -129,5 +140,12 @@ cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s);
 cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s);
 template <typename T>
 cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
+
+// tensor-core analysis (hpx_tc.cu): plan-time operand buffers and TMA
+// descriptors; the per-transform launch (operand pack + tile kernel)
+int tc_columns(int nbatch);  // N of the tile for a plan of nbatch channels
+cudaError_t build_tc_analysis(hpx_plan_s* p);
+cudaError_t launch_analysis_tc(const hpx_plan_s* p, float* alm, bool use_weight, double mfac, cudaStream_t s,
+                               int* nlaunch);
 
 }  // namespace hpx

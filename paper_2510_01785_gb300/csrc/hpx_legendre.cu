@@ -284,40 +284,59 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   double mu1 = 0.0, mu2 = 0.0;
   int buf = 0;
   if (t < LB) sCz[t] = (m + t <= lmax) ? coef_c[base + m + t] : 0.0;
+  // TAB: this warp's group rows (32 coalesced 128-byte rows per block),
+  // loaded one block ahead so the loads are in flight during the contraction
+  // and the reductions of the block before
+  int tls = INT_MAX;
+  const T* ttg = nullptr;
+  T nxt[TAB ? LB : 1];
+  if constexpr (TAB) {
+    const int g = warp * csize + crank;
+    if (g < tb.ngroup) {
+      tls = tb.lstart[(long long)m * tb.ngroup + g];
+      ttg = tb.tab + tb.off[(long long)m * tb.ngroup + g] + lane;
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int l = m + i;
+      nxt[i] = (l >= tls && l <= lmax) ? __ldcs(ttg + (long long)(l - tls) * 32) : (T)0;
+    }
+  }
   __syncthreads();
   for (int lb0 = m; lb0 <= lmax; lb0 += LB) {
     const double* cz = sCz + buf * LB;
     // --- recurrence: LB steps of mu_l = c_l z mu_{l-1} - mu_{l-2} ---
     T* myMu = sMu + (size_t)t * MS;
-    if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
-      // table rows of this warp's group (TAB): 32 coalesced 128-byte rows
-      int ls = INT_MAX;
-      const T* tg = nullptr;
-      if constexpr (TAB) {
-        const int g = warp * csize + crank;
-        if (g < tb.ngroup) {
-          ls = tb.lstart[(long long)m * tb.ngroup + g];
-          tg = tb.tab + tb.off[(long long)m * tb.ngroup + g] + lane;
+    if constexpr (TAB) {
+#pragma unroll
+      for (int i4 = 0; i4 < LB; i4 += 4) {
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(myMu + i4) = make_float4(nxt[i4], nxt[i4 + 1], nxt[i4 + 2], nxt[i4 + 3]);
+        } else {
+          *reinterpret_cast<double2*>(myMu + i4) = make_double2(nxt[i4], nxt[i4 + 1]);
+          *reinterpret_cast<double2*>(myMu + i4 + 2) = make_double2(nxt[i4 + 2], nxt[i4 + 3]);
         }
       }
+#pragma unroll
+      for (int i = 0; i < LB; ++i) {
+        const int l = lb0 + LB + i;
+        nxt[i] = (l >= tls && l <= lmax) ? __ldcs(ttg + (long long)(l - tls) * 32) : (T)0;
+      }
+    } else if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
 #pragma unroll
       for (int i4 = 0; i4 < LB; i4 += 4) {
         T v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int l = lb0 + i4 + u;
-          if constexpr (TAB) {
-            v[u] = (l >= ls && l <= lmax) ? __ldcs(tg + (long long)(l - ls) * 32) : (T)0;
-          } else {
-            double mu = fma(cz[i4 + u] * z, mu1, -mu2);
-            if (l == lc) {
-              mu = s1;
-              mu1 = s0;
-            }
-            mu2 = mu1;
-            mu1 = mu;
-            v[u] = to_real<T>(mu);
+          double mu = fma(cz[i4 + u] * z, mu1, -mu2);
+          if (l == lc) {
+            mu = s1;
+            mu1 = s0;
           }
+          mu2 = mu1;
+          mu1 = mu;
+          v[u] = to_real<T>(mu);
         }
         if constexpr (sizeof(T) == 4) {
           *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
@@ -679,8 +698,8 @@ cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s) {
 // plan-resident lambda table
 // ---------------------------------------------------------------------------
 // Earliest chain start of each (m, 32-pair group) and its number of rows.
-__global__ void k_table_groups(const int* __restrict__ lc_tab, int lmax, int npair, int ngroup, int* lstart,
-                               long long* rows) {
+__global__ void k_table_groups(const int* __restrict__ lc_tab, int lmax, int npair, int ngroup, int align,
+                               int* lstart, long long* rows) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (g >= ngroup) return;
@@ -689,6 +708,10 @@ __global__ void k_table_groups(const int* __restrict__ lc_tab, int lmax, int npa
     const int p = g * 32 + j;
     if (p < npair) ls = min(ls, lc_tab[(long long)m * npair + p]);
   }
+  // for the tensor-core analysis: aligned down to its tile grid m + align j,
+  // so that a group covers a tile either entirely or not at all (the extra
+  // rows hold zeros)
+  if (ls <= lmax) ls = m + ((ls - m) / align) * align;
   lstart[(long long)m * ngroup + g] = ls;
   rows[(long long)m * ngroup + g] = lmax + 1 - ls;
 }
@@ -740,8 +763,8 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s) {
   e = cudaMalloc((void**)&p->d_tab_off, sizeof(long long) * nent);
   if (e != cudaSuccess) return e;
   p->bytes += sizeof(long long) * nent;
-  k_table_groups<<<dim3((ng + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, ng,
-                                                                      p->d_tab_lstart, p->d_tab_off);
+  k_table_groups<<<dim3((ng + 127) / 128, p->mmax + 1), 128, 0, s>>>(
+      p->d_lc, p->lmax, p->npair, ng, (p->flags & HPX_PLAN_TENSOR_CORES) ? kTcTile : 1, p->d_tab_lstart, p->d_tab_off);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;

@@ -119,7 +119,7 @@ static void plan_free(hpx_plan_s* p) {
   if (!p) return;
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
-                  p->d_tab, p->d_tab_off, p->d_tab_lstart};
+                  p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->timing) {
@@ -177,8 +177,11 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e == cudaSuccess)
-    e = staged(p, 1, s,
-               [&](int* n) { return launch_analysis<T>(p, static_cast<T*>(alm), weighted, mfac, s, n); });
+    e = staged(p, 1, s, [&](int* n) {
+      if constexpr (sizeof(T) == 4)
+        if (p->tc_nn) return launch_analysis_tc(p, static_cast<float*>(alm), weighted, mfac, s, n);
+      return launch_analysis<T>(p, static_cast<T*>(alm), weighted, mfac, s, n);
+    });
   return e;
 }
 
@@ -248,8 +251,12 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("dtype %d is not provided by this build", (int)dtype);
     return HPX_ERR_UNSUPPORTED;
   }
-  if (flags & ~HPX_PLAN_LAMBDA_TABLE) {
+  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES)) {
     set_error("unknown plan flags 0x%x", flags);
+    return HPX_ERR_INVALID;
+  }
+  if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
+    set_error("HPX_PLAN_TENSOR_CORES needs an HPX_F32 plan with HPX_PLAN_LAMBDA_TABLE");
     return HPX_ERR_INVALID;
   }
   hpx_plan_s* p = new hpx_plan_s();
@@ -301,7 +308,8 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
             alloc((void**)&p->d_lc, sizeof(int) * nchain) && alloc((void**)&p->d_mu0, sizeof(double) * nchain) &&
             alloc((void**)&p->d_mu1, sizeof(double) * nchain) &&
             alloc(&p->d_spec, cs * (size_t)nbatch * p->nspec) &&
-            alloc(&p->d_F, cs * (size_t)nbatch * p->nring * (mmax + 1));
+            alloc(&p->d_F, cs * (size_t)nbatch * p->nring * (mmax + 1)) &&
+            alloc((void**)&p->d_status, sizeof(int));
   if (!ok) {
     plan_free(p);
     return HPX_ERR_NOMEM;
@@ -312,11 +320,15 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     plan_free(p);
     return cuda_fail(e, "cudaStreamCreate");
   }
-  k_ring_geometry<<<(p->nring + 127) / 128, 128, 0, s>>>(nside, p->d_ring);
-  e = cudaGetLastError();
+  e = cudaMemsetAsync(p->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_ring_geometry<<<(p->nring + 127) / 128, 128, 0, s>>>(nside, p->d_ring);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE))
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
+  if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc_analysis(p);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -364,9 +376,13 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
              sizeof(double) * (mmax + 1) + (2 * sizeof(double) + sizeof(float)) * nalm +
              (sizeof(int) + 2 * sizeof(double)) * nchain + cs * (size_t)nbatch * nspec +
              cs * (size_t)nbatch * nring * (mmax + 1);
+  const size_t ngroup = (npair + 31) / 32;
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
-    b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ((npair + 31) / 32);
-  return b;
+    b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ngroup;
+  if (flags & HPX_PLAN_TENSOR_CORES)  // group starts padded to the tile grid; the Gt operand
+    b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) +
+         sizeof(float) * (size_t)(mmax + 1) * ngroup * tc_columns(nbatch) * 32;
+  return b + sizeof(int);
 }
 
 size_t hpx_plan_table_bytes(hpx_plan plan) {
@@ -423,6 +439,19 @@ hpx_status hpx_map2alm_grad(hpx_plan plan, const void* grad_alm, void* grad_map,
   return transform(plan, grad_alm, grad_map, stream, false, true, "hpx_map2alm_grad", 0.5);
 }
 
+// Reads and clears the plan's device-side wait status (after a sync).
+static hpx_status read_status(hpx_plan p) {
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st != 0) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+  if (st != 0) {
+    set_error("a bounded device-side wait expired; the transform's output is incomplete");
+    return HPX_ERR_TIMEOUT;
+  }
+  return HPX_OK;
+}
+
 static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_t stream, bool analysis) {
   if (!p || !hin || !hout) {
     set_error("null argument");
@@ -454,7 +483,18 @@ static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
-  return HPX_OK;
+  return read_status(p);
+}
+
+hpx_status hpx_plan_device_status(hpx_plan plan) {
+  if (!plan) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(plan->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device synchronise");
+  return read_status(plan);
 }
 
 hpx_status hpx_map2alm_host(hpx_plan plan, const void* host_map, void* host_alm, hpx_stream_t stream) {

@@ -66,3 +66,20 @@ def test_null_plan_calls_are_rejected(hpxlib):
     assert L.hpx_map2alm(None, buf, buf, None) == 1
     assert L.hpx_plan_destroy(None) == 0
     assert L.hpx_plan_device_bytes(None) == 0
+    assert L.hpx_plan_device_status(None) == 1
+
+
+@pytest.mark.parametrize("dtype,flags", [(0, 3), (1, 2), (0, 2), (1, 4)])
+def test_tensor_core_flag_needs_an_f32_table_plan(hpxlib, dtype, flags):
+    L = hpxlib.lib()
+    h = ctypes.c_void_p()
+    assert L.hpx_plan_create_ex(16, 47, 47, 1, dtype, flags, ctypes.byref(h)) == 1
+    assert h.value is None
+
+
+def test_estimate_counts_the_tensor_core_operands(hpxlib):
+    L = hpxlib.lib()
+    table = L.hpx_plan_estimate_bytes(1024, 3071, 3071, 8, 1, 1)
+    tc = L.hpx_plan_estimate_bytes(1024, 3071, 3071, 8, 1, 3)
+    # Gt operand: (mmax+1) x 64 groups x 32 columns x 32 pairs x 4 bytes
+    assert tc - table >= 3072 * 64 * 32 * 32 * 4

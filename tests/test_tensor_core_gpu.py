@@ -1,0 +1,132 @@
+"""Tensor-core (tcgen05, 3xTF32) Legendre analysis against the FP64 oracle
+and against the CUDA-core path on the same table.
+
+The tensor-core plan computes the same sums as the CUDA-core FP32 path, in a
+different order and from TF32 split products, so it is held to the FP32
+tolerance against the oracle (relative L2 per channel <= 1e-5) and its
+error may not exceed twice that of the CUDA-core FP32 path (plus 1e-6).  Cases cover every N tile
+(8, 16, 32 and 64 channels per launch), more channels than one launch takes,
+tiles that end past lmax, mmax < lmax, and groups whose rows start inside
+the l range.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_01785_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def hpx():
+    import paper_2510_01785_gb300 as h
+    return h
+
+
+def rel_err(got, ref):
+    got = np.atleast_2d(np.asarray(got))
+    ref = np.atleast_2d(np.asarray(ref))
+    num = np.linalg.norm((got - ref).reshape(ref.shape[0], -1), axis=1)
+    den = np.linalg.norm(ref.reshape(ref.shape[0], -1), axis=1)
+    return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+CASES = [
+    # nside, lmax, mmax, nbatch
+    (1, 2, 2, 1),
+    (2, 5, 5, 3),
+    (8, 40, 30, 2),        # every ring aliases
+    (16, 47, 20, 3),       # mmax < lmax
+    (32, 0, 0, 1),         # lmax = 0
+    (64, 191, 191, 9),     # N = 64 (16 channels per launch), ragged
+    (32, 95, 95, 17),      # N = 128, ragged
+    (32, 95, 95, 40),      # N = 256, ragged
+    (32, 95, 95, 70),      # two launches of 64 channels
+    (128, 383, 383, 2),    # three l tiles per low m
+    (256, 400, 380, 1),
+    (512, 1535, 1535, 2),  # group starts well inside the l range
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"ns{c[0]}-l{c[1]}-m{c[2]}-b{c[3]}" for c in CASES])
+def test_tensor_core_analysis_parity(case):
+    nside, lmax, mmax, nb = case
+    maps = syn.white_maps(syn.SEED_BASE + 300 + nside, nside, nb).astype(np.float32)
+    alm = syn.gaussian_alm(syn.SEED_BASE + 400 + nside, lmax, mmax, nb, power=1.0).astype(np.complex64)
+    m64, a64 = maps.astype(np.float64), alm.astype(np.complex128)
+    h = hpx()
+    with h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc, \
+            h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True) as pt:
+        dm, da = torch.from_numpy(maps).cuda(), torch.from_numpy(alm).cuda()
+        got = {"map2alm": pc.map2alm(dm), "alm2map_adjoint": pc.alm2map_adjoint(dm),
+               "alm2map": pc.alm2map(da)}
+        cuda_core = {"map2alm": pt.map2alm(dm), "alm2map_adjoint": pt.alm2map_adjoint(dm)}
+        pc.device_status()
+        ref = {"map2alm": oracle.map2alm(m64, lmax, mmax),
+               "alm2map_adjoint": oracle.alm2map_adjoint(m64, lmax, mmax),
+               "alm2map": oracle.alm2map(a64, nside, lmax, mmax)}
+        for k, v in got.items():
+            e = rel_err(v.cpu().numpy(), ref[k])
+            assert e <= 1e-5, (k, e)
+            if k in cuda_core:  # no worse than the CUDA-core FP32 path, up to rounding noise
+                e_cc = rel_err(cuda_core[k].cpu().numpy(), ref[k])
+                print(f"{case} {k}: tensor cores {e:.3e}, CUDA cores {e_cc:.3e}")
+                assert e <= 2.0 * e_cc + 1e-6, (k, e, e_cc)
+        a = got["map2alm"].cpu().numpy()
+        assert np.all(a[:, : lmax + 1].imag == 0.0)
+
+
+def test_tensor_core_gradient_scaling():
+    """The adjoint-with-gradient entry point (m > 0 doubled) runs through the
+    same tile kernel: it matches the CUDA-core table plan."""
+    nside, lmax, nb = 64, 191, 3
+    maps = torch.from_numpy(syn.white_maps(91, nside, nb).astype(np.float32)).cuda()
+    h = hpx()
+    with h.Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc, \
+            h.Plan(nside, lmax, lmax, nb, "f32", lambda_table=True) as pt:
+        g1 = pc.alm2map_grad(maps)
+        g2 = pt.alm2map_grad(maps)
+        torch.cuda.synchronize()
+        assert rel_err(g1.cpu().numpy(), g2.cpu().numpy()) <= 1e-5
+
+
+def test_tensor_core_deterministic_and_status():
+    nside, lmax, nb = 128, 383, 5
+    maps = torch.from_numpy(syn.white_maps(92, nside, nb).astype(np.float32)).cuda()
+    with hpx().Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc:
+        a1 = pc.map2alm(maps).clone()
+        a2 = pc.map2alm(maps)
+        pc.device_status()
+        assert torch.equal(a1, a2)
+        host = pc.map2alm_host(maps.cpu().numpy())
+        assert np.array_equal(host.numpy(), a1.cpu().numpy())
+
+
+NS2, L2, B2 = 1024, 3071, 8
+
+
+def test_cfg2_tensor_core_sampled():
+    """Nside 1024, lmax 3071, 8 channels: sampled coefficients against the
+    oracle, and the whole output against the CUDA-core table plan."""
+    maps = syn.white_maps(syn.SEED_BASE + 2, NS2, B2).astype(np.float32)
+    h = hpx()
+    dm = torch.from_numpy(maps).cuda()
+    with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True, tensor_cores=True) as pc:
+        a = pc.map2alm(dm)
+        pc.device_status()
+        a = a.cpu().numpy()
+    with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True) as pt:
+        b = pt.map2alm(dm).cpu().numpy()
+    assert rel_err(a, b) <= 1e-5
+    ms = [0, 1, 2, 127, 128, 1024, 2047, 3000, 3071]
+    ls, mm = [], []
+    r = syn.rng(78)
+    for m in ms:
+        cand = sorted(set([m, min(m + 1, L2), min(m + 127, L2), min(m + 128, L2), L2]
+                          + list(r.integers(m, L2 + 1, 3))))
+        ls += cand
+        mm += [m] * len(cand)
+    ls, mm = np.array(ls, np.int32), np.array(mm, np.int32)
+    ref = oracle.analysis_sep(maps.astype(np.float64), L2, ls, mm, weights="equal")
+    assert rel_err(a[:, oracle.alm_index(L2, ls, mm)], ref) <= 1e-5
