@@ -287,13 +287,22 @@ def run_ours(args):
     active, total = plan_r.chain_stats()
     plan_r.close()
 
-    # plan-resident lambda table (built by the same FP64 recurrence at plan time)
+    # plan-resident lambda table (built by the same FP64 recurrence at plan
+    # time), Legendre analysis on the CUDA cores
+    plan_c = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
+    cc = timed_steps(plan_c, maps, alm_in, args, dist, dev, world, gpu_index)
+    cc["roofline"] = legendre_roofline(plan_c, cc["stages"], table=True)
+    plan_c.close()
+    torch.cuda.empty_cache()
+
+    # headline: the same table, Legendre analysis on the tensor cores
     t0 = time.perf_counter()
-    plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
+    plan = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, tensor_cores=True, device=dev)
     torch.cuda.synchronize(dev)
     plan_s = time.perf_counter() - t0
     plan_bytes = plan.device_bytes
     tab = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
+    plan.device_status()
     roofline = legendre_roofline(plan, tab["stages"], table=True)
     t_max, value, stage_report, clk = tab["t_max"], tab["value"], tab["stages"], tab["clocks"]
     launches = tab["launches"]
@@ -321,14 +330,16 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX,
                            "nbatch": NBATCH, "step": "map2alm + alm2map of the batch",
-                           "lambda": "plan-resident table generated once by the FP64 recurrence "
-                                     "(bit-identical results to recomputing it per transform)",
+                           "lambda": "plan-resident table generated once by the FP64 recurrence",
+                           "analysis": "tensor cores (tcgen05, 3xTF32 split products, FP32 group sums)",
                            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "significant_triples": active, "all_triples": total},
+                "cuda_core_table": {"value": cc["value"], "ms_per_step": cc["t_max"] / args.steps,
+                                    "roofline": cc["roofline"], "stages": cc["stages"], "clocks": cc["clocks"]},
                 "lambda_recompute": {"value": rec["value"], "ms_per_step": rec["t_max"] / args.steps,
                                      "roofline": rec["roofline"], "stages": rec["stages"],
                                      "clocks": rec["clocks"]}}
@@ -376,7 +387,8 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
     t_max = reduce_max(dist, t_ms, dev)
     report = {}
     for k, (ms, n) in stages.items():
-        report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
+        if n > 0 or k != "analysis_operand_pack":
+            report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
     return {"t_max": t_max, "value": throughput(world, args.steps, t_max), "stages": report,
             "clocks": clk, "launches": sum(n for _, n in stages.values())}
 
@@ -392,11 +404,18 @@ def legendre_roofline(plan, stages, table: bool):
     spec_bytes = 8 * NBATCH * (6 * NSIDE * NSIDE + 4 * NSIDE - 1)
     f_bytes = 8 * NBATCH * (4 * NSIDE - 1) * (MMAX + 1)
     tab_bytes = plan.table_bytes if table else 0
-    for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes)):
-        s = stages[k]
-        s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
+    tc = "analysis_operand_pack" in stages
+    # tensor-core analysis: the pack reads the spectra and writes the operand
+    # Gt[m][group][4 x channels][32] once; the tile kernel reads the table,
+    # Gt and writes alm
+    gt_bytes = 4 * (MMAX + 1) * ((2 * NSIDE + 31) // 32) * 32 * 4 * min(64, max(8, 1 << (NBATCH - 1).bit_length()))
+    for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes),
+                  ("analysis_operand_pack", spec_bytes + gt_bytes)):
+        if k in stages:
+            s = stages[k]
+            s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
     fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
-    leg_bytes = {"legendre_analysis": tab_bytes + spec_bytes + alm_bytes,
+    leg_bytes = {"legendre_analysis": tab_bytes + (gt_bytes if tc else spec_bytes) + alm_bytes,
                  "legendre_synthesis": tab_bytes + alm_bytes + f_bytes}
     for k in ("legendre_analysis", "legendre_synthesis"):
         s = stages[k]
@@ -409,9 +428,10 @@ def legendre_roofline(plan, stages, table: bool):
     dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k]["ms_per_launch"])
     kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
     if table:
+        kname = "k_analysis_tc" if (tc and dom == "legendre_analysis") else kname + "<table>"
         achieved = stages[dom]["hbm_gbs_algorithmic"]
-        return {"bound": "hbm", "kernel": kname + "<table>", "achieved": achieved, "peak": HBM_PEAK_GBS,
-                "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": kernel_traffic(kname + "<table>"),
+        return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": HBM_PEAK_GBS,
+                "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": kernel_traffic(kname),
                 "peak_source": HBM_PEAK_SOURCE,
                 "work": f"lambda table {tab_bytes} B + compulsory inputs/outputs {leg_bytes[dom] - tab_bytes} B "
                         f"per launch"}

@@ -217,9 +217,10 @@ hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi,
 
 /* Stage timing.  While enabled, every transform on the plan records a pair of
  * CUDA events on its stream around each stage: 0 ring analysis FFT, 1
- * Legendre analysis, 2 Legendre synthesis, 3 ring synthesis FFT.
+ * Legendre analysis, 2 Legendre synthesis, 3 ring synthesis FFT, 4 operand
+ * pack of the tensor-core analysis (HPX_PLAN_TENSOR_CORES plans only).
  * hpx_plan_stage_times waits for the recorded events, adds their elapsed
- * times (ms) and kernel launch counts into ms[4] and launches[4] (either may
+ * times (ms) and kernel launch counts into ms[5] and launches[5] (either may
  * be NULL), and clears the record.  Measurement support, not part of the
  * transform. */
 hpx_status hpx_plan_set_timing(hpx_plan plan, int enable);

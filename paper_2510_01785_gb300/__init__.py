@@ -225,7 +225,8 @@ class Plan:
         return dst
 
     # -- measurement support ------------------------------------------------
-    STAGES = ("ring_fft_analysis", "legendre_analysis", "legendre_synthesis", "ring_fft_synthesis")
+    STAGES = ("ring_fft_analysis", "legendre_analysis", "legendre_synthesis", "ring_fft_synthesis",
+              "analysis_operand_pack")
 
     def set_timing(self, enable: bool) -> None:
         """Record CUDA events around each stage of every following transform."""
@@ -233,8 +234,8 @@ class Plan:
 
     def stage_times(self) -> dict:
         """{stage: (total ms, kernel launches)} since the last call; waits."""
-        ms = np.zeros(4, np.float64)
-        n = np.zeros(4, np.int64)
+        ms = np.zeros(len(self.STAGES), np.float64)
+        n = np.zeros(len(self.STAGES), np.int64)
         check(lib().hpx_plan_stage_times(self._h, ctypes.c_void_p(ms.ctypes.data),
                                          ctypes.c_void_p(n.ctypes.data)), "hpx_plan_stage_times")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}

@@ -141,11 +141,13 @@ cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s);
 template <typename T>
 cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 
-// tensor-core analysis (hpx_tc.cu): plan-time operand buffers and TMA
-// descriptors; the per-transform launch (operand pack + tile kernel)
+// tensor-core analysis (hpx_tc.cu): plan-time operand buffer and TMA
+// descriptors; per launch of up to tc_channels_per_launch channels from b0,
+// the operand pack (from the ring spectra) and then the tile kernel
 int tc_columns(int nbatch);  // N of the tile for a plan of nbatch channels
 cudaError_t build_tc_analysis(hpx_plan_s* p);
-cudaError_t launch_analysis_tc(const hpx_plan_s* p, float* alm, bool use_weight, double mfac, cudaStream_t s,
-                               int* nlaunch);
+int tc_channels_per_launch(const hpx_plan_s* p);
+cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);
+cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s);
 
 }  // namespace hpx

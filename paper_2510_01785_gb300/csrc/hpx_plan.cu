@@ -105,6 +105,7 @@ struct DeviceGuard {
 };
 
 // Optional per-stage CUDA events (hpx_plan_set_timing).
+constexpr int kStages = 5;
 struct TimingRec {
   int stage;
   cudaEvent_t a, b;
@@ -176,13 +177,25 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     *n = 1;
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
-  if (e == cudaSuccess)
-    e = staged(p, 1, s, [&](int* n) {
-      if constexpr (sizeof(T) == 4)
-        if (p->tc_nn) return launch_analysis_tc(p, static_cast<float*>(alm), weighted, mfac, s, n);
-      return launch_analysis<T>(p, static_cast<T*>(alm), weighted, mfac, s, n);
-    });
-  return e;
+  if (e != cudaSuccess) return e;
+  if (p->tc_nn) {  // tensor cores: operand pack (stage 4), then the tile kernel (stage 1), per channel chunk
+    const int cp = tc_channels_per_launch(p);
+    for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
+      const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
+      e = staged(p, 4, s, [&](int* n) {
+        *n = 1;
+        return launch_pack_tc(p, b0, nb, weighted, s);
+      });
+      if (e == cudaSuccess)
+        e = staged(p, 1, s, [&](int* n) {
+          *n = 1;
+          return launch_tile_tc(p, static_cast<float*>(alm), b0, nb, mfac, s);
+        });
+    }
+    return e;
+  }
+  return staged(p, 1, s,
+                [&](int* n) { return launch_analysis<T>(p, static_cast<T*>(alm), weighted, mfac, s, n); });
 }
 
 template <typename T>
@@ -541,9 +554,9 @@ hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches) {
     return HPX_ERR_INVALID;
   }
   if (ms)
-    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    for (int k = 0; k < kStages; ++k) ms[k] = 0.0;
   if (launches)
-    for (int k = 0; k < 4; ++k) launches[k] = 0;
+    for (int k = 0; k < kStages; ++k) launches[k] = 0;
   TimingState* ts = static_cast<TimingState*>(plan->timing);
   if (!ts) return HPX_OK;
   DeviceGuard g(plan->device);

@@ -14,15 +14,13 @@
 // memory and tcgen05.ld brings the tile back for the epilogue (times P_l).
 //
 // FP32 accuracy from TF32 products: the tensor cores read the top 19 bits of
-// each float (10 mantissa bits).  Each operand is split as x = hi + lo with
-// hi = x rounded to the nearest TF32 value, so |lo| <= 2^-11 |x| and lo is
-// exact in FP32; lo is itself rounded to TF32 (error <= 2^-22 |x|).  Then
+// each float (10 mantissa bits), i.e. hi(x) = x truncated to TF32.  With
+// lo(x) = x - hi(x) (exact in FP32, |lo| < 2^-10 |x|) rounded to TF32,
 //   D = hi(L) hi(G) + hi(L) lo(G) + lo(L) hi(G)
 // ("3xTF32", the split-operand scheme of Markidis et al. 2018 and Ootomo &
-// Yokota 2022) has a relative error of at most about 3 x 2^-22 per product
-// (the two rounded remainders and the dropped lo*lo term), accumulated in
-// FP32 in tensor memory.  The split is done in shared memory on each landed
-// tile: hi overwrites the tile, lo goes to a second one.
+// Yokota 2022) drops the lo*lo term and the rounding of the remainders:
+// about 2^-20 relative per product at worst, 2^-22 typically.  The
+// remainders are formed in shared memory from each landed tile.
 //
 // Every mbarrier wait is bounded in time.  When one expires the CTA stops
 // issuing work, waits (again bounded) for the copies and products it has in
@@ -36,7 +34,6 @@
 namespace hpx {
 namespace {
 
-constexpr int kStagesMax = 4;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -118,12 +115,13 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
-// Splits a tile element in place: hi = tf32_rn(x) stays, lo = tf32_rn(x - hi)
-// (x - hi is exact in FP32) goes to the remainder tile.
-__device__ __forceinline__ void split4(float4& x, float4& lo) {
-  const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-  lo = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
-  x = h;
+// The part of x the tensor cores drop (they read the TF32 truncation of x),
+// exact in FP32, itself rounded to TF32.
+__device__ __forceinline__ float tf32_rem(float x) {
+  return tf32_rn(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
+}
+__device__ __forceinline__ float4 tf32_rem4(float4 x) {
+  return make_float4(tf32_rem(x.x), tf32_rem(x.y), tf32_rem(x.z), tf32_rem(x.w));
 }
 
 // ---------------------------------------------------------------------------
@@ -190,63 +188,94 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
 // ---------------------------------------------------------------------------
 template <int NN>
 struct TcShape {
-  static constexpr int kA = kTcTile * 128;        // lambda tile bytes: 128 rows x 32 floats
-  static constexpr int kG = NN * 128;             // Gt tile bytes
-  static constexpr int kStage = 2 * kA + 2 * kG;  // L, lo L, G, lo G
-  static constexpr int kNStage = (kStagesMax * kStage <= 200 * 1024) ? kStagesMax : (200 * 1024) / kStage;
-  static constexpr int kTmemCols = 2 * NN;        // two group accumulators
-  static constexpr size_t kSmem = (size_t)kNStage * kStage + 1024 /* base alignment */ + 1024 /* barriers, list */;
+  static constexpr int kA = kTcTile * 128;   // lambda tile bytes: 128 rows x 32 floats
+  static constexpr int kG = NN * 128;        // Gt tile bytes
+  static constexpr int kStage = kA + 2 * kG; // one stage: lambda tile, Gt tile, its remainder right after it
+  static constexpr int kLo = kA;             // lambda remainder buffer (two, alternating by group)
+  static constexpr int kNStage = (200 * 1024 - 2 * kLo) / kStage < 8 ? (200 * 1024 - 2 * kLo) / kStage : 8;
+  static constexpr int kTmemCols = 4 * NN;   // two group accumulators of 2 NN columns
+  static constexpr size_t kSmem =
+      (size_t)kNStage * kStage + 2 * kLo + 1024 /* base alignment */ + 2048 /* barriers, lists */;
+  static_assert(kNStage >= 2 && kTmemCols <= 512, "shape");
 };
+
+constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, warp 5 issues products
 
 // One CTA: rows l0 .. l0+127 of one m, all channels of the launch.
 //
-// Accumulation: the tensor cores add each instruction's products into the
-// accumulator with truncation, so one accumulator over all K would collect
-// an error growing with the number of ring pairs.  Each 32-pair group is
-// therefore accumulated alone (12 instructions) in one of two TMEM buffers
-// and added, with round-to-nearest FP32 adds, into per-thread register sums
-// while the next group's products run in the other buffer.
+// Per 32-pair group k, with L the lambda tile (128 x 32) and G the operand
+// tile (NN x 32) in shared memory:
+//   split: lo(L) and lo(G) are formed (hi is the hardware's TF32 truncation
+//          of the tile as loaded; lo = x - trunc(x), rounded to TF32);
+//          lo(G) sits right after G, so [G; lo G] is one N = 2 NN operand;
+//   products (4 steps of K = 8): D[:, 0:2NN] += L [G; lo G]^T and
+//          D[:, 0:NN] += lo(L) G^T, i.e. 8 instructions per group;
+//   drain: row l keeps D[l][j] + D[l][NN + j] for the NN/2 columns j of its
+//          parity and adds them into FP32 registers (round to nearest).
+// The tensor cores add each instruction's products into the accumulator
+// with truncation, so each group is accumulated alone, in one of two TMEM
+// buffers (2 NN columns each), while the other is drained.
 //
-// Roles: thread 0 issues the TMA copies, thread 32 the MMAs, all 128
-// threads split the landed tiles and drain the accumulators (thread t owns
-// TMEM lane t = row l0 + t).  No thread leaves the group loop early: after an
-// expired wait a thread only stops doing work, so the warp-collective
-// tcgen05.ld stays convergent.
+// Roles run decoupled, linked by mbarriers: warp 4 keeps up to kNStage
+// groups of copies in flight, warp 5 issues a group's products once it is
+// split and its accumulator is free, warps 0-3 split group k and then drain
+// group k-1.  After an expired wait a role stops working (the split/drain
+// warps keep looping without work, so their warp-collective tcgen05.ld stays
+// convergent), waits for what it started, and the CTA records the timeout.
 template <int NN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmG,
               const long long* __restrict__ tab_off, const int* __restrict__ lstart, int ngroup,
               const double* __restrict__ coef_p, float* __restrict__ alm, int lmax, long long nalm, int b0, int nb,
               double mfac, int* __restrict__ status) {
   using S = TcShape<NN>;
   constexpr int NS = S::kNStage, C2N = NN / 2;
-  static_assert(NN % 32 == 0 && NN <= 256, "N tile");
-  const int t = threadIdx.x, warp = t >> 5;
+  static_assert(NN % 32 == 0 && NN <= 128, "N tile");
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m = blockIdx.y;
   const int l0 = m + kTcTile * blockIdx.x;
   if (l0 > lmax) return;  // whole CTA, before any shared state
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* tiles = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + (size_t)NS * S::kStage);
-  uint64_t* conv = full + NS;   // tile split (128 arrivals)
+  unsigned char* lobuf = tiles + (size_t)NS * S::kStage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(lobuf + 2 * S::kLo);
+  uint64_t* conv = full + NS;   // stage split (128 arrivals)
   uint64_t* empty = conv + NS;  // stage's products done
   uint64_t* accf = empty + NS;  // [2] group accumulator complete
   uint64_t* acce = accf + 2;    // [2] group accumulator drained (128 arrivals)
   uint64_t* done = acce + 2;    // all products done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int* nact = reinterpret_cast<int*>(tmem_slot + 2);
-  int* glist = nact + 1;  // groups reaching this tile, in order (ngroup <= 128)
+  int* wcount = reinterpret_cast<int*>(tmem_slot + 2);  // [4]
+  int* rowA = wcount + 4;   // [128] TMA row of the lambda tile of active group k
+  int* rowG = rowA + 128;   // [128] TMA row of its Gt tile
   auto sL = [&](int s) { return tiles + (size_t)s * S::kStage; };
-  auto sLlo = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA; };
-  auto sG = [&](int s) { return tiles + (size_t)s * S::kStage + 2 * S::kA; };
-  auto sGlo = [&](int s) { return tiles + (size_t)s * S::kStage + 2 * S::kA + S::kG; };
+  auto sG = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA; };
+  auto sGlo = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA + S::kG; };
+  auto sLlo = [&](int b) { return lobuf + (size_t)b * S::kLo; };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(S::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // groups whose rows reach this tile (group starts lie on the tile grid
+  // m + 128 j, so a group covers the whole tile or starts after it), with
+  // their copy coordinates, compacted in group order
+  bool act = false;
+  int ra = 0, rg = 0;
+  unsigned bal = 0;
+  if (warp < 4) {
+    if (t < ngroup) {
+      const long long mg = (long long)m * ngroup + t;
+      const int ls = lstart[mg];
+      act = ls <= l0;
+      ra = (int)(tab_off[mg] / 32) + (l0 - ls);
+      rg = (int)(mg * NN);
+    }
+    bal = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) wcount[warp] = __popc(bal);
   }
   if (t == 32) {
     for (int s = 0; s < NS; ++s) {
@@ -260,147 +289,157 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     }
     mbar_init(done, 1);
     *abort_flag = 0;
-    // group starts lie on the tile grid m + 128 j, so a group either covers
-    // the whole tile or starts after it
-    int n = 0;
-    for (int g = 0; g < ngroup; ++g)
-      if (lstart[(long long)m * ngroup + g] <= l0) glist[n++] = g;
-    *nact = n;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (act) {
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wcount[w];
+    const int k = off + __popc(bal & ((1u << lane) - 1u));
+    rowA[k] = ra;
+    rowG[k] = rg;
+  }
+  const int na = wcount[0] + wcount[1] + wcount[2] + wcount[3];
   const uint32_t tmem = *tmem_slot;
-  const int na = *nact;
+  __syncthreads();
 
-  auto issue_loads = [&](int k) {  // thread 0
-    const int s = k % NS, g = glist[k];
-    const long long mg = (long long)m * ngroup + g;
-    const int row = (int)(tab_off[mg] / 32) + (l0 - lstart[mg]);
-    mbar_expect_tx(&full[s], S::kA + S::kG);
-    tma_load_2d(sL(s), &tmA, 0, row, &full[s]);
-    tma_load_2d(sG(s), &tmG, 0, (int)(mg * NN), &full[s]);
-  };
-  int issued = 0;
-  if (t == 0)
-    for (; issued < na && issued < NS; ++issued) issue_loads(issued);
-
-  // row l = l0 + t keeps the columns of its parity: S (n < C2N) for even
-  // l - m, A for odd
-  const int l = l0 + t;
-  const bool odd = ((l - m) & 1) != 0;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  float sum[C2N];
-#pragma unroll
-  for (int j = 0; j < C2N; ++j) sum[j] = 0.f;
-  auto drain = [&](int buf) {  // warp-collective
-#pragma unroll
-    for (int q = 0; q < C2N / 16; ++q) {
-      uint32_t rs[16], ra[16];
-      tmem_ld16(trow + (uint32_t)(buf * NN + q * 16), rs);
-      tmem_ld16(trow + (uint32_t)(buf * NN + C2N + q * 16), ra);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) sum[q * 16 + j] += __uint_as_float(odd ? ra[j] : rs[j]);
-    }
-  };
-
-  // instruction descriptor: D f32, A and B tf32, both K-major, N = NN, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) | ((128u >> 4) << 24);
-  bool alive = true, mma_issued = false;
-  for (int k = 0; k < na; ++k) {
-    const int s = k % NS;
-    const uint32_t ph = (uint32_t)(k / NS) & 1u;
-    if (alive) alive = wait_phase(&full[s], ph, abort_flag, true);
-    if (alive) {  // split 32 lambda floats and NN/4 Gt floats per thread
-      float4* a = reinterpret_cast<float4*>(sL(s)) + t * 8;
-      float4* alo = reinterpret_cast<float4*>(sLlo(s)) + t * 8;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float4 x = a[j], lo;
-        split4(x, lo);
-        a[j] = x;
-        alo[j] = lo;
+  if (warp == 4) {
+    // ---- copies: group k into stage k % NS once group k - NS's products are done
+    int issued = 0;
+    if (lane == 0) {
+      for (int k = 0; k < na; ++k) {
+        const int s = k % NS;
+        if (k >= NS && !wait_phase(&empty[s], (uint32_t)(k / NS - 1) & 1u, abort_flag, true)) break;
+        mbar_expect_tx(&full[s], S::kA + S::kG);
+        tma_load_2d(sL(s), &tmA, 0, rowA[k], &full[s]);
+        tma_load_2d(sG(s), &tmG, 0, rowG[k], &full[s]);
+        issued = k + 1;
       }
-      float4* gg = reinterpret_cast<float4*>(sG(s)) + t * (NN / 16);
-      float4* glo = reinterpret_cast<float4*>(sGlo(s)) + t * (NN / 16);
-#pragma unroll
-      for (int j = 0; j < NN / 16; ++j) {
-        float4 x = gg[j], lo;
-        split4(x, lo);
-        gg[j] = x;
-        glo[j] = lo;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv[s]);
+      // whatever was started completes before the CTA moves on
+      for (int k = issued > NS ? issued - NS : 0; k < issued; ++k)
+        wait_phase(&full[k % NS], (uint32_t)(k / NS) & 1u, abort_flag, false);
     }
-    if (t == 32 && alive) {
-      alive = wait_phase(&conv[s], ph, abort_flag, true);
-      if (alive && k >= 2) alive = wait_phase(&acce[k & 1], (uint32_t)((k - 2) >> 1) & 1u, abort_flag, true);
-      if (alive) {
+  } else if (warp == 5) {
+    // ---- products
+    if (lane == 0) {
+      // instruction descriptors: D f32, A and B tf32, both K-major, M = 128
+      const uint32_t id2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * NN >> 3) << 17) | ((128u >> 4) << 24);
+      const uint32_t id1 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) | ((128u >> 4) << 24);
+      bool issued_any = false;
+      for (int k = 0; k < na; ++k) {
+        const int s = k % NS, b = k & 1;
+        if (!wait_phase(&conv[s], (uint32_t)(k / NS) & 1u, abort_flag, true)) break;
+        if (k >= 2 && !wait_phase(&acce[b], (uint32_t)((k - 2) >> 1) & 1u, abort_flag, true)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)((k & 1) * NN);
-        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(s)), aG = smem_u32(sG(s)),
-                       aGlo = smem_u32(sGlo(s));
+        const uint32_t d = tmem + (uint32_t)(b * 2 * NN);
+        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(b)), aG = smem_u32(sG(s));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {  // K = 8 floats (32 bytes) per instruction
           const uint32_t off = 32u * j;
-          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aG + off), idesc, j > 0 ? 1u : 0u);
-          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aGlo + off), idesc, 1u);
-          umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aG + off), idesc, 1u);
+          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aG + off), id2, j > 0 ? 1u : 0u);
+          umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aG + off), id1, 1u);
         }
         umma_commit(&empty[s]);
-        umma_commit(&accf[k & 1]);
-        mma_issued = true;
+        umma_commit(&accf[b]);
+        issued_any = true;
+      }
+      if (issued_any) {
+        umma_commit(done);
+        wait_phase(done, 0, abort_flag, false);
       }
     }
-    if (t == 0 && alive && k >= 1 && issued < na) {  // refill the stage group k-1 used once its products are done
-      alive = wait_phase(&empty[(k - 1) % NS], (uint32_t)((k - 1) / NS) & 1u, abort_flag, true);
-      if (alive) issue_loads(issued++);
+  } else {
+    // ---- split and drain (thread t owns TMEM lane t = row l0 + t)
+    const int l = l0 + t;
+    const bool odd = ((l - m) & 1) != 0;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    float sum[C2N];
+#pragma unroll
+    for (int j = 0; j < C2N; ++j) sum[j] = 0.f;
+    auto drain = [&](int buf) {  // warp-collective
+      const uint32_t c0 = trow + (uint32_t)(buf * 2 * NN);
+#pragma unroll
+      for (int q = 0; q < C2N / 16; ++q) {
+        uint32_t s1[16], s2[16], a1[16], a2[16];
+        tmem_ld16(c0 + (uint32_t)(q * 16), s1);
+        tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
+        tmem_ld16(c0 + (uint32_t)(C2N + q * 16), a1);
+        tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          sum[q * 16 + j] += odd ? __uint_as_float(a1[j]) + __uint_as_float(a2[j])
+                                 : __uint_as_float(s1[j]) + __uint_as_float(s2[j]);
+      }
+    };
+    bool alive = true;
+    for (int k = 0; k < na; ++k) {
+      const int s = k % NS, b = k & 1;
+      if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
+      if (alive) {
+        // elementwise, so the swizzle does not matter; consecutive threads
+        // take consecutive 16-byte words.  Remainder buffer b was last read
+        // by group k-2's products, complete since this thread drained that
+        // group in the previous iteration.
+        const float4* a = reinterpret_cast<const float4*>(sL(s));
+        float4* alo = reinterpret_cast<float4*>(sLlo(b));
+#pragma unroll
+        for (int j = 0; j < S::kA / 2048; ++j) alo[j * 128 + t] = tf32_rem4(a[j * 128 + t]);
+        const float4* gg = reinterpret_cast<const float4*>(sG(s));
+        float4* glo = reinterpret_cast<float4*>(sGlo(s));
+#pragma unroll
+        for (int j = 0; j < S::kG / 2048; ++j) glo[j * 128 + t] = tf32_rem4(gg[j * 128 + t]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
+      }
+      if (k >= 1) {  // drain group k-1 while group k's products run
+        bool ok = alive && wait_phase(&accf[b ^ 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          drain(b ^ 1);
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(&acce[b ^ 1]);
+        } else {
+          alive = false;
+        }
+      }
     }
-    __syncwarp();
-    if (k >= 1) {  // drain group k-1 while group k's products run
-      bool ok = alive && wait_phase(&accf[(k - 1) & 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
+    if (na > 0) {  // the last group
+      bool ok = alive && wait_phase(&accf[(na - 1) & 1], (uint32_t)((na - 1) >> 1) & 1u, abort_flag, true);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        drain((k - 1) & 1);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&acce[(k - 1) & 1]);
-      } else {
-        alive = false;
+        drain((na - 1) & 1);
       }
     }
-  }
-  // every product and copy this CTA started completes before the last
-  // drain, or before the tensor memory is released after an abort
-  if (t == 32 && mma_issued) {
-    umma_commit(done);
-    wait_phase(done, 0, abort_flag, false);
-  }
-  if (t == 0)
-    for (int k = issued > NS ? issued - NS : 0; k < issued; ++k)
-      wait_phase(&full[k % NS], (uint32_t)(k / NS) & 1u, abort_flag, false);
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (*abort_flag == 0) {
-    if (na > 0) drain((na - 1) & 1);
-    if (l <= lmax) {
+    __syncwarp();
+    // the CTA-wide sync below orders these writes after every role finished;
+    // results are written only if no wait expired anywhere in the CTA
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag == 0 && l <= lmax) {
       const long long base = alm_base(lmax, m);
       const double scale = coef_p[base + l] * (m > 0 ? mfac : 1.0);
       float2* out = reinterpret_cast<float2*>(alm) + (long long)b0 * nalm + base + l;
 #pragma unroll
       for (int c = 0; c < C2N / 2; ++c)
-        if (c < nb) out[(long long)c * nalm] = make_float2((float)(scale * sum[2 * c]), (float)(scale * sum[2 * c + 1]));
+        if (c < nb)
+          out[(long long)c * nalm] = make_float2((float)(scale * sum[2 * c]), (float)(scale * sum[2 * c + 1]));
     }
-  } else if (t == 0) {
-    atomicExch(status, (int)HPX_ERR_TIMEOUT);
+    if (*abort_flag != 0 && t == 0) atomicExch(status, (int)HPX_ERR_TIMEOUT);
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
+    return;
   }
+  // warps 4 and 5: meet the split/drain warps at their two CTA-wide syncs
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
+  __syncthreads();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -429,33 +468,32 @@ bool encode_rows32(void* out, const void* base, unsigned long long rows, unsigne
 }
 
 template <int CP>
-cudaError_t launch_cp(const hpx_plan_s* p, float* alm, bool use_w, double mfac, cudaStream_t s, int* nlaunch) {
+cudaError_t launch_pack_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
+  k_pack_gt<CP><<<dim3((p->ngroup + 3) / 4, p->mmax + 1), 128, 0, s>>>(
+      (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (float*)p->d_gt, p->npair, p->nring, p->ngroup,
+      p->nspec, b0, nb, use_w ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <int CP>
+cudaError_t launch_tile_cp(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
   constexpr int NN = 4 * CP;
-  using Sh = TcShape<NN>;
   cudaError_t e = allow_max_smem(k_analysis_tc<NN>);
   if (e != cudaSuccess) return e;
   const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(p->tm_tab);
   const CUtensorMap* tmG = reinterpret_cast<const CUtensorMap*>(p->tm_gt);
   const dim3 tiles((p->lmax + kTcTile) / kTcTile, p->mmax + 1);
-  for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
-    const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
-    k_pack_gt<CP><<<dim3((p->ngroup + 3) / 4, p->mmax + 1), 128, 0, s>>>(
-        (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (float*)p->d_gt, p->npair, p->nring,
-        p->ngroup, p->nspec, b0, nb, use_w ? 1 : 0);
-    k_analysis_tc<NN><<<tiles, 128, Sh::kSmem, s>>>(*tmA, *tmG, p->d_tab_off, p->d_tab_lstart, p->ngroup,
-                                                    p->d_coef_p, alm, p->lmax, p->nalm, b0, nb, mfac, p->d_status);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    *nlaunch += 2;
-  }
-  return cudaSuccess;
+  k_analysis_tc<NN><<<tiles, kTcThreads, TcShape<NN>::kSmem, s>>>(*tmA, *tmG, p->d_tab_off, p->d_tab_lstart, p->ngroup,
+                                                          p->d_coef_p, alm, p->lmax, p->nalm, b0, nb, mfac,
+                                                          p->d_status);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 int tc_columns(int nbatch) {
   int cp = 8;
-  while (cp < nbatch && cp < 64) cp *= 2;
+  while (cp < nbatch && cp < 32) cp *= 2;
   return 4 * cp;
 }
 
@@ -474,13 +512,22 @@ cudaError_t build_tc_analysis(hpx_plan_s* p) {
   return cudaSuccess;
 }
 
-cudaError_t launch_analysis_tc(const hpx_plan_s* p, float* alm, bool use_w, double mfac, cudaStream_t s,
-                               int* nlaunch) {
+int tc_channels_per_launch(const hpx_plan_s* p) { return p->tc_nn / 4; }
+
+cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
   switch (p->tc_nn) {
-    case 32: return launch_cp<8>(p, alm, use_w, mfac, s, nlaunch);
-    case 64: return launch_cp<16>(p, alm, use_w, mfac, s, nlaunch);
-    case 128: return launch_cp<32>(p, alm, use_w, mfac, s, nlaunch);
-    case 256: return launch_cp<64>(p, alm, use_w, mfac, s, nlaunch);
+    case 32: return launch_pack_cp<8>(p, b0, nb, use_w, s);
+    case 64: return launch_pack_cp<16>(p, b0, nb, use_w, s);
+    case 128: return launch_pack_cp<32>(p, b0, nb, use_w, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  switch (p->tc_nn) {
+    case 32: return launch_tile_cp<8>(p, alm, b0, nb, mfac, s);
+    case 64: return launch_tile_cp<16>(p, alm, b0, nb, mfac, s);
+    case 128: return launch_tile_cp<32>(p, alm, b0, nb, mfac, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -4,8 +4,9 @@ and against the CUDA-core path on the same table.
 The tensor-core plan computes the same sums as the CUDA-core FP32 path, in a
 different order and from TF32 split products, so it is held to the FP32
 tolerance against the oracle (relative L2 per channel <= 1e-5) and its
-error may not exceed twice that of the CUDA-core FP32 path (plus 1e-6).  Cases cover every N tile
-(8, 16, 32 and 64 channels per launch), more channels than one launch takes,
+error may not exceed twice that of the CUDA-core FP32 path (plus 1e-6).
+Cases cover every N tile (8, 16 and 32 channels per launch), more channels
+than one launch takes,
 tiles that end past lmax, mmax < lmax, and groups whose rows start inside
 the l range.
 """
@@ -41,8 +42,8 @@ CASES = [
     (32, 0, 0, 1),         # lmax = 0
     (64, 191, 191, 9),     # N = 64 (16 channels per launch), ragged
     (32, 95, 95, 17),      # N = 128, ragged
-    (32, 95, 95, 40),      # N = 256, ragged
-    (32, 95, 95, 70),      # two launches of 64 channels
+    (32, 95, 95, 40),      # two launches (32 + 8 channels)
+    (32, 95, 95, 70),      # three launches (32 + 32 + 6)
     (128, 383, 383, 2),    # three l tiles per low m
     (256, 400, 380, 1),
     (512, 1535, 1535, 2),  # group starts well inside the l range
