@@ -93,15 +93,17 @@ typedef enum {
                                         (l, m, ring pair), about 30 GB in
                                         float at nside 1024, lmax 3071. */
 #define HPX_PLAN_TENSOR_CORES 2u     /* with HPX_PLAN_LAMBDA_TABLE on an
-                                        HPX_F32 plan: the Legendre analysis
-                                        (Eq. 26-27) runs as a tensor-core
-                                        matrix product (tcgen05, three TF32
+                                        HPX_F32 plan: both Legendre stages
+                                        (Eq. 24-27) run as tensor-core
+                                        matrix products (tcgen05, three TF32
                                         split products per term, "3xTF32"),
-                                        fed by TMA from the table.  Results
-                                        agree with the CUDA-core path to FP32
-                                        rounding, not bit for bit.  Other
-                                        dtypes or a missing table flag:
-                                        HPX_ERR_INVALID. */
+                                        fed by TMA from the table and from a
+                                        second, transposed copy of it made
+                                        at plan time (about twice the table
+                                        memory).  Results agree with the
+                                        CUDA-core path to FP32 rounding, not
+                                        bit for bit.  Other dtypes or a
+                                        missing table flag: HPX_ERR_INVALID. */
 
 /* Number of packed coefficients for (lmax, mmax). */
 int64_t hpx_nalm(int lmax, int mmax);
@@ -217,11 +219,11 @@ hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi,
 
 /* Stage timing.  While enabled, every transform on the plan records a pair of
  * CUDA events on its stream around each stage: 0 ring analysis FFT, 1
- * Legendre analysis, 2 Legendre synthesis, 3 ring synthesis FFT, 4 operand
- * pack of the tensor-core analysis (HPX_PLAN_TENSOR_CORES plans only).
- * hpx_plan_stage_times waits for the recorded events, adds their elapsed
- * times (ms) and kernel launch counts into ms[5] and launches[5] (either may
- * be NULL), and clears the record.  Measurement support, not part of the
+ * Legendre analysis, 2 Legendre synthesis, 3 ring synthesis FFT, 4 and 5
+ * the operand packs of the tensor-core analysis and synthesis
+ * (HPX_PLAN_TENSOR_CORES plans only).  hpx_plan_stage_times waits for the
+ * recorded events, adds their elapsed times (ms) and kernel launch counts
+ * into ms[6] and launches[6] (either may be NULL), and clears the record.  Measurement support, not part of the
  * transform. */
 hpx_status hpx_plan_set_timing(hpx_plan plan, int enable);
 hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches);

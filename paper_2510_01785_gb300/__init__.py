@@ -226,7 +226,7 @@ class Plan:
 
     # -- measurement support ------------------------------------------------
     STAGES = ("ring_fft_analysis", "legendre_analysis", "legendre_synthesis", "ring_fft_synthesis",
-              "analysis_operand_pack")
+              "analysis_operand_pack", "synthesis_operand_pack")
 
     def set_timing(self, enable: bool) -> None:
         """Record CUDA events around each stage of every following transform."""

@@ -78,12 +78,20 @@ struct hpx_plan_s {
   int* d_tab_lstart;   // [mmax+1][ngroup] first l stored for the group
   int ngroup;
   long long tab_elems;
-  // tensor-core analysis (HPX_PLAN_TENSOR_CORES): per-transform operand
-  // Gt[m][g][n][32] and the TMA descriptors of it and of the table
-  int tc_nn;           // N columns of the tensor-core tile (0: not used)
-  void* d_gt;
-  alignas(64) unsigned char tm_tab[128];
+  // tensor-core Legendre stages (HPX_PLAN_TENSOR_CORES)
+  int tc_nn;           // N columns of the tensor-core tiles (0: not used)
+  void* d_gt;          // analysis operand Gt[m][group][n][32] (per transform)
+  void* d_at;          // synthesis operand At[chunk][n][32] (per transform)
+  long long* d_achunk; // [mmax+2] first At chunk of each m
+  void* d_stab;        // column lambda table: blocks of 128 pairs x 32 l
+  long long* d_stab_off;  // [mmax+1][nptile] first element of each (m, pair tile)
+  int* d_stab_lstart;  // [mmax+1][nptile] first l stored
+  int nptile;
+  long long stab_elems;
+  alignas(64) unsigned char tm_tab[128];   // TMA descriptors
   alignas(64) unsigned char tm_gt[128];
+  alignas(64) unsigned char tm_stab[128];
+  alignas(64) unsigned char tm_at[128];
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
   size_t bytes;
 };
@@ -117,6 +125,23 @@ cudaError_t allow_max_smem(F* func) {
   return e;
 }
 
+// A recurrence value in the contraction's type.  The float case avoids the
+// double-to-float conversion instruction, which on this GPU issues to the same
+// scarce FP64 pipe as the recurrence: sign, exponent and top 24 significand
+// bits are moved with integer operations (rounded half up in magnitude), and
+// |x| < 2^-126 becomes 0.  |x| here is far below 2^128.  Every lambda table
+// and kernel converts with this one function, so their values agree bit for
+// bit.
+template <typename T> __device__ __forceinline__ T to_real(double x);
+template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_real<float>(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = __funnelshift_l(lo, ahi, 3) + 0x40000000u + ((lo >> 28) & 1u);
+  f = (ahi < (897u << 20)) ? 0u : (f | (hi & 0x80000000u));
+  return __uint_as_float(f);
+}
+
 __host__ __device__ inline long long alm_base(int lmax, int m) {  // index(l = 0, m); index(l, m) = alm_base + l
   return (long long)m * (2 * lmax + 1 - m) / 2;
 }
@@ -141,13 +166,18 @@ cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s);
 template <typename T>
 cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 
-// tensor-core analysis (hpx_tc.cu): plan-time operand buffer and TMA
-// descriptors; per launch of up to tc_channels_per_launch channels from b0,
-// the operand pack (from the ring spectra) and then the tile kernel
+// tensor-core Legendre stages (hpx_tc.cu): plan-time column table, operand
+// buffers and TMA descriptors; per launch of up to tc_channels_per_launch
+// channels from b0, an operand pack and then the tile kernel.  The analysis
+// pack reads the ring spectra and the tile kernel writes alm; the synthesis
+// pack reads alm and the tile kernel writes the ring workspace d_F.
 int tc_columns(int nbatch);  // N of the tile for a plan of nbatch channels
-cudaError_t build_tc_analysis(hpx_plan_s* p);
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch);
+cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s);
 int tc_channels_per_launch(const hpx_plan_s* p);
 cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);
 cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s);
+cudaError_t launch_pack_at_tc(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s);
+cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s);
 
 }  // namespace hpx

@@ -175,21 +175,6 @@ template <> struct LaneTile<32> { static constexpr int CPL = 8, LPL = 4; };
 
 template <typename T> struct MuStride { static constexpr int v = LB + 16 / (int)sizeof(T); };
 
-// A recurrence value in the contraction's type.  The float case avoids the
-// double-to-float conversion instruction, which on this GPU issues to the same
-// scarce FP64 pipe as the recurrence: sign, exponent and top 24 significand
-// bits are moved with integer operations (rounded half up in magnitude), and
-// |x| < 2^-126 becomes 0.  |x| here is far below 2^128.
-template <typename T> __device__ __forceinline__ T to_real(double x);
-template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
-template <> __device__ __forceinline__ float to_real<float>(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned ahi = hi & 0x7fffffffu;
-  unsigned f = __funnelshift_l(lo, ahi, 3) + 0x40000000u + ((lo >> 28) & 1u);
-  f = (ahi < (897u << 20)) ? 0u : (f | (hi & 0x80000000u));
-  return __uint_as_float(f);
-}
-
 template <typename T, int CP>
 size_t analysis_smem(int nthr) {
   constexpr int C2N = 2 * CP;

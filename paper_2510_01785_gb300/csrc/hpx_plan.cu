@@ -105,7 +105,7 @@ struct DeviceGuard {
 };
 
 // Optional per-stage CUDA events (hpx_plan_set_timing).
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 struct TimingRec {
   int stage;
   cudaEvent_t a, b;
@@ -120,7 +120,8 @@ static void plan_free(hpx_plan_s* p) {
   if (!p) return;
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
-                  p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status};
+                  p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
+                  p->d_stab, p->d_stab_off, p->d_stab_lstart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->timing) {
@@ -201,8 +202,24 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
 template <typename T>
 static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, double mfac,
                                  cudaStream_t s) {
-  cudaError_t e =
-      staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), mfac, s, n); });
+  cudaError_t e = cudaSuccess;
+  if (p->tc_nn) {  // tensor cores: operand pack (stage 5), then the tile kernel (stage 2), per channel chunk
+    const int cp = tc_channels_per_launch(p);
+    for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
+      const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
+      e = staged(p, 5, s, [&](int* n) {
+        *n = 1;
+        return launch_pack_at_tc(p, static_cast<const float*>(alm), b0, nb, mfac, s);
+      });
+      if (e == cudaSuccess)
+        e = staged(p, 2, s, [&](int* n) {
+          *n = 1;
+          return launch_synthesis_tc(p, b0, nb, s);
+        });
+    }
+  } else {
+    e = staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), mfac, s, n); });
+  }
   if (e == cudaSuccess)
     e = staged(p, 3, s, [&](int* n) {
       *n = 1;
@@ -341,7 +358,7 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE))
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
-  if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc_analysis(p);
+  if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -392,9 +409,8 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
   const size_t ngroup = (npair + 31) / 32;
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
     b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ngroup;
-  if (flags & HPX_PLAN_TENSOR_CORES)  // group starts padded to the tile grid; the Gt operand
-    b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) +
-         sizeof(float) * (size_t)(mmax + 1) * ngroup * tc_columns(nbatch) * 32;
+  if (flags & HPX_PLAN_TENSOR_CORES)  // row-table starts padded to the tile grid; column table; operands
+    b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch);
   return b + sizeof(int);
 }
 

@@ -1,5 +1,5 @@
-// Tensor-core Legendre analysis for FP32 plans with a lambda table
-// (HPX_PLAN_TENSOR_CORES; Sec. III-D Eq. 14, Eq. 26-27).
+// Tensor-core Legendre stages for FP32 plans with a lambda table
+// (HPX_PLAN_TENSOR_CORES; Sec. III-D Eq. 14, Eq. 24-27).
 //
 // For one m the analysis is a matrix product over ring pairs p:
 //   D[l][n] = sum_p Lambda[l][p] Gt[n][p],
@@ -12,6 +12,13 @@
 // 128-byte swizzle atom along K) and a Gt tile (N rows x 32 floats) arrive by
 // TMA in a shared-memory ring of stages; tcgen05.mma accumulates in tensor
 // memory and tcgen05.ld brings the tile back for the epilogue (times P_l).
+//
+// The synthesis is the same product the other way round:
+//   D[p][n] = sum_l Lambda[l][p] At[n][l],
+// At holding P_l a_lm split by the parity of l - m, so that the columns give
+// E (even) and O (odd) and the rings get E + O (north) and E - O (south).
+// Its lambda tiles come from a column copy of the table, [p][l] blocks of
+// 128 pairs x 32 l, so that both operands are K-major as in the analysis.
 //
 // FP32 accuracy from TF32 products: the tensor cores read the top 19 bits of
 // each float (10 mantissa bits), i.e. hi(x) = x truncated to TF32.  With
@@ -28,6 +35,9 @@
 // memory and returns; its output rows are then left unwritten.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <climits>
+#include <vector>
 
 #include "hpx_internal.cuh"
 
@@ -186,14 +196,117 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
 // ---------------------------------------------------------------------------
 // the tile kernel
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// synthesis operands
+// ---------------------------------------------------------------------------
+// Coefficient operand At[m][j][n][32] for l = m + 32 j + (0..31): row n < 2 CP
+// holds part n%2 of P_l mfac a_lm of channel n/2 where l - m is even (0
+// elsewhere), row 2 CP + n the same for odd l - m; zero past lmax.  Only
+// Re a_l0 enters (real maps).  One warp per (m, j).
+template <int CP>
+__global__ void __launch_bounds__(128)
+k_pack_at(const float2* __restrict__ alm, const double* __restrict__ coef_p, const long long* __restrict__ achunk,
+          float* __restrict__ at, int lmax, int mmax, long long nalm, int b0, int nb, double mfac) {
+  constexpr int C2N = 2 * CP, NN = 2 * C2N;
+  const int m = blockIdx.y, j = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (m > mmax || j > (lmax - m) / 32) return;
+  const int l = m + 32 * j + lane;
+  float* out = at + (achunk[m] + j) * NN * 32 + lane;
+  const bool in = l <= lmax;
+  const bool odd = ((l - m) & 1) != 0;
+  const long long base = alm_base(lmax, m);
+  const double s = in ? coef_p[base + l] * (m > 0 ? mfac : 1.0) : 0.0;
+#pragma unroll 4
+  for (int c = 0; c < CP; ++c) {
+    float2 a = make_float2(0.f, 0.f);
+    if (in && c < nb) {
+      a = alm[(long long)(b0 + c) * nalm + base + l];
+      a = make_float2((float)(s * a.x), m == 0 ? 0.f : (float)(s * a.y));
+    }
+    const float2 e = odd ? make_float2(0.f, 0.f) : a, o = odd ? a : make_float2(0.f, 0.f);
+    out[(2 * c) * 32] = e.x;
+    out[(2 * c + 1) * 32] = e.y;
+    out[(C2N + 2 * c) * 32] = o.x;
+    out[(C2N + 2 * c + 1) * 32] = o.y;
+  }
+}
+
+// Column lambda table for the synthesis: per (m, tile T of 128 ring pairs),
+// from ls_T = the tile's first significant l (aligned down to m + 32 j) to
+// lmax, blocks of 128 pairs x 32 l, element [p][l] = the recurrence value of
+// chain (m, 128 T + p) in the same float as the row table (zero before the
+// chain's start, past lmax and for pairs past npair).
+__global__ void k_stab_tiles(const int* __restrict__ lc_tab, int lmax, int npair, int nptile, int* lstart,
+                             long long* nblk) {
+  const int T = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  if (T >= nptile) return;
+  int ls = lmax + 1;
+  for (int j = 0; j < 128; ++j) {
+    const int p = T * 128 + j;
+    if (p < npair) ls = min(ls, lc_tab[(long long)m * npair + p]);
+  }
+  if (ls <= lmax) ls = m + ((ls - m) / 32) * 32;
+  lstart[(long long)m * nptile + T] = ls;
+  nblk[(long long)m * nptile + T] = ls <= lmax ? (lmax - ls) / 32 + 1 : 0;
+}
+
+__global__ void k_stab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+                            const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
+                            const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
+                            const long long* __restrict__ off, int lmax, int npair, int nptile, float* tab) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  const int T = p >> 7;
+  if (T >= nptile) return;
+  const long long mT = (long long)m * nptile + T;
+  const int ls = lstart[mT];
+  if (ls > lmax) return;
+  const int lend = ls + ((lmax - ls) / 32 + 1) * 32;  // end of the last block
+  float* out = tab + off[mT] + (p & 127) * 32;
+  double z = 0.0, s0 = 0.0, s1 = 0.0;
+  int lc = INT_MAX;
+  if (p < npair) {
+    const long long ci = (long long)m * npair + p;
+    z = rings[p].z;
+    lc = lc_tab[ci];
+    s0 = mu0_tab[ci];
+    s1 = mu1_tab[ci];
+  }
+  const long long base = alm_base(lmax, m);
+  double mu1 = 0.0, mu2 = 0.0;
+  for (int l4 = ls; l4 < lend; l4 += 4) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int l = l4 + u;
+      float f = 0.f;
+      if (l <= lmax && p < npair) {  // the row table's recurrence, operation for operation
+        double mu = fma(coef_c[base + l] * z, mu1, -mu2);
+        if (l == lc) {
+          mu = s1;
+          mu1 = s0;
+        }
+        mu2 = mu1;
+        mu1 = mu;
+        f = to_real<float>(mu);
+      }
+      v[u] = f;
+    }
+    const int r = l4 - ls;
+    *reinterpret_cast<float4*>(out + (long long)(r >> 5) * 4096 + (r & 31)) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the tile kernels
+// ---------------------------------------------------------------------------
 template <int NN>
 struct TcShape {
   static constexpr int kA = kTcTile * 128;   // lambda tile bytes: 128 rows x 32 floats
-  static constexpr int kG = NN * 128;        // Gt tile bytes
-  static constexpr int kStage = kA + 2 * kG; // one stage: lambda tile, Gt tile, its remainder right after it
-  static constexpr int kLo = kA;             // lambda remainder buffer (two, alternating by group)
+  static constexpr int kG = NN * 128;        // B tile bytes (Gt or At)
+  static constexpr int kStage = kA + 2 * kG; // one stage: lambda tile, B tile, its remainder right after it
+  static constexpr int kLo = kA;             // lambda remainder buffer (two, alternating by K block)
   static constexpr int kNStage = (200 * 1024 - 2 * kLo) / kStage < 8 ? (200 * 1024 - 2 * kLo) / kStage : 8;
-  static constexpr int kTmemCols = 4 * NN;   // two group accumulators of 2 NN columns
+  static constexpr int kTmemCols = 4 * NN;   // two block accumulators of 2 NN columns
   static constexpr size_t kSmem =
       (size_t)kNStage * kStage + 2 * kLo + 1024 /* base alignment */ + 2048 /* barriers, lists */;
   static_assert(kNStage >= 2 && kTmemCols <= 512, "shape");
@@ -201,40 +314,57 @@ struct TcShape {
 
 constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, warp 5 issues products
 
-// One CTA: rows l0 .. l0+127 of one m, all channels of the launch.
-//
-// Per 32-pair group k, with L the lambda tile (128 x 32) and G the operand
-// tile (NN x 32) in shared memory:
-//   split: lo(L) and lo(G) are formed (hi is the hardware's TF32 truncation
+struct TcArgs {
+  const long long* off;    // analysis: row table offsets [m][group]; synthesis: column table [m][p tile]
+  const int* lstart;       // first l stored, same indexing
+  int ngroup;              // groups (analysis) or p tiles (synthesis) per m
+  const long long* achunk; // synthesis: first At chunk of each m
+  const double* coef_p;    // analysis: P_l
+  float* out;              // analysis: alm [b][nalm] complex; synthesis: F [b][nring][mmax+1] complex
+  int lmax, mmax, npair, nring;
+  long long nalm;
+  int b0, nb;
+  double mfac;
+  int* status;
+};
+
+// One CTA: a 128-row tile of one m, all channels of the launch.
+//   analysis (SYN false): rows are l = l0 .. l0+127, K runs over the 32-pair
+//     groups whose table rows reach the tile, B = Gt: D[l][n] = sum_p L G;
+//   synthesis (SYN true): rows are ring pairs p = 128 T .. 128 T + 127, K runs
+//     over 32-l chunks from the tile's first significant l, A = the column
+//     table's blocks, B = At: D[p][n] = sum_l L^T At.
+// Per K block k, with L the lambda tile (128 x 32) and B (NN x 32) in shared
+// memory:
+//   split: lo(L) and lo(B) are formed (hi is the hardware's TF32 truncation
 //          of the tile as loaded; lo = x - trunc(x), rounded to TF32);
-//          lo(G) sits right after G, so [G; lo G] is one N = 2 NN operand;
-//   products (4 steps of K = 8): D[:, 0:2NN] += L [G; lo G]^T and
-//          D[:, 0:NN] += lo(L) G^T, i.e. 8 instructions per group;
-//   drain: row l keeps D[l][j] + D[l][NN + j] for the NN/2 columns j of its
-//          parity and adds them into FP32 registers (round to nearest).
+//          lo(B) sits right after B, so [B; lo B] is one N = 2 NN operand;
+//   products (4 steps of K = 8): D[:, 0:2NN] += L [B; lo B]^T and
+//          D[:, 0:NN] += lo(L) B^T, i.e. 8 instructions per block;
+//   drain: D[r][j] + D[r][NN + j] is added into FP32 registers (round to
+//          nearest): the NN/2 columns of the row's parity (analysis) or all
+//          NN (synthesis).
 // The tensor cores add each instruction's products into the accumulator
-// with truncation, so each group is accumulated alone, in one of two TMEM
+// with truncation, so each block is accumulated alone, in one of two TMEM
 // buffers (2 NN columns each), while the other is drained.
 //
 // Roles run decoupled, linked by mbarriers: warp 4 keeps up to kNStage
-// groups of copies in flight, warp 5 issues a group's products once it is
-// split and its accumulator is free, warps 0-3 split group k and then drain
-// group k-1.  After an expired wait a role stops working (the split/drain
+// blocks of copies in flight, warp 5 issues a block's products once it is
+// split and its accumulator is free, warps 0-3 split block k and then drain
+// block k-1.  After an expired wait a role stops working (the split/drain
 // warps keep looping without work, so their warp-collective tcgen05.ld stays
 // convergent), waits for what it started, and the CTA records the timeout.
-template <int NN>
+template <int NN, bool SYN>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmG,
-              const long long* __restrict__ tab_off, const int* __restrict__ lstart, int ngroup,
-              const double* __restrict__ coef_p, float* __restrict__ alm, int lmax, long long nalm, int b0, int nb,
-              double mfac, int* __restrict__ status) {
+k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   using S = TcShape<NN>;
   constexpr int NS = S::kNStage, C2N = NN / 2;
+  constexpr int NSUM = SYN ? NN : C2N;
   static_assert(NN % 32 == 0 && NN <= 128, "N tile");
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m = blockIdx.y;
-  const int l0 = m + kTcTile * blockIdx.x;
-  if (l0 > lmax) return;  // whole CTA, before any shared state
+  const int l0 = m + kTcTile * blockIdx.x;  // analysis tile
+  if (!SYN && l0 > a.lmax) return;          // whole CTA, before any shared state
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* tiles = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -242,17 +372,17 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   uint64_t* full = reinterpret_cast<uint64_t*>(lobuf + 2 * S::kLo);
   uint64_t* conv = full + NS;   // stage split (128 arrivals)
   uint64_t* empty = conv + NS;  // stage's products done
-  uint64_t* accf = empty + NS;  // [2] group accumulator complete
-  uint64_t* acce = accf + 2;    // [2] group accumulator drained (128 arrivals)
+  uint64_t* accf = empty + NS;  // [2] block accumulator complete
+  uint64_t* acce = accf + 2;    // [2] block accumulator drained (128 arrivals)
   uint64_t* done = acce + 2;    // all products done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* wcount = reinterpret_cast<int*>(tmem_slot + 2);  // [4]
-  int* rowA = wcount + 4;   // [128] TMA row of the lambda tile of active group k
-  int* rowG = rowA + 128;   // [128] TMA row of its Gt tile
+  int* rowA = wcount + 4;   // analysis: [128] TMA row of the lambda tile of active group k
+  int* rowB = rowA + 128;   // analysis: [128] TMA row of its Gt tile
   auto sL = [&](int s) { return tiles + (size_t)s * S::kStage; };
-  auto sG = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA; };
-  auto sGlo = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA + S::kG; };
+  auto sB = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA; };
+  auto sBlo = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA + S::kG; };
   auto sLlo = [&](int b) { return lobuf + (size_t)b * S::kLo; };
 
   if (warp == 0) {
@@ -260,22 +390,33 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                  "r"(S::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // groups whose rows reach this tile (group starts lie on the tile grid
-  // m + 128 j, so a group covers the whole tile or starts after it), with
-  // their copy coordinates, compacted in group order
+  // K blocks.  Analysis: groups whose rows reach this tile (group starts lie
+  // on the tile grid m + 128 j, so a group covers the whole tile or starts
+  // after it), with their copy coordinates, compacted in group order.
+  // Synthesis: every 32-l chunk from the tile's first stored l.
   bool act = false;
-  int ra = 0, rg = 0;
+  int ra = 0, rb = 0;
   unsigned bal = 0;
-  if (warp < 4) {
-    if (t < ngroup) {
-      const long long mg = (long long)m * ngroup + t;
-      const int ls = lstart[mg];
+  if (!SYN && warp < 4) {
+    if (t < a.ngroup) {
+      const long long mg = (long long)m * a.ngroup + t;
+      const int ls = a.lstart[mg];
       act = ls <= l0;
-      ra = (int)(tab_off[mg] / 32) + (l0 - ls);
-      rg = (int)(mg * NN);
+      ra = (int)(a.off[mg] / 32) + (l0 - ls);
+      rb = (int)(mg * NN);
     }
     bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) wcount[warp] = __popc(bal);
+  }
+  int na = 0, ra0 = 0, rb0 = 0;  // synthesis: block count, first rows
+  if (SYN) {
+    const long long mT = (long long)m * a.ngroup + blockIdx.x;
+    const int ls = a.lstart[mT];
+    if (ls <= a.lmax) {
+      na = (a.lmax - ls) / 32 + 1;
+      ra0 = (int)(a.off[mT] / 32);
+      rb0 = (int)((a.achunk[m] + (ls - m) / 32) * NN);
+    }
   }
   if (t == 32) {
     for (int s = 0; s < NS; ++s) {
@@ -294,27 +435,29 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (act) {
-    int off = 0;
-    for (int w = 0; w < warp; ++w) off += wcount[w];
-    const int k = off + __popc(bal & ((1u << lane) - 1u));
-    rowA[k] = ra;
-    rowG[k] = rg;
+  if (!SYN) {
+    if (act) {
+      int off = 0;
+      for (int w = 0; w < warp; ++w) off += wcount[w];
+      const int k = off + __popc(bal & ((1u << lane) - 1u));
+      rowA[k] = ra;
+      rowB[k] = rb;
+    }
+    na = wcount[0] + wcount[1] + wcount[2] + wcount[3];
   }
-  const int na = wcount[0] + wcount[1] + wcount[2] + wcount[3];
   const uint32_t tmem = *tmem_slot;
   __syncthreads();
 
   if (warp == 4) {
-    // ---- copies: group k into stage k % NS once group k - NS's products are done
+    // ---- copies: block k into stage k % NS once block k - NS's products are done
     int issued = 0;
     if (lane == 0) {
       for (int k = 0; k < na; ++k) {
         const int s = k % NS;
         if (k >= NS && !wait_phase(&empty[s], (uint32_t)(k / NS - 1) & 1u, abort_flag, true)) break;
         mbar_expect_tx(&full[s], S::kA + S::kG);
-        tma_load_2d(sL(s), &tmA, 0, rowA[k], &full[s]);
-        tma_load_2d(sG(s), &tmG, 0, rowG[k], &full[s]);
+        tma_load_2d(sL(s), &tmA, 0, SYN ? ra0 + k * 128 : rowA[k], &full[s]);
+        tma_load_2d(sB(s), &tmB, 0, SYN ? rb0 + k * NN : rowB[k], &full[s]);
         issued = k + 1;
       }
       // whatever was started completes before the CTA moves on
@@ -334,12 +477,12 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if (k >= 2 && !wait_phase(&acce[b], (uint32_t)((k - 2) >> 1) & 1u, abort_flag, true)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(b * 2 * NN);
-        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(b)), aG = smem_u32(sG(s));
+        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(b)), aB = smem_u32(sB(s));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {  // K = 8 floats (32 bytes) per instruction
           const uint32_t off = 32u * j;
-          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aG + off), id2, j > 0 ? 1u : 0u);
-          umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aG + off), id1, 1u);
+          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id2, j > 0 ? 1u : 0u);
+          umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
         }
         umma_commit(&empty[s]);
         umma_commit(&accf[b]);
@@ -351,27 +494,39 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       }
     }
   } else {
-    // ---- split and drain (thread t owns TMEM lane t = row l0 + t)
+    // ---- split and drain (thread t owns TMEM lane t = row t of the tile)
     const int l = l0 + t;
     const bool odd = ((l - m) & 1) != 0;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    float sum[C2N];
+    float sum[NSUM];
 #pragma unroll
-    for (int j = 0; j < C2N; ++j) sum[j] = 0.f;
+    for (int j = 0; j < NSUM; ++j) sum[j] = 0.f;
     auto drain = [&](int buf) {  // warp-collective
       const uint32_t c0 = trow + (uint32_t)(buf * 2 * NN);
+      if constexpr (SYN) {
 #pragma unroll
-      for (int q = 0; q < C2N / 16; ++q) {
-        uint32_t s1[16], s2[16], a1[16], a2[16];
-        tmem_ld16(c0 + (uint32_t)(q * 16), s1);
-        tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
-        tmem_ld16(c0 + (uint32_t)(C2N + q * 16), a1);
-        tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
-        tmem_wait_ld();
+        for (int q = 0; q < NN / 16; ++q) {
+          uint32_t v1[16], v2[16];
+          tmem_ld16(c0 + (uint32_t)(q * 16), v1);
+          tmem_ld16(c0 + (uint32_t)(NN + q * 16), v2);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          sum[q * 16 + j] += odd ? __uint_as_float(a1[j]) + __uint_as_float(a2[j])
-                                 : __uint_as_float(s1[j]) + __uint_as_float(s2[j]);
+          for (int j = 0; j < 16; ++j) sum[q * 16 + j] += __uint_as_float(v1[j]) + __uint_as_float(v2[j]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < C2N / 16; ++q) {
+          uint32_t s1[16], s2[16], a1[16], a2[16];
+          tmem_ld16(c0 + (uint32_t)(q * 16), s1);
+          tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
+          tmem_ld16(c0 + (uint32_t)(C2N + q * 16), a1);
+          tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            sum[q * 16 + j] += odd ? __uint_as_float(a1[j]) + __uint_as_float(a2[j])
+                                   : __uint_as_float(s1[j]) + __uint_as_float(s2[j]);
+        }
       }
     };
     bool alive = true;
@@ -381,20 +536,20 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       if (alive) {
         // elementwise, so the swizzle does not matter; consecutive threads
         // take consecutive 16-byte words.  Remainder buffer b was last read
-        // by group k-2's products, complete since this thread drained that
-        // group in the previous iteration.
-        const float4* a = reinterpret_cast<const float4*>(sL(s));
-        float4* alo = reinterpret_cast<float4*>(sLlo(b));
+        // by block k-2's products, complete since this thread drained that
+        // block in the previous iteration.
+        const float4* x = reinterpret_cast<const float4*>(sL(s));
+        float4* xlo = reinterpret_cast<float4*>(sLlo(b));
 #pragma unroll
-        for (int j = 0; j < S::kA / 2048; ++j) alo[j * 128 + t] = tf32_rem4(a[j * 128 + t]);
-        const float4* gg = reinterpret_cast<const float4*>(sG(s));
-        float4* glo = reinterpret_cast<float4*>(sGlo(s));
+        for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
+        const float4* y = reinterpret_cast<const float4*>(sB(s));
+        float4* ylo = reinterpret_cast<float4*>(sBlo(s));
 #pragma unroll
-        for (int j = 0; j < S::kG / 2048; ++j) glo[j * 128 + t] = tf32_rem4(gg[j * 128 + t]);
+        for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
       }
-      if (k >= 1) {  // drain group k-1 while group k's products run
+      if (k >= 1) {  // drain block k-1 while block k's products run
         bool ok = alive && wait_phase(&accf[b ^ 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
@@ -407,7 +562,7 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       }
     }
-    if (na > 0) {  // the last group
+    if (na > 0) {  // the last block
       bool ok = alive && wait_phase(&accf[(na - 1) & 1], (uint32_t)((na - 1) >> 1) & 1u, abort_flag, true);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
@@ -420,16 +575,36 @@ k_analysis_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // results are written only if no wait expired anywhere in the CTA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (*abort_flag == 0 && l <= lmax) {
-      const long long base = alm_base(lmax, m);
-      const double scale = coef_p[base + l] * (m > 0 ? mfac : 1.0);
-      float2* out = reinterpret_cast<float2*>(alm) + (long long)b0 * nalm + base + l;
+    if (*abort_flag == 0) {
+      if constexpr (SYN) {
+        // north ring p: E + O; its mirror (none for the equator): E - O
+        const int p = blockIdx.x * 128 + t;
+        if (p < a.npair) {
+          const int ys = p == a.npair - 1 ? -1 : a.nring - 1 - p;
+          float2* F = reinterpret_cast<float2*>(a.out);
+          const long long mstride = a.mmax + 1;
 #pragma unroll
-      for (int c = 0; c < C2N / 2; ++c)
-        if (c < nb)
-          out[(long long)c * nalm] = make_float2((float)(scale * sum[2 * c]), (float)(scale * sum[2 * c + 1]));
+          for (int c = 0; c < C2N / 2; ++c) {
+            if (c < a.nb) {
+              const float er = sum[2 * c], ei = sum[2 * c + 1], orr = sum[C2N + 2 * c], oi = sum[C2N + 2 * c + 1];
+              const long long fb = (long long)(a.b0 + c) * a.nring;
+              F[(fb + p) * mstride + m] = make_float2(er + orr, ei + oi);
+              if (ys >= 0) F[(fb + ys) * mstride + m] = make_float2(er - orr, ei - oi);
+            }
+          }
+        }
+      } else if (l <= a.lmax) {
+        const long long base = alm_base(a.lmax, m);
+        const double scale = a.coef_p[base + l] * (m > 0 ? a.mfac : 1.0);
+        float2* out = reinterpret_cast<float2*>(a.out) + (long long)a.b0 * a.nalm + base + l;
+#pragma unroll
+        for (int c = 0; c < C2N / 2; ++c)
+          if (c < a.nb)
+            out[(long long)c * a.nalm] =
+                make_float2((float)(scale * sum[2 * c]), (float)(scale * sum[2 * c + 1]));
+      }
     }
-    if (*abort_flag != 0 && t == 0) atomicExch(status, (int)HPX_ERR_TIMEOUT);
+    if (*abort_flag != 0 && t == 0) atomicExch(a.status, (int)HPX_ERR_TIMEOUT);
     __syncthreads();
     if (warp == 0)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
@@ -467,6 +642,26 @@ bool encode_rows32(void* out, const void* base, unsigned long long rows, unsigne
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double mfac) {
+  TcArgs a;
+  a.off = syn ? p->d_stab_off : p->d_tab_off;
+  a.lstart = syn ? p->d_stab_lstart : p->d_tab_lstart;
+  a.ngroup = syn ? p->nptile : p->ngroup;
+  a.achunk = p->d_achunk;
+  a.coef_p = p->d_coef_p;
+  a.out = out;
+  a.lmax = p->lmax;
+  a.mmax = p->mmax;
+  a.npair = p->npair;
+  a.nring = p->nring;
+  a.nalm = p->nalm;
+  a.b0 = b0;
+  a.nb = nb;
+  a.mfac = mfac;
+  a.status = p->d_status;
+  return a;
+}
+
 template <int CP>
 cudaError_t launch_pack_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
   k_pack_gt<CP><<<dim3((p->ngroup + 3) / 4, p->mmax + 1), 128, 0, s>>>(
@@ -476,16 +671,23 @@ cudaError_t launch_pack_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cuda
 }
 
 template <int CP>
-cudaError_t launch_tile_cp(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+cudaError_t launch_pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  const int nchunk0 = p->lmax / 32 + 1;  // chunks of m = 0, the most
+  k_pack_at<CP><<<dim3((nchunk0 + 3) / 4, p->mmax + 1), 128, 0, s>>>(
+      (const float2*)alm, p->d_coef_p, p->d_achunk, (float*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, mfac);
+  return cudaGetLastError();
+}
+
+template <int CP, bool SYN>
+cudaError_t launch_tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
   constexpr int NN = 4 * CP;
-  cudaError_t e = allow_max_smem(k_analysis_tc<NN>);
+  cudaError_t e = allow_max_smem(k_legendre_tc<NN, SYN>);
   if (e != cudaSuccess) return e;
-  const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(p->tm_tab);
-  const CUtensorMap* tmG = reinterpret_cast<const CUtensorMap*>(p->tm_gt);
-  const dim3 tiles((p->lmax + kTcTile) / kTcTile, p->mmax + 1);
-  k_analysis_tc<NN><<<tiles, kTcThreads, TcShape<NN>::kSmem, s>>>(*tmA, *tmG, p->d_tab_off, p->d_tab_lstart, p->ngroup,
-                                                          p->d_coef_p, alm, p->lmax, p->nalm, b0, nb, mfac,
-                                                          p->d_status);
+  const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_stab : p->tm_tab);
+  const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_at : p->tm_gt);
+  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, p->mmax + 1);
+  k_legendre_tc<NN, SYN><<<grid, kTcThreads, TcShape<NN>::kSmem, s>>>(*tmA, *tmB,
+                                                                       tc_args(p, SYN, out, b0, nb, mfac));
   return cudaGetLastError();
 }
 
@@ -497,22 +699,84 @@ int tc_columns(int nbatch) {
   return 4 * cp;
 }
 
-cudaError_t build_tc_analysis(hpx_plan_s* p) {
+int tc_channels_per_launch(const hpx_plan_s* p) { return p->tc_nn / 4; }
+
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch) {
+  const size_t npair = 2 * (size_t)nside, ngroup = (npair + 31) / 32, nptile = (npair + 127) / 128;
+  const size_t nn = (size_t)tc_columns(nbatch);
+  size_t chunks = 0;
+  for (int m = 0; m <= mmax; ++m) chunks += (size_t)((lmax - m) / 32 + 1);
+  return sizeof(float) * (size_t)(mmax + 1) * ngroup * nn * 32     // Gt
+         + sizeof(float) * chunks * nn * 32                         // At
+         + sizeof(float) * chunks * nptile * 128 * 32               // column table (upper bound)
+         + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * nptile + sizeof(long long) * (mmax + 2);
+}
+
+cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   const int nn = tc_columns(p->nbatch);
-  const size_t elems = (size_t)(p->mmax + 1) * p->ngroup * nn * 32;
+  // analysis operand
+  size_t elems = (size_t)(p->mmax + 1) * p->ngroup * nn * 32;
   cudaError_t e = cudaMalloc(&p->d_gt, elems * sizeof(float));
   if (e != cudaSuccess) return e;
   p->bytes += elems * sizeof(float);
+  // synthesis operand: chunk offsets of each m, then At
+  std::vector<long long> ach(p->mmax + 2);
+  ach[0] = 0;
+  for (int m = 0; m <= p->mmax; ++m) ach[m + 1] = ach[m] + (p->lmax - m) / 32 + 1;
+  e = cudaMalloc((void**)&p->d_achunk, sizeof(long long) * (p->mmax + 2));
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(long long) * (p->mmax + 2);
+  e = cudaMemcpy(p->d_achunk, ach.data(), sizeof(long long) * (p->mmax + 2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  elems = (size_t)ach[p->mmax + 1] * nn * 32;
+  e = cudaMalloc(&p->d_at, elems * sizeof(float));
+  if (e != cudaSuccess) return e;
+  p->bytes += elems * sizeof(float);
+  // column table
+  p->nptile = (p->npair + 127) / 128;
+  const long long nent = (long long)(p->mmax + 1) * p->nptile;
+  e = cudaMalloc((void**)&p->d_stab_lstart, sizeof(int) * nent);
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(int) * nent;
+  e = cudaMalloc((void**)&p->d_stab_off, sizeof(long long) * nent);
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(long long) * nent;
+  k_stab_tiles<<<dim3((p->nptile + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, p->nptile,
+                                                                           p->d_stab_lstart, p->d_stab_off);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  std::vector<long long> off(nent);
+  e = cudaMemcpy(off.data(), p->d_stab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  long long acc = 0;
+  for (long long i = 0; i < nent; ++i) {
+    const long long nb = off[i];
+    off[i] = acc;
+    acc += nb * 128 * 32;
+  }
+  p->stab_elems = acc;
+  e = cudaMemcpy(p->d_stab_off, off.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&p->d_stab, sizeof(float) * (acc > 0 ? acc : 32));
+  if (e != cudaSuccess) return e;
+  p->bytes += sizeof(float) * (acc > 0 ? acc : 32);
+  k_stab_fill<<<dim3(p->nptile, p->mmax + 1), 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
+                                                           p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair,
+                                                           p->nptile, static_cast<float*>(p->d_stab));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned long long at_rows = (unsigned long long)ach[p->mmax + 1] * nn;
   if (!encode_rows32(p->tm_tab, p->d_tab, (unsigned long long)(p->tab_elems / 32), kTcTile) ||
-      !encode_rows32(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * nn, nn)) {
+      !encode_rows32(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * nn, nn) ||
+      !encode_rows32(p->tm_stab, p->d_stab, (unsigned long long)(acc > 0 ? acc / 32 : 1), 128) ||
+      !encode_rows32(p->tm_at, p->d_at, at_rows, nn)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return cudaErrorInvalidValue;
   }
   p->tc_nn = nn;
   return cudaSuccess;
 }
-
-int tc_channels_per_launch(const hpx_plan_s* p) { return p->tc_nn / 4; }
 
 cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
   switch (p->tc_nn) {
@@ -525,9 +789,28 @@ cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_w, cuda
 
 cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
   switch (p->tc_nn) {
-    case 32: return launch_tile_cp<8>(p, alm, b0, nb, mfac, s);
-    case 64: return launch_tile_cp<16>(p, alm, b0, nb, mfac, s);
-    case 128: return launch_tile_cp<32>(p, alm, b0, nb, mfac, s);
+    case 32: return launch_tile_cp<8, false>(p, alm, b0, nb, mfac, s);
+    case 64: return launch_tile_cp<16, false>(p, alm, b0, nb, mfac, s);
+    case 128: return launch_tile_cp<32, false>(p, alm, b0, nb, mfac, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pack_at_tc(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  switch (p->tc_nn) {
+    case 32: return launch_pack_at_cp<8>(p, alm, b0, nb, mfac, s);
+    case 64: return launch_pack_at_cp<16>(p, alm, b0, nb, mfac, s);
+    case 128: return launch_pack_at_cp<32>(p, alm, b0, nb, mfac, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s) {
+  float* F = static_cast<float*>(p->d_F);
+  switch (p->tc_nn) {
+    case 32: return launch_tile_cp<8, true>(p, F, b0, nb, 1.0, s);
+    case 64: return launch_tile_cp<16, true>(p, F, b0, nb, 1.0, s);
+    case 128: return launch_tile_cp<32, true>(p, F, b0, nb, 1.0, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,4 +1,4 @@
-"""Tensor-core (tcgen05, 3xTF32) Legendre analysis against the FP64 oracle
+"""Tensor-core (tcgen05, 3xTF32) Legendre stages against the FP64 oracle
 and against the CUDA-core path on the same table.
 
 The tensor-core plan computes the same sums as the CUDA-core FP32 path, in a
@@ -51,7 +51,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"ns{c[0]}-l{c[1]}-m{c[2]}-b{c[3]}" for c in CASES])
-def test_tensor_core_analysis_parity(case):
+def test_tensor_core_parity(case):
     nside, lmax, mmax, nb = case
     maps = syn.white_maps(syn.SEED_BASE + 300 + nside, nside, nb).astype(np.float32)
     alm = syn.gaussian_alm(syn.SEED_BASE + 400 + nside, lmax, mmax, nb, power=1.0).astype(np.complex64)
@@ -60,13 +60,14 @@ def test_tensor_core_analysis_parity(case):
     with h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc, \
             h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True) as pt:
         dm, da = torch.from_numpy(maps).cuda(), torch.from_numpy(alm).cuda()
-        got = {"map2alm": pc.map2alm(dm), "alm2map_adjoint": pc.alm2map_adjoint(dm),
-               "alm2map": pc.alm2map(da)}
-        cuda_core = {"map2alm": pt.map2alm(dm), "alm2map_adjoint": pt.alm2map_adjoint(dm)}
+        ops = (("map2alm", dm), ("alm2map_adjoint", dm), ("alm2map", da), ("map2alm_adjoint", da))
+        got = {k: getattr(pc, k)(x) for k, x in ops}
+        cuda_core = {k: getattr(pt, k)(x) for k, x in ops}
         pc.device_status()
         ref = {"map2alm": oracle.map2alm(m64, lmax, mmax),
                "alm2map_adjoint": oracle.alm2map_adjoint(m64, lmax, mmax),
-               "alm2map": oracle.alm2map(a64, nside, lmax, mmax)}
+               "alm2map": oracle.alm2map(a64, nside, lmax, mmax),
+               "map2alm_adjoint": oracle.map2alm_adjoint(a64, nside, lmax, mmax)}
         for k, v in got.items():
             e = rel_err(v.cpu().numpy(), ref[k])
             assert e <= 1e-5, (k, e)
@@ -79,17 +80,20 @@ def test_tensor_core_analysis_parity(case):
 
 
 def test_tensor_core_gradient_scaling():
-    """The adjoint-with-gradient entry point (m > 0 doubled) runs through the
-    same tile kernel: it matches the CUDA-core table plan."""
+    """The gradient entry points (m > 0 doubled on the way out of the
+    analysis, halved on the way into the synthesis) run through the same tile
+    kernels: they match the CUDA-core table plan."""
     nside, lmax, nb = 64, 191, 3
     maps = torch.from_numpy(syn.white_maps(91, nside, nb).astype(np.float32)).cuda()
+    alm = torch.from_numpy(syn.gaussian_alm(93, lmax, lmax, nb).astype(np.complex64)).cuda()
     h = hpx()
     with h.Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc, \
             h.Plan(nside, lmax, lmax, nb, "f32", lambda_table=True) as pt:
-        g1 = pc.alm2map_grad(maps)
-        g2 = pt.alm2map_grad(maps)
-        torch.cuda.synchronize()
-        assert rel_err(g1.cpu().numpy(), g2.cpu().numpy()) <= 1e-5
+        for op, x in (("alm2map_grad", maps), ("map2alm_grad", alm)):
+            g1 = getattr(pc, op)(x)
+            g2 = getattr(pt, op)(x)
+            torch.cuda.synchronize()
+            assert rel_err(g1.cpu().numpy(), g2.cpu().numpy()) <= 1e-5, op
 
 
 def test_tensor_core_deterministic_and_status():
@@ -98,28 +102,42 @@ def test_tensor_core_deterministic_and_status():
     with hpx().Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc:
         a1 = pc.map2alm(maps).clone()
         a2 = pc.map2alm(maps)
+        s1 = pc.alm2map(a1).clone()
+        s2 = pc.alm2map(a1)
         pc.device_status()
-        assert torch.equal(a1, a2)
+        assert torch.equal(a1, a2) and torch.equal(s1, s2)
         host = pc.map2alm_host(maps.cpu().numpy())
         assert np.array_equal(host.numpy(), a1.cpu().numpy())
+        host = pc.alm2map_host(a1.cpu().numpy())
+        assert np.array_equal(host.numpy(), s1.cpu().numpy())
 
 
 NS2, L2, B2 = 1024, 3071, 8
 
 
 def test_cfg2_tensor_core_sampled():
-    """Nside 1024, lmax 3071, 8 channels: sampled coefficients against the
-    oracle, and the whole output against the CUDA-core table plan."""
+    """Nside 1024, lmax 3071, 8 channels: sampled coefficients and rings
+    against the oracle, and whole outputs against the CUDA-core table plan."""
     maps = syn.white_maps(syn.SEED_BASE + 2, NS2, B2).astype(np.float32)
+    alm_in = syn.gaussian_alm(syn.SEED_BASE + 3, L2, L2, B2, power=2.0).astype(np.complex64)
     h = hpx()
-    dm = torch.from_numpy(maps).cuda()
+    dm, da = torch.from_numpy(maps).cuda(), torch.from_numpy(alm_in).cuda()
     with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True, tensor_cores=True) as pc:
         a = pc.map2alm(dm)
+        smap = pc.alm2map(da)
         pc.device_status()
-        a = a.cpu().numpy()
+        a, smap = a.cpu().numpy(), smap.cpu().numpy()
     with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True) as pt:
         b = pt.map2alm(dm).cpu().numpy()
+        bmap = pt.alm2map(da).cpu().numpy()
     assert rel_err(a, b) <= 1e-5
+    assert rel_err(smap, bmap) <= 1e-5
+    R = 4 * NS2 - 1
+    rings = np.array([0, 1, 2, 127, 128, 511, 1023, 1500, 2047, 3070, R - 2, R - 1], np.int32)
+    ref = oracle.synthesis_sep(alm_in.astype(np.complex128), NS2, L2, L2, rings)
+    g = oracle.ring_geometry(NS2)
+    got = np.concatenate([smap[:, g["start"][y]: g["start"][y] + g["nphi"][y]] for y in rings], axis=1)
+    assert rel_err(got, ref) <= 1e-5
     ms = [0, 1, 2, 127, 128, 1024, 2047, 3000, 3071]
     ls, mm = [], []
     r = syn.rng(78)
