@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "SHT analysis+synthesis per s at Nside 1024 vs roofline; serving p50/p99 latency"
 UNIT = "analysis+synthesis/s"
 NSIDE, LMAX, MMAX, NBATCH = 1024, 3071, 3071, 8
+MIXED_NSIDE, MIXED_LMAX, MIXED_NBATCH = 1024, 2047, 64  # the mixed-precision workload
 WORKLOAD = "healpix-sht-nside1024-lmax3071-b8-f32"
 SEED = 2510017850 + 2
 
@@ -63,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run (config 5)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run (config 3)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-drain", type=float, default=15.0)
@@ -312,6 +314,12 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = measure_e2e(plan, maps, alm_in, dist, dev, args.steps, world)
 
+    mixed = None
+    if not args.no_mixed:
+        plan.close()
+        torch.cuda.empty_cache()
+        mixed = run_mixed(args, dist, dev, world, gpu_index)
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
         plan.close()
@@ -335,7 +343,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "serving": serving,
+                "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "significant_triples": active, "all_triples": total},
                 "cuda_core_table": {"value": cc["value"], "ms_per_step": cc["t_max"] / args.steps,
@@ -523,6 +531,60 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
     out["sustainable_point"] = {"offered_rps": len(sreqs) / duration, "wall_s": swall, "batches": ssrv.batches,
                                 "transforms_per_s": sum(r.nch for r in sreqs if r.t_done is not None) / swall,
                                 **srep}
+    return out
+
+
+MIXED_MODES = ("f32", "bf16", "bf16x3", "fp16", "fp16x3")
+
+
+def run_mixed(args, dist, dev, world, gpu_index) -> dict:
+    """The mixed-precision workload (Nside 1024, lmax 2047, 64 channels,
+    per-channel scales in [1e-2, 1e3], coefficient variance (l+1)^-3): one
+    step (map2alm + alm2map) per mode, the FP32 tensor-core plan first; each
+    16-bit mode's outputs are compared with the FP32 ones on the same inputs."""
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import synthetic as syn
+
+    ns, lmax, nb = MIXED_NSIDE, MIXED_LMAX, MIXED_NBATCH
+    sc = syn.channel_scales(SEED + 30, nb)
+    alm_np = syn.gaussian_alm(SEED + 31, lmax, lmax, nb, power=3.0, scales=sc).astype(np.complex64)
+    alm_in = torch.from_numpy(alm_np).to(dev)
+    out = {"config": {"workload": f"healpix-sht-nside{ns}-lmax{lmax}-b{nb}-mixed", "nside": ns, "lmax": lmax,
+                      "nbatch": nb, "inputs": "alm N(0,(l+1)^-3) x channel scale U(1e-2,1e3); "
+                                              "maps = their FP32 synthesis"},
+           "modes": {}}
+    ref = None
+    maps = None
+    for mode in MIXED_MODES:
+        kw = dict(lambda_table=True, tensor_cores=True) if mode == "f32" else {}
+        plan = hpx.Plan(ns, lmax, lmax, nb, mode, device=dev, **kw)
+        if maps is None:
+            maps = plan.alm2map(alm_in)
+        a = plan.map2alm(maps)
+        s = plan.alm2map(alm_in)
+        torch.cuda.synchronize(dev)
+        rec = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
+        plan.device_status()
+        r = {"value": rec["value"], "unit": UNIT, "ms_per_step": rec["t_max"] / args.steps,
+             "stages": rec["stages"], "table_bytes": plan.table_bytes,
+             "column_table_bytes": plan.column_table_bytes, "clocks": rec["clocks"]}
+        if ref is None:
+            ref = (a.clone(), s.clone())
+        else:
+            def err(x, y):
+                d = (x - y).abs().pow(2).sum(dim=1).sqrt() / y.abs().pow(2).sum(dim=1).sqrt().clamp_min(1e-300)
+                return float(d.max())
+            r["rel_l2_vs_f32"] = {"map2alm": err(a, ref[0]), "alm2map": err(s, ref[1])}
+        out["modes"][mode] = r
+        del a, s
+        plan.close()
+        torch.cuda.empty_cache()
+    f32 = out["modes"]["f32"]["ms_per_step"]
+    for mode, r in out["modes"].items():
+        r["speedup_vs_f32"] = f32 / r["ms_per_step"]
     return out
 
 

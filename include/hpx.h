@@ -59,9 +59,19 @@ typedef struct hpx_plan_s* hpx_plan;
  *   HPX_F64        double maps/coefficients, FP64 contraction.
  *   HPX_F32        float maps/coefficients, FP32 contraction; lambda_lm still
  *                  comes from the FP64 recurrence.
- *   HPX_F32_BF16 / HPX_F32_FP16     float I/O, the ring x lambda contraction
- *                  on tensor cores in BF16 / FP16 with FP32 accumulation.
- *   HPX_F32_BF16X3 / HPX_F32_FP16X3 the same with split hi+lo products. */
+ *   HPX_F32_BF16 / HPX_F32_FP16     float I/O (ring transforms in FP32);
+ *                  both Legendre stages on tensor cores from plan-resident
+ *                  BF16 / FP16 lambda tables (rounded from the FP64
+ *                  recurrence) and BF16 / FP16 operands, FP32 accumulation.
+ *                  FP16 operands are scaled per channel by a power of two
+ *                  (from the largest component of the channel's spectra or
+ *                  coefficients) to stay in range; the scale is undone on
+ *                  output.
+ *   HPX_F32_BF16X3 / HPX_F32_FP16X3 the same with split products: every
+ *                  value is stored as hi + lo (lo = the remainder rounded
+ *                  again) and hi*hi + hi*lo + lo*hi are accumulated.
+ * The four 16-bit dtypes always build their tables and use the tensor-core
+ * path (HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES are implied). */
 typedef enum {
   HPX_F64 = 0,
   HPX_F32 = 1,
@@ -240,8 +250,13 @@ hpx_status hpx_plan_chain_stats(hpx_plan plan, int64_t* active, int64_t* total);
 size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch,
                                hpx_dtype dtype, unsigned flags);
 
-/* Bytes of the plan-resident lambda table (0 without HPX_PLAN_LAMBDA_TABLE). */
+/* Bytes of the plan-resident lambda table (0 without HPX_PLAN_LAMBDA_TABLE);
+ * hi and lo parts together for the x3 dtypes. */
 size_t hpx_plan_table_bytes(hpx_plan plan);
+
+/* Bytes of the transposed copy of the table the tensor-core synthesis reads
+ * (0 without the tensor-core path). */
+size_t hpx_plan_column_table_bytes(hpx_plan plan);
 
 /* Status of the plan's device-side waits.  Synchronises the plan's device,
  * returns HPX_ERR_TIMEOUT if a bounded wait inside one of the plan's kernels

@@ -112,6 +112,11 @@ class Plan:
         """Bytes of the plan-resident lambda table (0 when recomputing)."""
         return int(lib().hpx_plan_table_bytes(self._h))
 
+    @property
+    def column_table_bytes(self) -> int:
+        """Bytes of the table copy the tensor-core synthesis reads (0 without it)."""
+        return int(lib().hpx_plan_column_table_bytes(self._h))
+
     # -- argument checks ----------------------------------------------------
     def _map(self, t: torch.Tensor, name: str) -> torch.Tensor:
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device):

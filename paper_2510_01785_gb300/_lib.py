@@ -42,6 +42,7 @@ SIGNATURES = {
     "hpx_plan_stage_times": (_I, [_P, _P, _P]),
     "hpx_plan_chain_stats": (_I, [_P, _P, _P]),
     "hpx_plan_table_bytes": (_SZ, [_P]),
+    "hpx_plan_column_table_bytes": (_SZ, [_P]),
     "hpx_plan_estimate_bytes": (_SZ, [_I, _I, _I, _I, _I, _U]),
     "hpx_plan_device_status": (_I, [_P]),
     "hpx_last_error": (ctypes.c_char_p, []),

@@ -4,12 +4,22 @@
 // equally spaced pixels.  A real ring of length N is transformed through a
 // complex transform of half length H = N/2 (even samples as real parts, odd
 // samples as imaginary parts).  When H is a power of two that transform is a
-// radix-2 FFT in shared memory; otherwise it is Bluestein's chirp-z transform
-// (Eq. 17-23): chirp multiply, a power-of-two circular convolution done as
-// FFT -> pointwise product with the precomputed kernel spectrum -> inverse
-// FFT, and a final chirp multiply.  One CTA handles one (ring, channel); the
-// whole transform stays in shared memory, so each stage reads its input from
-// HBM once and writes its output once.
+// power-of-two FFT in shared memory; otherwise it is Bluestein's chirp-z
+// transform (Eq. 17-23): chirp multiply, a power-of-two circular convolution
+// done as FFT -> pointwise product with the precomputed kernel spectrum ->
+// inverse FFT, and a final chirp multiply.  One CTA handles one (ring,
+// channel); the whole transform stays in shared memory, so each stage reads
+// its input from HBM once and writes its output once.  Belt rings (all of
+// length 4 nside) and cap rings are launched separately, each launch with the
+// shared memory its longest transform needs.
+//
+// The power-of-two FFT is a Stockham (self-sorting) transform: radix-8
+// passes, then one radix-4 or radix-2 pass if log2 M is not a multiple of 3,
+// natural order in and out.  Each pass reads its butterflies' inputs into
+// registers, synchronises, and writes the outputs; shared-memory element i
+// lives at i + i/8, which keeps every pass's scattered writes free of bank
+// conflicts.  One twiddle per butterfly comes from the table; its powers are
+// formed by multiplication.
 //
 // Chirp and phase angles pi r / N are reduced exactly in integers before the
 // FP64 sincospi that fills the tables.
@@ -21,8 +31,12 @@ __device__ __forceinline__ int brev(int k, int logm) {
   return (int)(__brev((unsigned)k) >> (32 - logm));
 }
 
-// Radix-2 decimation in frequency: natural order in, bit-reversed order out.
-// tw[j] = exp(-2 pi i j / 2^logtw); inv conjugates the twiddles.
+// shared-memory position of FFT element i
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ inline size_t padded_len(size_t n) { return n + n / 8 + 1; }
+
+// Radix-2 decimation in frequency (natural order in, bit-reversed order out),
+// used once per plan to transform the Bluestein kernels in FP64.
 template <typename V>
 __device__ void fft_dif(V* buf, int logm, const V* __restrict__ tw, int logtw, bool inv) {
   const int half_n = 1 << (logm - 1);
@@ -42,73 +56,171 @@ __device__ void fft_dif(V* buf, int logm, const V* __restrict__ tw, int logtw, b
   }
 }
 
-// Radix-2 decimation in time: bit-reversed order in, natural order out.
-template <typename V>
-__device__ void fft_dit(V* buf, int logm, const V* __restrict__ tw, int logtw, bool inv) {
-  const int half_n = 1 << (logm - 1);
-  for (int s = 0; s < logm; ++s) {
-    const int half = 1 << s;
-    for (int t = threadIdx.x; t < half_n; t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> s) << (s + 1)) + pos;
-      const int i1 = i0 + half;
-      V w = tw[pos << (logtw - s - 1)];
-      if (inv) w.y = -w.y;
-      const V a = buf[i0], b = cmul(buf[i1], w);
-      buf[i0] = cadd(a, b);
-      buf[i1] = csub(a, b);
+// x * (-i) (forward) or x * (+i) (inverse)
+template <bool INV, typename V> __device__ __forceinline__ V rot90(V x) {
+  return INV ? cmk<V>(-x.y, x.x) : cmk<V>(x.y, -x.x);
+}
+
+// In-register DFT of length R in {2, 4, 8} (decimation in frequency: radix-2
+// splits down to length 2), sign -1 (forward) or +1 (INV).  Natural order in
+// and out.
+template <int R, bool INV, typename V>
+__device__ __forceinline__ void dft_small(V (&v)[R]) {
+  using T = decltype(V::x);
+  if constexpr (R == 2) {
+    const V a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const V u0 = cadd(v[0], v[2]), u1 = cadd(v[1], v[3]);
+    const V w0 = csub(v[0], v[2]), w1 = rot90<INV>(csub(v[1], v[3]));
+    v[0] = cadd(u0, u1);
+    v[2] = csub(u0, u1);
+    v[1] = cadd(w0, w1);
+    v[3] = csub(w0, w1);
+  } else {
+    const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+    V u[4], w[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      u[r] = cadd(v[r], v[r + 4]);
+      w[r] = csub(v[r], v[r + 4]);
     }
-    __syncthreads();
+    // w[r] *= exp(-+ 2 pi i r / 8)
+    w[1] = INV ? cmk<V>(h * (w[1].x - w[1].y), h * (w[1].x + w[1].y))
+               : cmk<V>(h * (w[1].x + w[1].y), h * (w[1].y - w[1].x));
+    w[2] = rot90<INV>(w[2]);
+    w[3] = INV ? cmk<V>(-h * (w[3].x + w[3].y), h * (w[3].x - w[3].y))
+               : cmk<V>(h * (w[3].y - w[3].x), -h * (w[3].x + w[3].y));
+    dft_small<4, INV>(u);
+    dft_small<4, INV>(w);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[2 * r] = u[r];
+      v[2 * r + 1] = w[r];
+    }
   }
 }
 
-// DFT of length H of buf[0..H) in place, for H = 2^logm (power-of-two case,
-// result left in bit-reversed order) or via Bluestein with the kernel
-// spectrum Bk of length 2^logm (result in natural order).  E is the ring's
-// table exp(-i pi r / N), N = 2H, so the chirp exp(-pi i n^2 / H) is
+// One Stockham pass of radix R over a length-2^logm transform in shared memory
+// (positions pad8): butterfly j (j < M/R) takes elements j + r M/R, multiplies
+// element r by W^(k r) with W = exp(-+ 2 pi i / (Ns R)), k = j mod Ns, does the
+// length-R DFT and writes element r to (j - k) R + k + r Ns.  Each thread
+// handles butterflies threadIdx.x + q blockDim.x, q < Q (blockDim.x * Q * R
+// >= M).  tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1).
+template <int R, int Q, bool INV, typename V>
+__device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw) {
+  const int nb = (1 << logm) / R;
+  V v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = threadIdx.x + q * blockDim.x;
+    if (j < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = buf[pad8(j + r * nb)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = threadIdx.x + q * blockDim.x;
+    if (j < nb) {
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+        // k / (Ns R) < 1/2: inside the stored half of the table
+        V w = tw[k << (logtw - __ffs(Ns * R) + 1)];
+        if (INV) w.y = -w.y;
+        V wr = w;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          v[q][r] = cmul(v[q][r], wr);
+          if (r + 1 < R) wr = cmul(wr, w);
+        }
+      }
+      dft_small<R, INV>(v[q]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad8(base + r * Ns)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Length-2^logm FFT of buf (positions pad8), natural order in and out; needs
+// blockDim.x * 16 >= 2^logm.  Caller has synchronised after filling buf.
+template <bool INV, typename V>
+__device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw) {
+  int Ns = 1, rest = logm;
+  if (rest % 3 == 1) {
+    stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw);
+    Ns <<= 1;
+    rest -= 1;
+  } else if (rest % 3 == 2) {
+    stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw);
+    Ns <<= 2;
+    rest -= 2;
+  }
+  for (; rest > 0; rest -= 3) {
+    stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw);
+    Ns <<= 3;
+  }
+}
+
+// DFT of length H of buf[0..H) (positions pad8) in place, natural order:
+// the power-of-two FFT when H = 2^logm, else Bluestein with the kernel
+// spectrum Bk (length 2^logm, natural order, scaled 1/2^logm).  E is the
+// ring's table exp(-i pi r / N), N = 2H, so the chirp exp(-pi i n^2 / H) is
 // E[2 n^2 mod 2N].  Caller has synchronised after filling buf.
 template <typename V>
 __device__ void ring_dft(V* buf, int H, int logm, bool bluestein, const V* __restrict__ E,
                          const V* __restrict__ Bk, const V* __restrict__ tw, int logtw) {
-  // chirp index 2 n^2 mod 2N: n < H <= 8192, so 32-bit unsigned arithmetic is exact
-  const unsigned twoN = 4u * (unsigned)H;
   if (!bluestein) {
-    fft_dif(buf, logm, tw, logtw, false);
+    fft_pow2<false>(buf, logm, tw, logtw);
     return;
   }
+  // chirp index 2 n^2 mod 2N: n < H <= 8192, so 32-bit unsigned arithmetic is exact
+  const unsigned twoN = 4u * (unsigned)H;
   const int M = 1 << logm;
   for (int n = threadIdx.x; n < M; n += blockDim.x) {
-    if (n < H) buf[n] = cmul(buf[n], E[(2u * (unsigned)n * (unsigned)n) % twoN]);
-    else buf[n] = cmk<V>(0, 0);
+    if (n < H) buf[pad8(n)] = cmul(buf[pad8(n)], E[(2u * (unsigned)n * (unsigned)n) % twoN]);
+    else buf[pad8(n)] = cmk<V>(0, 0);
   }
   __syncthreads();
-  fft_dif(buf, logm, tw, logtw, false);
-  for (int j = threadIdx.x; j < M; j += blockDim.x) buf[j] = cmul(buf[j], Bk[j]);
+  fft_pow2<false>(buf, logm, tw, logtw);
+  for (int j = threadIdx.x; j < M; j += blockDim.x) buf[pad8(j)] = cmul(buf[pad8(j)], Bk[j]);
   __syncthreads();
-  fft_dit(buf, logm, tw, logtw, true);
-  for (int k = threadIdx.x; k < H; k += blockDim.x) buf[k] = cmul(buf[k], E[(2u * (unsigned)k * (unsigned)k) % twoN]);
+  fft_pow2<true>(buf, logm, tw, logtw);
+  for (int k = threadIdx.x; k < H; k += blockDim.x)
+    buf[pad8(k)] = cmul(buf[pad8(k)], E[(2u * (unsigned)k * (unsigned)k) % twoN]);
   __syncthreads();
+}
+
+// Ring of launch slot q: belt launches take y = y0 + q; cap launches take the
+// north caps 0 .. nside-2 and then the south caps 3 nside .. 4 nside - 2.
+__device__ __forceinline__ int slot_ring(int q, int caps, int nside) {
+  if (!caps) return nside - 1 + q;
+  return q < nside - 1 ? q : q + 2 * nside + 1;
 }
 
 // ---------------------------------------------------------------------------
 // analysis: real ring -> half spectrum X_y[k], k = 0..N/2 (Eq. 13)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* __restrict__ rings,
            const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab,
-           const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec) {
+           const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec, int caps, int nside) {
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int y = blockIdx.x, b = blockIdx.y;
+  const int y = slot_ring(blockIdx.x, caps, nside), b = blockIdx.y;
   const RingInfo R = rings[y];
   const int H = R.nphi >> 1, logm = R.logm;
   const bool blue = R.btab >= 0;
   const V* E = etab + R.etab;
   // (x[2n], x[2n+1]) as one complex sample z[n]
   const V* x2 = reinterpret_cast<const V*>(map + (long long)b * npix + R.start);
-  for (int n = threadIdx.x; n < H; n += blockDim.x) buf[n] = x2[n];
+  for (int n = threadIdx.x; n < H; n += blockDim.x) buf[pad8(n)] = x2[n];
   __syncthreads();
   ring_dft(buf, H, logm, blue, E, blue ? btab + R.btab : nullptr, tw, logtw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
@@ -116,8 +228,8 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   for (int k = threadIdx.x; k <= H; k += blockDim.x) {
     const int k1 = (k == H) ? 0 : k;
     const int k2 = (k == 0) ? 0 : H - k;
-    const V zk = buf[blue ? k1 : brev(k1, logm)];
-    const V zc = cconj(buf[blue ? k2 : brev(k2, logm)]);
+    const V zk = buf[pad8(k1)];
+    const V zc = cconj(buf[pad8(k2)]);
     const V e = cscale(cadd(zk, zc), (T)0.5);
     const V d = cscale(csub(zk, zc), (T)0.5);
     const V o = cmk<V>(d.y, -d.x);
@@ -132,15 +244,15 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
 // D[k] = sum_{m = k mod N} F_m e^{i m phi0} + sum_{m = -k mod N, m >= 1}
 // conj(F_m e^{i m phi0}) (the aliasing fold; m = 0 contributes Re F_0).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __restrict__ rings,
            const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab,
            const C2<T>* __restrict__ tw, int logtw, long long npix, int nring, int mmax,
-           int scale_by_weight) {
+           int scale_by_weight, int caps, int nside) {
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int y = blockIdx.x, b = blockIdx.y;
+  const int y = slot_ring(blockIdx.x, caps, nside), b = blockIdx.y;
   const RingInfo R = rings[y];
   const int N = R.nphi, H = N >> 1, logm = R.logm, sig = R.sigma;
   const unsigned twoN = 2u * (unsigned)N;  // sigma m < 2^15: 32-bit arithmetic is exact
@@ -165,41 +277,39 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
       }
-      if (lane == 0) buf[k] = acc;
+      if (lane == 0) buf[pad8(k)] = acc;
     }
   } else {
     for (int k = threadIdx.x; k <= H; k += blockDim.x) {
       V acc = cmk<V>(0, 0);
       for (int m = k; m <= mmax; m += N) acc = cadd(acc, term(m));
       for (int m = N - k; m <= mmax; m += N) acc = cadd(acc, cconj(term(m)));
-      buf[k] = acc;
+      buf[pad8(k)] = acc;
     }
   }
   __syncthreads();
   // Z[k] = (D[k] + conj D[H-k]) + i exp(2 pi i k / N) (D[k] - conj D[H-k]), k < H;
   // the ring is then z = IDFT_H(Z) with p[2n] = Re z[n], p[2n+1] = Im z[n].
+  // Computed as conj(DFT_H(conj Z)), so conj Z is stored.
   for (int k = threadIdx.x; k <= H / 2; k += blockDim.x) {
     const int kc = H - k;
-    const V dk = buf[k], dc = buf[kc];
+    const V dk = buf[pad8(k)], dc = buf[pad8(kc)];
     const V s1 = cadd(dk, cconj(dc)), d1 = csub(dk, cconj(dc));
     const V t1 = cmul(cconj(E[2 * k]), d1);
     const V zk = cmk<V>(s1.x - t1.y, s1.y + t1.x);
     if (k > 0 && kc != k) {
       const V s2 = cadd(dc, cconj(dk)), d2 = csub(dc, cconj(dk));
       const V t2 = cmul(cconj(E[2 * kc]), d2);
-      buf[kc] = cmk<V>(s2.x - t2.y, s2.y + t2.x);
+      buf[pad8(kc)] = cmk<V>(s2.x - t2.y, -(s2.y + t2.x));
     }
-    buf[k] = zk;
+    buf[pad8(k)] = cconj(zk);
   }
-  __syncthreads();
-  // IDFT_H(Z) = conj(DFT_H(conj Z))
-  for (int n = threadIdx.x; n < H; n += blockDim.x) buf[n] = cconj(buf[n]);
   __syncthreads();
   ring_dft(buf, H, logm, blue, E, blue ? btab + R.btab : nullptr, tw, logtw);
   const T sc = scale_by_weight ? (T)R.w : (T)1;
   V* out = reinterpret_cast<V*>(map + (long long)b * npix + R.start);
   for (int n = threadIdx.x; n < H; n += blockDim.x) {
-    const V r = buf[blue ? n : brev(n, logm)];
+    const V r = buf[pad8(n)];
     out[n] = cmk<V>(r.x * sc, -r.y * sc);
   }
 }
@@ -235,8 +345,7 @@ __global__ void k_build_twiddles(int logtw, C2<T>* tw) {
 
 // Bluestein kernel spectrum of the cap ring i (H = 2i not a power of two):
 // b[j] = exp(+pi i j^2 / H) for |j| < H (indices mod M), zero elsewhere;
-// stored as FFT_M(b) / M in the DIF output order, so the pointwise product
-// happens in bit-reversed order between the DIF and DIT passes.
+// stored as FFT_M(b) / M in natural order.
 template <typename T>
 __global__ void k_build_bluestein(const RingInfo* __restrict__ rings, const double2* __restrict__ tw64,
                                   int logtw, C2<T>* btab) {
@@ -260,8 +369,10 @@ __global__ void k_build_bluestein(const RingInfo* __restrict__ rings, const doub
   __syncthreads();
   fft_dif(buf, R.logm, tw64, logtw, false);
   const double inv = 1.0 / (double)M;
-  for (int j = threadIdx.x; j < M; j += blockDim.x)
-    btab[R.btab + j] = cmk<C2<T>>((T)(buf[j].x * inv), (T)(buf[j].y * inv));
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double2 v = buf[brev(k, R.logm)];  // DIF leaves frequency k at position brev(k)
+    btab[R.btab + k] = cmk<C2<T>>((T)(v.x * inv), (T)(v.y * inv));
+  }
 }
 
 template <typename T>
@@ -288,28 +399,51 @@ cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s) {
   return e;
 }
 
+// Launch shapes: the belt rings (2 nside + 1 of them, H = 2 nside) and the
+// cap rings (2 (nside - 1), H = 2i, Bluestein length up to 2^logm_max).
+struct RingLaunch {
+  int caps, nslots, logm, threads;
+};
+static int fft_threads(int logm) {  // 16 elements per thread at most, 64..512 threads
+  int t = (1 << logm) / 16;
+  if (t < 64) t = 64;
+  return t;
+}
+static RingLaunch belt_launch(const hpx_plan_s* p) {
+  int logh = 0;
+  while ((1 << logh) < 2 * p->nside) ++logh;
+  return {0, 2 * p->nside + 1, logh, fft_threads(logh)};
+}
+static RingLaunch caps_launch(const hpx_plan_s* p) {
+  return {1, 2 * (p->nside - 1), p->logm_max, fft_threads(p->logm_max)};
+}
+
 template <typename T>
 cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   using V = C2<T>;
-  const size_t smem = ((size_t(1) << p->logm_max) + 1) * sizeof(V);
   cudaError_t e = allow_max_smem(k_ring_r2c<T>);
-  if (e != cudaSuccess) return e;
-  k_ring_r2c<T><<<dim3(p->nring, p->nbatch), 256, smem, s>>>(
-      map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw,
-      p->logtw, p->npix, p->nspec);
-  return cudaGetLastError();
+  for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
+    if (e != cudaSuccess || L.nslots <= 0) continue;
+    k_ring_r2c<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
+        map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw, p->logtw,
+        p->npix, p->nspec, L.caps, p->nside);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <typename T>
 cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s) {
   using V = C2<T>;
-  const size_t smem = ((size_t(1) << p->logm_max) + 1) * sizeof(V);
   cudaError_t e = allow_max_smem(k_ring_c2r<T>);
-  if (e != cudaSuccess) return e;
-  k_ring_c2r<T><<<dim3(p->nring, p->nbatch), 256, smem, s>>>(
-      (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw,
-      p->logtw, p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0);
-  return cudaGetLastError();
+  for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
+    if (e != cudaSuccess || L.nslots <= 0) continue;
+    k_ring_c2r<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
+        (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw, p->logtw,
+        p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0, L.caps, p->nside);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template cudaError_t build_fft_tables<float>(hpx_plan_s*, cudaStream_t);

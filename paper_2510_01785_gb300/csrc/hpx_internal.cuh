@@ -78,19 +78,27 @@ struct hpx_plan_s {
   int* d_tab_lstart;   // [mmax+1][ngroup] first l stored for the group
   int ngroup;
   long long tab_elems;
-  // tensor-core Legendre stages (HPX_PLAN_TENSOR_CORES)
-  int tc_nn;           // N columns of the tensor-core tiles (0: not used)
-  void* d_gt;          // analysis operand Gt[m][group][n][32] (per transform)
-  void* d_at;          // synthesis operand At[chunk][n][32] (per transform)
+  // tensor-core Legendre stages (HPX_PLAN_TENSOR_CORES and the 16-bit dtypes)
+  int tc_nn_a, tc_nn_s;  // N columns of the analysis / synthesis tiles (0: not used)
+  int tc_mode;         // 0 FP32 (3xTF32), 1 one 16-bit product, 2 16-bit x3
+  int tc_fmt;          // 16-bit operand format: 0 FP16, 1 BF16
+  float tc_sfac_a, tc_sfac_s;  // channel-scale bound factors of the current transform
+  void* d_tab_lo;      // 16-bit x3: remainders of the row table
+  void* d_gt;          // analysis operand Gt[m][group][rows][row width] (per transform)
+  void* d_at;          // synthesis operand At[chunk][rows][row width] (per transform)
   long long* d_achunk; // [mmax+2] first At chunk of each m
-  void* d_stab;        // column lambda table: blocks of 128 pairs x 32 l
+  unsigned* d_bmax;    // [nbatch] 16-bit modes: largest operand component per channel
+  void* d_stab;        // column lambda table: blocks of 128 pairs x (32 or 64) l
+  void* d_stab_lo;     // 16-bit x3: its remainders
   long long* d_stab_off;  // [mmax+1][nptile] first element of each (m, pair tile)
   int* d_stab_lstart;  // [mmax+1][nptile] first l stored
   int nptile;
   long long stab_elems;
   alignas(64) unsigned char tm_tab[128];   // TMA descriptors
+  alignas(64) unsigned char tm_tablo[128];
   alignas(64) unsigned char tm_gt[128];
   alignas(64) unsigned char tm_stab[128];
+  alignas(64) unsigned char tm_stablo[128];
   alignas(64) unsigned char tm_at[128];
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
   size_t bytes;
@@ -171,13 +179,15 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 // channels from b0, an operand pack and then the tile kernel.  The analysis
 // pack reads the ring spectra and the tile kernel writes alm; the synthesis
 // pack reads alm and the tile kernel writes the ring workspace d_F.
-int tc_columns(int nbatch);  // N of the tile for a plan of nbatch channels
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch);
+// The 16-bit dtypes (HPX_F32_BF16 ...) have only this path; their tables
+// (row and column, hi and for x3 lo parts) are built here too.
+int tc_columns(int nbatch, int cap);  // N of a tile for nbatch channels, at most cap per launch
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype);
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s);
-int tc_channels_per_launch(const hpx_plan_s* p);
-cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);
+int tc_channels_per_launch(const hpx_plan_s* p, bool synthesis);
+cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);
 cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s);
-cudaError_t launch_pack_at_tc(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s);
+cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s);
 cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s);
 
 }  // namespace hpx

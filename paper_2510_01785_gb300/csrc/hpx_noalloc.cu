@@ -69,6 +69,10 @@ extern "C" hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* 
     hpx::set_error("hpx_map2alm_noalloc: data pointers must be 16-byte aligned");
     return HPX_ERR_INVALID;
   }
+  if (plan->dtype != HPX_F64 && plan->dtype != HPX_F32) {
+    hpx::set_error("hpx_map2alm_noalloc: the 16-bit mixed-precision dtypes are not provided here; use hpx_map2alm");
+    return HPX_ERR_UNSUPPORTED;
+  }
   const size_t real = plan->dtype == HPX_F64 ? sizeof(double) : sizeof(float);
   const size_t need = 2 * real * (size_t)plan->nbatch * (size_t)plan->nspec;
   if (need > kScratchBytes) {

@@ -121,7 +121,7 @@ static void plan_free(hpx_plan_s* p) {
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
-                  p->d_stab, p->d_stab_off, p->d_stab_lstart};
+                  p->d_stab, p->d_stab_off, p->d_stab_lstart, p->d_tab_lo, p->d_stab_lo, p->d_bmax};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->timing) {
@@ -179,8 +179,8 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e != cudaSuccess) return e;
-  if (p->tc_nn) {  // tensor cores: operand pack (stage 4), then the tile kernel (stage 1), per channel chunk
-    const int cp = tc_channels_per_launch(p);
+  if (p->tc_nn_a) {  // tensor cores: operand pack (stage 4), then the tile kernel (stage 1), per channel chunk
+    const int cp = tc_channels_per_launch(p, false);
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 4, s, [&](int* n) {
@@ -203,8 +203,8 @@ template <typename T>
 static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, double mfac,
                                  cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (p->tc_nn) {  // tensor cores: operand pack (stage 5), then the tile kernel (stage 2), per channel chunk
-    const int cp = tc_channels_per_launch(p);
+  if (p->tc_nn_s) {  // tensor cores: operand pack (stage 5), then the tile kernel (stage 2), per channel chunk
+    const int cp = tc_channels_per_launch(p, true);
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 5, s, [&](int* n) {
@@ -277,15 +277,18 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("nbatch must be in [1, 65535], got %d", nbatch);
     return HPX_ERR_INVALID;
   }
-  if (dtype != HPX_F64 && dtype != HPX_F32) {
-    set_error("dtype %d is not provided by this build", (int)dtype);
-    return HPX_ERR_UNSUPPORTED;
+  if (dtype < HPX_F64 || dtype > HPX_F32_FP16X3) {
+    set_error("unknown dtype %d", (int)dtype);
+    return HPX_ERR_INVALID;
   }
   if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES)) {
     set_error("unknown plan flags 0x%x", flags);
     return HPX_ERR_INVALID;
   }
-  if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
+  const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
+  if (mixed) {
+    flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES;  // the 16-bit dtypes' only path
+  } else if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
     set_error("HPX_PLAN_TENSOR_CORES needs an HPX_F32 plan with HPX_PLAN_LAMBDA_TABLE");
     return HPX_ERR_INVALID;
   }
@@ -356,7 +359,7 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
-  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE))
+  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && !mixed)
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
@@ -407,16 +410,28 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
              (sizeof(int) + 2 * sizeof(double)) * nchain + cs * (size_t)nbatch * nspec +
              cs * (size_t)nbatch * nring * (mmax + 1);
   const size_t ngroup = (npair + 31) / 32;
+  const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
+  if (mixed) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype);
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
     b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ngroup;
   if (flags & HPX_PLAN_TENSOR_CORES)  // row-table starts padded to the tile grid; column table; operands
-    b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch);
+    b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) +
+         tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype);
   return b + sizeof(int);
 }
 
 size_t hpx_plan_table_bytes(hpx_plan plan) {
   if (!plan || !plan->d_tab) return 0;
-  return (size_t)plan->tab_elems * (plan->dtype == HPX_F64 ? sizeof(double) : sizeof(float));
+  const size_t es = plan->dtype == HPX_F64 ? sizeof(double) : plan->dtype == HPX_F32 ? sizeof(float) : 2;
+  const size_t parts = plan->d_tab_lo ? 2 : 1;
+  return (size_t)plan->tab_elems * es * parts;
+}
+
+size_t hpx_plan_column_table_bytes(hpx_plan plan) {
+  if (!plan || !plan->d_stab) return 0;
+  const size_t es = plan->dtype == HPX_F32 ? sizeof(float) : 2;
+  const size_t parts = plan->d_stab_lo ? 2 : 1;
+  return (size_t)plan->stab_elems * es * parts;
 }
 
 hpx_status hpx_map2alm(hpx_plan plan, const void* map, void* alm, hpx_stream_t stream) {

@@ -35,6 +35,8 @@
 // memory and returns; its output rows are then left unwritten.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <climits>
 #include <vector>
@@ -105,6 +107,11 @@ __device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, ui
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -135,21 +142,92 @@ __device__ __forceinline__ float4 tf32_rem4(float4 x) {
 }
 
 // ---------------------------------------------------------------------------
-// operand pack: Gt[m][g][n][32] from the ring spectra
+// operand element types
+// ---------------------------------------------------------------------------
+// float: FP32 tables and operands; the products are 3xTF32 with the
+//   remainders made in shared memory (mode 0).
+// __nv_bfloat16 / __half: 16-bit tables and operands (kind::f16 products,
+//   FP32 accumulation); the hi part, and for the x3 modes the lo part
+//   lo = x - hi rounded again, are stored (modes 1 and 2).
+// A row of any operand tile is 128 bytes: 32 floats or 64 16-bit values.
+template <typename E> struct Elt;
+template <> struct Elt<float> {
+  static constexpr int kw = 32;
+  static __device__ __forceinline__ float from_float(float v) { return v; }
+  static __device__ __forceinline__ float to_float(float v) { return v; }
+  static __device__ __forceinline__ float from_double(double v) { return to_real<float>(v); }
+  static __device__ __forceinline__ double to_double(float v) { return (double)v; }
+};
+template <> struct Elt<__nv_bfloat16> {
+  static constexpr int kw = 64;
+  static __device__ __forceinline__ __nv_bfloat16 from_float(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 from_double(double v) { return __double2bfloat16(v); }
+  static __device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+};
+template <> struct Elt<__half> {
+  static constexpr int kw = 64;
+  static __device__ __forceinline__ __half from_float(float v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half from_double(double v) { return __double2half(v); }
+  static __device__ __forceinline__ double to_double(__half v) { return (double)__half2float(v); }
+};
+
+// Operand value v (already scaled) into row n of a tile column: hi at row n,
+// and for x3 the remainder at row NN + n.
+template <typename E>
+__device__ __forceinline__ void put(E* col, int n, int NN, float v, bool x3) {
+  constexpr int KW = Elt<E>::kw;
+  const E h = Elt<E>::from_float(v);
+  col[(long long)n * KW] = h;
+  if (x3) col[(long long)(NN + n) * KW] = Elt<E>::from_float(v - Elt<E>::to_float(h));
+}
+
+// Power of two s with s * bound <= 2^14, from the channel's recorded largest
+// component |x| (bit pattern of a non-negative float) times sfac, so that
+// FP16 operands stay in range; 1 without a record (FP32 operands) or for an
+// all-zero channel.
+__device__ __forceinline__ float chan_scale(const unsigned* bmax, int b, float sfac) {
+  if (!bmax) return 1.f;
+  const float amax = __uint_as_float(bmax[b]) * sfac;
+  if (!(amax > 0.f) || !(amax < 3.0e38f)) return 1.f;
+  int e;
+  frexpf(amax, &e);  // amax < 2^e
+  return ldexpf(1.f, 14 - e);
+}
+
+// Largest |component| of each channel b0 .. b0+nb-1 of x ([b][stride] floats,
+// n per channel), as float bits, into bmax[b] (atomic max; zeroed first).
+__global__ void k_absmax(const float* __restrict__ x, long long n, long long stride, int b0, unsigned* bmax) {
+  const int b = b0 + blockIdx.y;
+  const float* xb = x + (long long)b * stride;
+  float v = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v = fmaxf(v, fabsf(xb[i]));
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(bmax + b, __float_as_uint(v));
+}
+
+// ---------------------------------------------------------------------------
+// analysis operand: Gt[m][g][rows][KW] from the ring spectra
 // ---------------------------------------------------------------------------
 // For pair p (north ring p, south ring nring-1-p; the equator ring pairs with
 // nothing) G(y) = W_y X_y[m mod N] exp(-i m phi_0) as in the CUDA-core
 // analysis; row n < 2 CP holds part n%2 of S = G(north) + G(south) for channel
-// n/2, row 2 CP + n that of A = G(north) - G(south).  One warp per group.
-template <int CP>
+// n/2, row 2 CP + n that of A = G(north) - G(south), times the channel's
+// scale; for x3 rows NN .. 2 NN - 1 hold the remainders.  KW consecutive
+// threads per group (one tile column each).
+template <int CP, typename E>
 __global__ void __launch_bounds__(128)
 k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, const RingInfo* __restrict__ rings,
-          float* __restrict__ gt, int npair, int nring, int ngroup, long long nspec, int b0, int nb, int use_w) {
-  constexpr int C2N = 2 * CP, NN = 2 * C2N;
-  const int g = blockIdx.x * 4 + (threadIdx.x >> 5), m = blockIdx.y, lane = threadIdx.x & 31;
+          E* __restrict__ gt, int npair, int nring, int ngroup, long long nspec, int b0, int nb, int use_w, int x3,
+          const unsigned* __restrict__ bmax, float sfac) {
+  constexpr int KW = Elt<E>::kw, C2N = 2 * CP, NN = 2 * C2N;
+  const int rb = x3 ? 2 * NN : NN;
+  const int g = blockIdx.x * (128 / KW) + threadIdx.x / KW, m = blockIdx.y, lane = threadIdx.x % KW;
   if (g >= ngroup) return;
-  const int p = g * 32 + lane;
-  float* out = gt + ((long long)m * ngroup + g) * NN * 32 + lane;
+  const int p = g * KW + lane;
+  E* out = gt + ((long long)m * ngroup + g) * rb * KW + lane;
   const bool active = p < npair;
   const bool has_south = active && p != npair - 1;
   int k = 0, N = 2;
@@ -175,6 +253,7 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
 #pragma unroll 4
   for (int c = 0; c < CP; ++c) {
     float2 gn = make_float2(0.f, 0.f), gs = gn;
+    float sc = 1.f;
     if (active && c < nb) {
       const float2* X = spec + (long long)(b0 + c) * nspec;
       float2 x = X[on + kk];
@@ -185,33 +264,33 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
         if (conj) x = cconj(x);
         gs = cscale(cmul(x, es), ws);
       }
+      sc = chan_scale(bmax, b0 + c, sfac);
     }
-    out[(2 * c) * 32] = gn.x + gs.x;
-    out[(2 * c + 1) * 32] = gn.y + gs.y;
-    out[(C2N + 2 * c) * 32] = gn.x - gs.x;
-    out[(C2N + 2 * c + 1) * 32] = gn.y - gs.y;
+    put(out, 2 * c, NN, (gn.x + gs.x) * sc, x3);
+    put(out, 2 * c + 1, NN, (gn.y + gs.y) * sc, x3);
+    put(out, C2N + 2 * c, NN, (gn.x - gs.x) * sc, x3);
+    put(out, C2N + 2 * c + 1, NN, (gn.y - gs.y) * sc, x3);
   }
 }
 
 // ---------------------------------------------------------------------------
-// the tile kernel
+// synthesis operand: At[chunk][rows][KW] from alm
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// synthesis operands
-// ---------------------------------------------------------------------------
-// Coefficient operand At[m][j][n][32] for l = m + 32 j + (0..31): row n < 2 CP
-// holds part n%2 of P_l mfac a_lm of channel n/2 where l - m is even (0
-// elsewhere), row 2 CP + n the same for odd l - m; zero past lmax.  Only
-// Re a_l0 enters (real maps).  One warp per (m, j).
-template <int CP>
+// For l = m + KW j + (0..KW-1): row n < 2 CP holds part n%2 of
+// s_c P_l mfac a_lm of channel n/2 where l - m is even (0 elsewhere), row
+// 2 CP + n the same for odd l - m; zero past lmax; x3 remainders in rows
+// NN .. 2 NN - 1.  Only Re a_l0 enters (real maps).
+template <int CP, typename E>
 __global__ void __launch_bounds__(128)
 k_pack_at(const float2* __restrict__ alm, const double* __restrict__ coef_p, const long long* __restrict__ achunk,
-          float* __restrict__ at, int lmax, int mmax, long long nalm, int b0, int nb, double mfac) {
-  constexpr int C2N = 2 * CP, NN = 2 * C2N;
-  const int m = blockIdx.y, j = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (m > mmax || j > (lmax - m) / 32) return;
-  const int l = m + 32 * j + lane;
-  float* out = at + (achunk[m] + j) * NN * 32 + lane;
+          E* __restrict__ at, int lmax, int mmax, long long nalm, int b0, int nb, double mfac, int x3,
+          const unsigned* __restrict__ bmax, float sfac) {
+  constexpr int KW = Elt<E>::kw, C2N = 2 * CP, NN = 2 * C2N;
+  const int rb = x3 ? 2 * NN : NN;
+  const int m = blockIdx.y, j = blockIdx.x * (128 / KW) + threadIdx.x / KW, lane = threadIdx.x % KW;
+  if (m > mmax || j > (lmax - m) / KW) return;
+  const int l = m + KW * j + lane;
+  E* out = at + (achunk[m] + j) * rb * KW + lane;
   const bool in = l <= lmax;
   const bool odd = ((l - m) & 1) != 0;
   const long long base = alm_base(lmax, m);
@@ -221,22 +300,97 @@ k_pack_at(const float2* __restrict__ alm, const double* __restrict__ coef_p, con
     float2 a = make_float2(0.f, 0.f);
     if (in && c < nb) {
       a = alm[(long long)(b0 + c) * nalm + base + l];
-      a = make_float2((float)(s * a.x), m == 0 ? 0.f : (float)(s * a.y));
+      const double sc = s * (double)chan_scale(bmax, b0 + c, sfac);
+      a = make_float2((float)(sc * a.x), m == 0 ? 0.f : (float)(sc * a.y));
     }
     const float2 e = odd ? make_float2(0.f, 0.f) : a, o = odd ? a : make_float2(0.f, 0.f);
-    out[(2 * c) * 32] = e.x;
-    out[(2 * c + 1) * 32] = e.y;
-    out[(C2N + 2 * c) * 32] = o.x;
-    out[(C2N + 2 * c + 1) * 32] = o.y;
+    put(out, 2 * c, NN, e.x, x3);
+    put(out, 2 * c + 1, NN, e.y, x3);
+    put(out, C2N + 2 * c, NN, o.x, x3);
+    put(out, C2N + 2 * c + 1, NN, o.y, x3);
   }
 }
 
-// Column lambda table for the synthesis: per (m, tile T of 128 ring pairs),
-// from ls_T = the tile's first significant l (aligned down to m + 32 j) to
-// lmax, blocks of 128 pairs x 32 l, element [p][l] = the recurrence value of
-// chain (m, 128 T + p) in the same float as the row table (zero before the
-// chain's start, past lmax and for pairs past npair).
-__global__ void k_stab_tiles(const int* __restrict__ lc_tab, int lmax, int npair, int nptile, int* lstart,
+// ---------------------------------------------------------------------------
+// plan-time lambda tables of the tensor-core stages
+// ---------------------------------------------------------------------------
+// The recurrence of every table, operation for operation the same as the
+// CUDA-core kernels' (so FP32 tables hold identical values): from l = ls,
+// mu_l = c_l z mu_{l-1} - mu_{l-2}, restarted at the chain start lc with the
+// stored (mu_{lc-1}, mu_lc); zero before lc.
+struct Chain {
+  double z, s0, s1, mu1, mu2;
+  int lc;
+  const double* c;
+  __device__ __forceinline__ double step(int l) {
+    double mu = fma(c[l] * z, mu1, -mu2);
+    if (l == lc) {
+      mu = s1;
+      mu1 = s0;
+    }
+    mu2 = mu1;
+    mu1 = mu;
+    return mu;
+  }
+};
+__device__ __forceinline__ Chain chain_at(const RingInfo* rings, const double* coef_c, const int* lc_tab,
+                                          const double* mu0_tab, const double* mu1_tab, int lmax, int npair, int m,
+                                          int p) {
+  Chain ch{0.0, 0.0, 0.0, 0.0, 0.0, INT_MAX, coef_c + alm_base(lmax, m)};
+  if (p < npair) {
+    const long long ci = (long long)m * npair + p;
+    ch.z = rings[p].z;
+    ch.lc = lc_tab[ci];
+    ch.s0 = mu0_tab[ci];
+    ch.s1 = mu1_tab[ci];
+  }
+  return ch;
+}
+
+// Row table (analysis) of 16-bit types: per (m, group of KW = 64 pairs), rows
+// l = ls_g .. lmax of 64 values, ls_g the group's first significant l aligned
+// down to the analysis tile grid m + 128 j.  (The FP32 row table, in groups
+// of 32 pairs, is the CUDA-core kernels' table.)
+__global__ void k_rtab_groups(const int* __restrict__ lc_tab, int lmax, int npair, int kw, int ngroup, int* lstart,
+                              long long* rows) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  if (g >= ngroup) return;
+  int ls = lmax + 1;
+  for (int j = 0; j < kw; ++j) {
+    const int p = g * kw + j;
+    if (p < npair) ls = min(ls, lc_tab[(long long)m * npair + p]);
+  }
+  if (ls <= lmax) ls = m + ((ls - m) / kTcTile) * kTcTile;
+  lstart[(long long)m * ngroup + g] = ls;
+  rows[(long long)m * ngroup + g] = lmax + 1 - ls;
+}
+
+template <typename E>
+__global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+                            const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
+                            const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
+                            const long long* __restrict__ off, int lmax, int npair, int ngroup, E* hi, E* lo) {
+  constexpr int KW = Elt<E>::kw;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  const int g = p / KW;
+  if (g >= ngroup) return;
+  const long long mg = (long long)m * ngroup + g;
+  const int ls = lstart[mg];
+  const long long o = off[mg] + (p % KW);
+  Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
+  for (int l = ls; l <= lmax; ++l) {
+    const double mu = p < npair ? ch.step(l) : 0.0;
+    const E h = Elt<E>::from_double(mu);
+    hi[o + (long long)(l - ls) * KW] = h;
+    if (lo) lo[o + (long long)(l - ls) * KW] = Elt<E>::from_double(mu - Elt<E>::to_double(h));
+  }
+}
+
+// Column table (synthesis): per (m, tile T of 128 ring pairs), from ls_T =
+// the tile's first significant l (aligned down to m + KW j) to lmax, blocks
+// of 128 pairs x KW l, element [p][l] (zero before a chain's start, past lmax
+// and for pairs past npair).
+__global__ void k_ctab_tiles(const int* __restrict__ lc_tab, int lmax, int npair, int kw, int nptile, int* lstart,
                              long long* nblk) {
   const int T = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
   if (T >= nptile) return;
@@ -245,122 +399,118 @@ __global__ void k_stab_tiles(const int* __restrict__ lc_tab, int lmax, int npair
     const int p = T * 128 + j;
     if (p < npair) ls = min(ls, lc_tab[(long long)m * npair + p]);
   }
-  if (ls <= lmax) ls = m + ((ls - m) / 32) * 32;
+  if (ls <= lmax) ls = m + ((ls - m) / kw) * kw;
   lstart[(long long)m * nptile + T] = ls;
-  nblk[(long long)m * nptile + T] = ls <= lmax ? (lmax - ls) / 32 + 1 : 0;
+  nblk[(long long)m * nptile + T] = ls <= lmax ? (lmax - ls) / kw + 1 : 0;
 }
 
-__global__ void k_stab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+template <typename E>
+__global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
-                            const long long* __restrict__ off, int lmax, int npair, int nptile, float* tab) {
+                            const long long* __restrict__ off, int lmax, int npair, int nptile, E* hi, E* lo) {
+  constexpr int KW = Elt<E>::kw, V = 16 / (int)sizeof(E);  // values per 16-byte store
   const int p = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
   const int T = p >> 7;
   if (T >= nptile) return;
   const long long mT = (long long)m * nptile + T;
   const int ls = lstart[mT];
   if (ls > lmax) return;
-  const int lend = ls + ((lmax - ls) / 32 + 1) * 32;  // end of the last block
-  float* out = tab + off[mT] + (p & 127) * 32;
-  double z = 0.0, s0 = 0.0, s1 = 0.0;
-  int lc = INT_MAX;
-  if (p < npair) {
-    const long long ci = (long long)m * npair + p;
-    z = rings[p].z;
-    lc = lc_tab[ci];
-    s0 = mu0_tab[ci];
-    s1 = mu1_tab[ci];
-  }
-  const long long base = alm_base(lmax, m);
-  double mu1 = 0.0, mu2 = 0.0;
-  for (int l4 = ls; l4 < lend; l4 += 4) {
-    float v[4];
+  const int lend = ls + ((lmax - ls) / KW + 1) * KW;  // end of the last block
+  const long long o = off[mT] + (long long)(p & 127) * KW;
+  Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
+  for (int lv = ls; lv < lend; lv += V) {
+    alignas(16) E h[V];
+    alignas(16) E r[V];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int l = l4 + u;
-      float f = 0.f;
-      if (l <= lmax && p < npair) {  // the row table's recurrence, operation for operation
-        double mu = fma(coef_c[base + l] * z, mu1, -mu2);
-        if (l == lc) {
-          mu = s1;
-          mu1 = s0;
-        }
-        mu2 = mu1;
-        mu1 = mu;
-        f = to_real<float>(mu);
-      }
-      v[u] = f;
+    for (int u = 0; u < V; ++u) {
+      const int l = lv + u;
+      const double mu = (l <= lmax && p < npair) ? ch.step(l) : 0.0;
+      h[u] = Elt<E>::from_double(mu);
+      r[u] = Elt<E>::from_double(mu - Elt<E>::to_double(h[u]));
     }
-    const int r = l4 - ls;
-    *reinterpret_cast<float4*>(out + (long long)(r >> 5) * 4096 + (r & 31)) = make_float4(v[0], v[1], v[2], v[3]);
+    const int q = lv - ls;
+    const long long at = o + (long long)(q / KW) * 128 * KW + (q % KW);
+    *reinterpret_cast<uint4*>(hi + at) = *reinterpret_cast<const uint4*>(h);
+    if (lo) *reinterpret_cast<uint4*>(lo + at) = *reinterpret_cast<const uint4*>(r);
   }
 }
 
 // ---------------------------------------------------------------------------
-// the tile kernels
+// the tile kernel
 // ---------------------------------------------------------------------------
-template <int NN>
+// MODE 0: FP32 operands, 3xTF32 with the remainders made in shared memory;
+// MODE 1: one 16-bit product; MODE 2: 16-bit x3 (stored hi and lo parts).
+template <int NN, int MODE>
 struct TcShape {
-  static constexpr int kA = kTcTile * 128;   // lambda tile bytes: 128 rows x 32 floats
-  static constexpr int kG = NN * 128;        // B tile bytes (Gt or At)
-  static constexpr int kStage = kA + 2 * kG; // one stage: lambda tile, B tile, its remainder right after it
-  static constexpr int kLo = kA;             // lambda remainder buffer (two, alternating by K block)
+  static constexpr int kA = kTcTile * 128;  // lambda tile bytes: 128 rows x 128 bytes
+  static constexpr int kG = NN * 128;       // B tile bytes (Gt or At)
+  static constexpr int kStage = MODE == 0 ? kA + 2 * kG : MODE == 1 ? kA + kG : 2 * kA + 2 * kG;
+  static constexpr int kLo = MODE == 0 ? kA : 0;  // lambda remainder buffers (two, alternating by K block)
+  static constexpr int kBuf = MODE == 0 ? 2 * NN : NN;  // TMEM columns of one block accumulator
+  static constexpr int kTmemCols = 2 * kBuf;
   static constexpr int kNStage = (200 * 1024 - 2 * kLo) / kStage < 8 ? (200 * 1024 - 2 * kLo) / kStage : 8;
-  static constexpr int kTmemCols = 4 * NN;   // two block accumulators of 2 NN columns
   static constexpr size_t kSmem =
       (size_t)kNStage * kStage + 2 * kLo + 1024 /* base alignment */ + 2048 /* barriers, lists */;
-  static_assert(kNStage >= 2 && kTmemCols <= 512, "shape");
+  static_assert(kNStage >= 2 && kTmemCols <= 512 && kTmemCols >= 32, "shape");
 };
 
 constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, warp 5 issues products
 
 struct TcArgs {
-  const long long* off;    // analysis: row table offsets [m][group]; synthesis: column table [m][p tile]
-  const int* lstart;       // first l stored, same indexing
-  int ngroup;              // groups (analysis) or p tiles (synthesis) per m
-  const long long* achunk; // synthesis: first At chunk of each m
-  const double* coef_p;    // analysis: P_l
-  float* out;              // analysis: alm [b][nalm] complex; synthesis: F [b][nring][mmax+1] complex
+  const long long* off;     // analysis: row table offsets [m][group]; synthesis: column table [m][p tile]
+  const int* lstart;        // first l stored, same indexing
+  int ngroup;               // groups (analysis) or p tiles (synthesis) per m
+  const long long* achunk;  // synthesis: first At chunk of each m
+  const double* coef_p;     // analysis: P_l
+  const unsigned* bmax;     // 16-bit operands: per-channel largest component
+  float sfac;               // bound factor for the channel scale
+  float* out;               // analysis: alm [b][nalm] complex; synthesis: F [b][nring][mmax+1] complex
   int lmax, mmax, npair, nring;
   long long nalm;
   int b0, nb;
   double mfac;
+  uint32_t fmt;             // 16-bit modes: operand format of kind::f16 (0 FP16, 1 BF16)
   int* status;
 };
 
 // One CTA: a 128-row tile of one m, all channels of the launch.
-//   analysis (SYN false): rows are l = l0 .. l0+127, K runs over the 32-pair
+//   analysis (SYN false): rows are l = l0 .. l0+127, K runs over the KW-pair
 //     groups whose table rows reach the tile, B = Gt: D[l][n] = sum_p L G;
 //   synthesis (SYN true): rows are ring pairs p = 128 T .. 128 T + 127, K runs
-//     over 32-l chunks from the tile's first significant l, A = the column
+//     over KW-l chunks from the tile's first significant l, A = the column
 //     table's blocks, B = At: D[p][n] = sum_l L^T At.
-// Per K block k, with L the lambda tile (128 x 32) and B (NN x 32) in shared
-// memory:
-//   split: lo(L) and lo(B) are formed (hi is the hardware's TF32 truncation
-//          of the tile as loaded; lo = x - trunc(x), rounded to TF32);
-//          lo(B) sits right after B, so [B; lo B] is one N = 2 NN operand;
-//   products (4 steps of K = 8): D[:, 0:2NN] += L [B; lo B]^T and
-//          D[:, 0:NN] += lo(L) B^T, i.e. 8 instructions per block;
-//   drain: D[r][j] + D[r][NN + j] is added into FP32 registers (round to
-//          nearest): the NN/2 columns of the row's parity (analysis) or all
-//          NN (synthesis).
-// The tensor cores add each instruction's products into the accumulator
-// with truncation, so each block is accumulated alone, in one of two TMEM
-// buffers (2 NN columns each), while the other is drained.
+// Per K block k, with L the lambda tile (128 x KW) and B (NN x KW) in shared
+// memory, in 4 instruction steps of 32 bytes along K:
+//   MODE 0: lo(L), lo(B) are formed (hi is the hardware's TF32 truncation of
+//           the tile as loaded; lo = x - trunc(x), rounded to TF32); lo(B)
+//           sits right after B, so D[:, 0:2NN] += L [B; lo B]^T and
+//           D[:, 0:NN] += lo(L) B^T (2 instructions per step); the drain
+//           adds D[r][j] + D[r][NN + j];
+//   MODE 1: D += L B^T;  MODE 2: D += L B^T + L lo(B)^T + lo(L) B^T, with
+//           lo(L) and lo(B) loaded next to L and B.
+// The drain keeps the NN/2 columns of the row's parity (analysis) or all NN
+// (synthesis) and adds them into FP32 registers (round to nearest).  The
+// tensor cores add each instruction's products into the accumulator with
+// truncation, so each block is accumulated alone, in one of two TMEM
+// buffers, while the other is drained.
 //
 // Roles run decoupled, linked by mbarriers: warp 4 keeps up to kNStage
-// blocks of copies in flight, warp 5 issues a block's products once it is
-// split and its accumulator is free, warps 0-3 split block k and then drain
-// block k-1.  After an expired wait a role stops working (the split/drain
-// warps keep looping without work, so their warp-collective tcgen05.ld stays
-// convergent), waits for what it started, and the CTA records the timeout.
-template <int NN, bool SYN>
+// blocks of copies in flight, warp 5 issues a block's products once it has
+// landed (and, MODE 0, is split) and its accumulator is free, warps 0-3 split
+// block k (MODE 0) and drain block k-1.  After an expired wait a role stops
+// working (the split/drain warps keep looping without work, so their
+// warp-collective tcgen05.ld stays convergent), waits for what it started,
+// and the CTA records the timeout.
+template <int NN, bool SYN, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  using S = TcShape<NN>;
-  constexpr int NS = S::kNStage, C2N = NN / 2;
+k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+              const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  using S = TcShape<NN, MODE>;
+  constexpr int NS = S::kNStage, C2N = NN / 2, KW = MODE == 0 ? 32 : 64;
+  constexpr int RB = MODE == 2 ? 2 * NN : NN;  // operand rows per K block in memory
   constexpr int NSUM = SYN ? NN : C2N;
-  static_assert(NN % 32 == 0 && NN <= 128, "N tile");
+  static_assert(NN % 32 == 0 && NN <= (MODE == 0 || SYN ? 128 : 256), "N tile");
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m = blockIdx.y;
   const int l0 = m + kTcTile * blockIdx.x;  // analysis tile
@@ -370,7 +520,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   unsigned char* tiles = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* lobuf = tiles + (size_t)NS * S::kStage;
   uint64_t* full = reinterpret_cast<uint64_t*>(lobuf + 2 * S::kLo);
-  uint64_t* conv = full + NS;   // stage split (128 arrivals)
+  uint64_t* conv = full + NS;   // stage split (128 arrivals; MODE 0)
   uint64_t* empty = conv + NS;  // stage's products done
   uint64_t* accf = empty + NS;  // [2] block accumulator complete
   uint64_t* acce = accf + 2;    // [2] block accumulator drained (128 arrivals)
@@ -379,11 +529,13 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* wcount = reinterpret_cast<int*>(tmem_slot + 2);  // [4]
   int* rowA = wcount + 4;   // analysis: [128] TMA row of the lambda tile of active group k
-  int* rowB = rowA + 128;   // analysis: [128] TMA row of its Gt tile
+  int* rowB = rowA + 128;   // analysis: [128] TMA row of its operand tile
   auto sL = [&](int s) { return tiles + (size_t)s * S::kStage; };
-  auto sB = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA; };
-  auto sBlo = [&](int s) { return tiles + (size_t)s * S::kStage + S::kA + S::kG; };
-  auto sLlo = [&](int b) { return lobuf + (size_t)b * S::kLo; };
+  auto sB = [&](int s) { return tiles + (size_t)s * S::kStage + (MODE == 2 ? 2 : 1) * S::kA; };
+  auto sBlo = [&](int s) { return tiles + (size_t)s * S::kStage + (MODE == 2 ? 2 : 1) * S::kA + S::kG; };
+  auto sLlo = [&](int s, int b) {
+    return MODE == 2 ? tiles + (size_t)s * S::kStage + S::kA : lobuf + (size_t)b * S::kLo;
+  };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -393,7 +545,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   // K blocks.  Analysis: groups whose rows reach this tile (group starts lie
   // on the tile grid m + 128 j, so a group covers the whole tile or starts
   // after it), with their copy coordinates, compacted in group order.
-  // Synthesis: every 32-l chunk from the tile's first stored l.
+  // Synthesis: every KW-l chunk from the tile's first stored l.
   bool act = false;
   int ra = 0, rb = 0;
   unsigned bal = 0;
@@ -402,8 +554,8 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const long long mg = (long long)m * a.ngroup + t;
       const int ls = a.lstart[mg];
       act = ls <= l0;
-      ra = (int)(a.off[mg] / 32) + (l0 - ls);
-      rb = (int)(mg * NN);
+      ra = (int)(a.off[mg] / KW) + (l0 - ls);
+      rb = (int)(mg * RB);
     }
     bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) wcount[warp] = __popc(bal);
@@ -413,9 +565,9 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const long long mT = (long long)m * a.ngroup + blockIdx.x;
     const int ls = a.lstart[mT];
     if (ls <= a.lmax) {
-      na = (a.lmax - ls) / 32 + 1;
-      ra0 = (int)(a.off[mT] / 32);
-      rb0 = (int)((a.achunk[m] + (ls - m) / 32) * NN);
+      na = (a.lmax - ls) / KW + 1;
+      ra0 = (int)(a.off[mT] / KW);
+      rb0 = (int)((a.achunk[m] + (ls - m) / KW) * RB);
     }
   }
   if (t == 32) {
@@ -452,12 +604,18 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // ---- copies: block k into stage k % NS once block k - NS's products are done
     int issued = 0;
     if (lane == 0) {
+      constexpr uint32_t kBytes = MODE == 2 ? 2 * (S::kA + S::kG) : S::kA + S::kG;
       for (int k = 0; k < na; ++k) {
         const int s = k % NS;
         if (k >= NS && !wait_phase(&empty[s], (uint32_t)(k / NS - 1) & 1u, abort_flag, true)) break;
-        mbar_expect_tx(&full[s], S::kA + S::kG);
-        tma_load_2d(sL(s), &tmA, 0, SYN ? ra0 + k * 128 : rowA[k], &full[s]);
-        tma_load_2d(sB(s), &tmB, 0, SYN ? rb0 + k * NN : rowB[k], &full[s]);
+        const int r_a = SYN ? ra0 + k * 128 : rowA[k], r_b = SYN ? rb0 + k * RB : rowB[k];
+        mbar_expect_tx(&full[s], kBytes);
+        tma_load_2d(sL(s), &tmA, 0, r_a, &full[s]);
+        tma_load_2d(sB(s), &tmB, 0, r_b, &full[s]);
+        if (MODE == 2) {
+          tma_load_2d(sLlo(s, 0), &tmAlo, 0, r_a, &full[s]);
+          tma_load_2d(sBlo(s), &tmB, 0, r_b + NN, &full[s]);
+        }
         issued = k + 1;
       }
       // whatever was started completes before the CTA moves on
@@ -467,22 +625,33 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   } else if (warp == 5) {
     // ---- products
     if (lane == 0) {
-      // instruction descriptors: D f32, A and B tf32, both K-major, M = 128
-      const uint32_t id2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * NN >> 3) << 17) | ((128u >> 4) << 24);
-      const uint32_t id1 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) | ((128u >> 4) << 24);
+      // instruction descriptors: D f32, A and B K-major, M = 128; tf32 (2)
+      // or the 16-bit format
+      const uint32_t f = MODE == 0 ? 2u : a.fmt;
+      const uint32_t id2 = (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(2 * NN >> 3) << 17) | ((128u >> 4) << 24);
+      const uint32_t id1 = (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(NN >> 3) << 17) | ((128u >> 4) << 24);
       bool issued_any = false;
       for (int k = 0; k < na; ++k) {
         const int s = k % NS, b = k & 1;
-        if (!wait_phase(&conv[s], (uint32_t)(k / NS) & 1u, abort_flag, true)) break;
+        if (!wait_phase(MODE == 0 ? &conv[s] : &full[s], (uint32_t)(k / NS) & 1u, abort_flag, true)) break;
         if (k >= 2 && !wait_phase(&acce[b], (uint32_t)((k - 2) >> 1) & 1u, abort_flag, true)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(b * 2 * NN);
-        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(b)), aB = smem_u32(sB(s));
+        const uint32_t d = tmem + (uint32_t)(b * S::kBuf);
+        const uint32_t aL = smem_u32(sL(s)), aLlo = smem_u32(sLlo(s, b)), aB = smem_u32(sB(s)),
+                       aBlo = smem_u32(sBlo(s));
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {  // K = 8 floats (32 bytes) per instruction
+        for (int j = 0; j < 4; ++j) {  // 32 bytes along K per instruction (8 tf32 or 16 16-bit values)
           const uint32_t off = 32u * j;
-          umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id2, j > 0 ? 1u : 0u);
-          umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
+          if constexpr (MODE == 0) {
+            umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id2, j > 0 ? 1u : 0u);
+            umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
+          } else {
+            umma_f16(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id1, j > 0 ? 1u : 0u);
+            if constexpr (MODE == 2) {
+              umma_f16(d, sdesc_sw128(aL + off), sdesc_sw128(aBlo + off), id1, 1u);
+              umma_f16(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
+            }
+          }
         }
         umma_commit(&empty[s]);
         umma_commit(&accf[b]);
@@ -501,53 +670,58 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     float sum[NSUM];
 #pragma unroll
     for (int j = 0; j < NSUM; ++j) sum[j] = 0.f;
+    auto col = [&](const uint32_t* v1, const uint32_t* v2, int j) {
+      return MODE == 0 ? __uint_as_float(v1[j]) + __uint_as_float(v2[j]) : __uint_as_float(v1[j]);
+    };
     auto drain = [&](int buf) {  // warp-collective
-      const uint32_t c0 = trow + (uint32_t)(buf * 2 * NN);
+      const uint32_t c0 = trow + (uint32_t)(buf * S::kBuf);
       if constexpr (SYN) {
 #pragma unroll
         for (int q = 0; q < NN / 16; ++q) {
           uint32_t v1[16], v2[16];
           tmem_ld16(c0 + (uint32_t)(q * 16), v1);
-          tmem_ld16(c0 + (uint32_t)(NN + q * 16), v2);
+          if (MODE == 0) tmem_ld16(c0 + (uint32_t)(NN + q * 16), v2);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sum[q * 16 + j] += __uint_as_float(v1[j]) + __uint_as_float(v2[j]);
+          for (int j = 0; j < 16; ++j) sum[q * 16 + j] += col(v1, v2, j);
         }
       } else {
 #pragma unroll
         for (int q = 0; q < C2N / 16; ++q) {
           uint32_t s1[16], s2[16], a1[16], a2[16];
           tmem_ld16(c0 + (uint32_t)(q * 16), s1);
-          tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
           tmem_ld16(c0 + (uint32_t)(C2N + q * 16), a1);
-          tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
+          if (MODE == 0) {
+            tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
+            tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
+          }
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            sum[q * 16 + j] += odd ? __uint_as_float(a1[j]) + __uint_as_float(a2[j])
-                                   : __uint_as_float(s1[j]) + __uint_as_float(s2[j]);
+          for (int j = 0; j < 16; ++j) sum[q * 16 + j] += odd ? col(a1, a2, j) : col(s1, s2, j);
         }
       }
     };
     bool alive = true;
     for (int k = 0; k < na; ++k) {
       const int s = k % NS, b = k & 1;
-      if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
-      if (alive) {
-        // elementwise, so the swizzle does not matter; consecutive threads
-        // take consecutive 16-byte words.  Remainder buffer b was last read
-        // by block k-2's products, complete since this thread drained that
-        // block in the previous iteration.
-        const float4* x = reinterpret_cast<const float4*>(sL(s));
-        float4* xlo = reinterpret_cast<float4*>(sLlo(b));
+      if (MODE == 0) {
+        if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
+        if (alive) {
+          // elementwise, so the swizzle does not matter; consecutive threads
+          // take consecutive 16-byte words.  Remainder buffer b was last read
+          // by block k-2's products, complete since this thread drained that
+          // block in the previous iteration.
+          const float4* x = reinterpret_cast<const float4*>(sL(s));
+          float4* xlo = reinterpret_cast<float4*>(sLlo(s, b));
 #pragma unroll
-        for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
-        const float4* y = reinterpret_cast<const float4*>(sB(s));
-        float4* ylo = reinterpret_cast<float4*>(sBlo(s));
+          for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
+          const float4* y = reinterpret_cast<const float4*>(sB(s));
+          float4* ylo = reinterpret_cast<float4*>(sBlo(s));
 #pragma unroll
-        for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&conv[s]);
+          for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&conv[s]);
+        }
       }
       if (k >= 1) {  // drain block k-1 while block k's products run
         bool ok = alive && wait_phase(&accf[b ^ 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
@@ -586,7 +760,9 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
           for (int c = 0; c < C2N / 2; ++c) {
             if (c < a.nb) {
-              const float er = sum[2 * c], ei = sum[2 * c + 1], orr = sum[C2N + 2 * c], oi = sum[C2N + 2 * c + 1];
+              const float inv = 1.f / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
+              const float er = sum[2 * c] * inv, ei = sum[2 * c + 1] * inv;
+              const float orr = sum[C2N + 2 * c] * inv, oi = sum[C2N + 2 * c + 1] * inv;
               const long long fb = (long long)(a.b0 + c) * a.nring;
               F[(fb + p) * mstride + m] = make_float2(er + orr, ei + oi);
               if (ys >= 0) F[(fb + ys) * mstride + m] = make_float2(er - orr, ei - oi);
@@ -599,9 +775,10 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         float2* out = reinterpret_cast<float2*>(a.out) + (long long)a.b0 * a.nalm + base + l;
 #pragma unroll
         for (int c = 0; c < C2N / 2; ++c)
-          if (c < a.nb)
-            out[(long long)c * a.nalm] =
-                make_float2((float)(scale * sum[2 * c]), (float)(scale * sum[2 * c + 1]));
+          if (c < a.nb) {
+            const double sc = scale / (double)chan_scale(a.bmax, a.b0 + c, a.sfac);
+            out[(long long)c * a.nalm] = make_float2((float)(sc * sum[2 * c]), (float)(sc * sum[2 * c + 1]));
+          }
       }
     }
     if (*abort_flag != 0 && t == 0) atomicExch(a.status, (int)HPX_ERR_TIMEOUT);
@@ -629,17 +806,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// A row-major float matrix of `rows` rows x 32 columns, read as tiles of
-// box_rows x 32 in the 128-byte swizzle; rows past the end read as zero.
-bool encode_rows32(void* out, const void* base, unsigned long long rows, unsigned box_rows) {
+// A row-major matrix of `rows` rows of 128 bytes (32 floats or 64 16-bit
+// values), read as tiles of box_rows rows in the 128-byte swizzle; rows past
+// the end read as zero.
+bool encode_rows128(void* out, const void* base, unsigned long long rows, unsigned box_rows, int esize) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
-  cuuint64_t dims[2] = {32, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {32 * sizeof(float)};
-  cuuint32_t box[2] = {32, box_rows}, es[2] = {1, 1};
-  return enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
-             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const unsigned kw = 128 / esize;
+  cuuint64_t dims[2] = {kw, (cuuint64_t)(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {kw, box_rows}, es[2] = {1, 1};
+  return enc(reinterpret_cast<CUtensorMap*>(out),
+             esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+             const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double mfac) {
@@ -649,6 +830,8 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.ngroup = syn ? p->nptile : p->ngroup;
   a.achunk = p->d_achunk;
   a.coef_p = p->d_coef_p;
+  a.bmax = p->tc_mode ? p->d_bmax : nullptr;
+  a.sfac = syn ? p->tc_sfac_s : p->tc_sfac_a;
   a.out = out;
   a.lmax = p->lmax;
   a.mmax = p->mmax;
@@ -658,90 +841,188 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.b0 = b0;
   a.nb = nb;
   a.mfac = mfac;
+  a.fmt = (uint32_t)p->tc_fmt;
   a.status = p->d_status;
   return a;
 }
 
-template <int CP>
-cudaError_t launch_pack_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
-  k_pack_gt<CP><<<dim3((p->ngroup + 3) / 4, p->mmax + 1), 128, 0, s>>>(
-      (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (float*)p->d_gt, p->npair, p->nring, p->ngroup,
-      p->nspec, b0, nb, use_w ? 1 : 0);
+template <int CP, typename E>
+cudaError_t pack_gt_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
+  constexpr int KW = Elt<E>::kw;
+  k_pack_gt<CP, E><<<dim3((p->ngroup + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
+      (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (E*)p->d_gt, p->npair, p->nring, p->ngroup,
+      p->nspec, b0, nb, use_w ? 1 : 0, p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_a);
   return cudaGetLastError();
 }
 
-template <int CP>
-cudaError_t launch_pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
-  const int nchunk0 = p->lmax / 32 + 1;  // chunks of m = 0, the most
-  k_pack_at<CP><<<dim3((nchunk0 + 3) / 4, p->mmax + 1), 128, 0, s>>>(
-      (const float2*)alm, p->d_coef_p, p->d_achunk, (float*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, mfac);
+template <int CP, typename E>
+cudaError_t pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  constexpr int KW = Elt<E>::kw;
+  const int nchunk0 = p->lmax / KW + 1;  // chunks of m = 0, the most
+  k_pack_at<CP, E><<<dim3((nchunk0 + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
+      (const float2*)alm, p->d_coef_p, p->d_achunk, (E*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, mfac,
+      p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_s);
   return cudaGetLastError();
 }
 
-template <int CP, bool SYN>
-cudaError_t launch_tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
+template <int CP, bool SYN, int MODE>
+cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
   constexpr int NN = 4 * CP;
-  cudaError_t e = allow_max_smem(k_legendre_tc<NN, SYN>);
+  cudaError_t e = allow_max_smem(k_legendre_tc<NN, SYN, MODE>);
   if (e != cudaSuccess) return e;
   const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_stab : p->tm_tab);
+  const CUtensorMap* tmAlo = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_stablo : p->tm_tablo);
   const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_at : p->tm_gt);
   const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, p->mmax + 1);
-  k_legendre_tc<NN, SYN><<<grid, kTcThreads, TcShape<NN>::kSmem, s>>>(*tmA, *tmB,
-                                                                       tc_args(p, SYN, out, b0, nb, mfac));
+  k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, MODE>::kSmem, s>>>(
+      *tmA, *tmAlo, *tmB, tc_args(p, SYN, out, b0, nb, mfac));
+  return cudaGetLastError();
+}
+
+// Dispatch on the plan's operand type (float for mode 0, else 16-bit).
+template <int CP>
+cudaError_t pack_gt_t(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
+  if (p->tc_mode == 0) return pack_gt_cp<CP, float>(p, b0, nb, use_w, s);
+  return p->tc_fmt == 1 ? pack_gt_cp<CP, __nv_bfloat16>(p, b0, nb, use_w, s)
+                        : pack_gt_cp<CP, __half>(p, b0, nb, use_w, s);
+}
+template <int CP>
+cudaError_t pack_at_t(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  if (p->tc_mode == 0) return pack_at_cp<CP, float>(p, alm, b0, nb, mfac, s);
+  return p->tc_fmt == 1 ? pack_at_cp<CP, __nv_bfloat16>(p, alm, b0, nb, mfac, s)
+                        : pack_at_cp<CP, __half>(p, alm, b0, nb, mfac, s);
+}
+template <int CP, bool SYN>
+cudaError_t tile_t(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
+  switch (p->tc_mode) {
+    case 0: if constexpr (CP <= 32) return tile_cp<CP, SYN, 0>(p, out, b0, nb, mfac, s); break;
+    case 1: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 1>(p, out, b0, nb, mfac, s); break;
+    case 2: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 2>(p, out, b0, nb, mfac, s); break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+int tc_mode_of(int dtype) {
+  switch (dtype) {
+    case HPX_F32: return 0;
+    case HPX_F32_BF16: case HPX_F32_FP16: return 1;
+    case HPX_F32_BF16X3: case HPX_F32_FP16X3: return 2;
+    default: return -1;
+  }
+}
+
+cudaError_t absmax(hpx_plan_s const* p, const float* x, long long n, long long stride, int b0, int nb,
+                   cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p->d_bmax + b0, 0, sizeof(unsigned) * nb, s);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (n + 255) / 256;
+  k_absmax<<<dim3((unsigned)(blocks < 256 ? blocks : 256), nb), 256, 0, s>>>(x, n, stride, b0, p->d_bmax);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_columns(int nbatch) {
+int tc_columns(int nbatch, int cap) {
   int cp = 8;
-  while (cp < nbatch && cp < 32) cp *= 2;
+  while (cp < nbatch && cp < cap) cp *= 2;
   return 4 * cp;
 }
 
-int tc_channels_per_launch(const hpx_plan_s* p) { return p->tc_nn / 4; }
+int tc_channels_per_launch(const hpx_plan_s* p, bool syn) { return (syn ? p->tc_nn_s : p->tc_nn_a) / 4; }
 
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch) {
-  const size_t npair = 2 * (size_t)nside, ngroup = (npair + 31) / 32, nptile = (npair + 127) / 128;
-  const size_t nn = (size_t)tc_columns(nbatch);
-  size_t chunks = 0;
-  for (int m = 0; m <= mmax; ++m) chunks += (size_t)((lmax - m) / 32 + 1);
-  return sizeof(float) * (size_t)(mmax + 1) * ngroup * nn * 32     // Gt
-         + sizeof(float) * chunks * nn * 32                         // At
-         + sizeof(float) * chunks * nptile * 128 * 32               // column table (upper bound)
-         + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * nptile + sizeof(long long) * (mmax + 2);
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype) {
+  const int mode = tc_mode_of(dtype);
+  if (mode < 0) return 0;
+  const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
+  const size_t npair = 2 * (size_t)nside, ngroup = (npair + kw - 1) / kw, nptile = (npair + 127) / 128;
+  const size_t nna = (size_t)tc_columns(nbatch, mode ? 64 : 32), nns = (size_t)tc_columns(nbatch, 32);
+  size_t chunks = 0, rows = 0;
+  for (int m = 0; m <= mmax; ++m) {
+    chunks += (size_t)((lmax - m) / kw + 1);
+    rows += (size_t)(lmax + 1 - m) + kTcTile;
+  }
+  size_t b = es * (size_t)(mmax + 1) * ngroup * nna * kw * parts  // Gt
+             + es * chunks * nns * kw * parts                     // At
+             + es * parts * chunks * nptile * 128 * kw            // column table (upper bound)
+             + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * (nptile + ngroup) +
+             sizeof(long long) * (mmax + 2) + sizeof(unsigned) * nbatch;
+  if (mode) b += es * parts * rows * ngroup * kw;  // 16-bit row table (upper bound)
+  return b;
 }
 
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
-  const int nn = tc_columns(p->nbatch);
+  const int mode = tc_mode_of(p->dtype);
+  if (mode < 0) return cudaErrorInvalidValue;
+  p->tc_mode = mode;
+  p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;
+  const int kw = mode ? 64 : 32, es = mode ? 2 : 4;
+  const int nna = tc_columns(p->nbatch, mode ? 64 : 32), nns = tc_columns(p->nbatch, 32);
+  const int rba = mode == 2 ? 2 * nna : nna, rbs = mode == 2 ? 2 * nns : nns;
+  auto dalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) p->bytes += bytes > 0 ? bytes : 16;
+    return e;
+  };
+  // 16-bit row table (the FP32 one is built with the plan's CUDA-core table)
+  cudaError_t e = cudaSuccess;
+  if (mode) {
+    const int ng = (p->npair + kw - 1) / kw;
+    p->ngroup = ng;
+    const long long nent = (long long)(p->mmax + 1) * ng;
+    e = dalloc((void**)&p->d_tab_lstart, sizeof(int) * nent);
+    if (e == cudaSuccess) e = dalloc((void**)&p->d_tab_off, sizeof(long long) * nent);
+    if (e != cudaSuccess) return e;
+    k_rtab_groups<<<dim3((ng + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, kw, ng,
+                                                                       p->d_tab_lstart, p->d_tab_off);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    std::vector<long long> off(nent);
+    e = cudaMemcpy(off.data(), p->d_tab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    long long acc = 0;
+    for (long long i = 0; i < nent; ++i) {
+      const long long r = off[i];
+      off[i] = acc;
+      acc += (long long)kw * r;
+    }
+    p->tab_elems = acc;
+    e = cudaMemcpy(p->d_tab_off, off.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&p->d_tab, (size_t)es * acc);
+    if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_tab_lo, (size_t)es * acc);
+    if (e != cudaSuccess) return e;
+    const dim3 g((ng * kw + 127) / 128, p->mmax + 1);
+    if (p->tc_fmt == 1)
+      k_rtab_fill<__nv_bfloat16><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
+                                                   p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair, ng,
+                                                   (__nv_bfloat16*)p->d_tab, (__nv_bfloat16*)p->d_tab_lo);
+    else
+      k_rtab_fill<__half><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart,
+                                            p->d_tab_off, p->lmax, p->npair, ng, (__half*)p->d_tab,
+                                            (__half*)p->d_tab_lo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // analysis operand
-  size_t elems = (size_t)(p->mmax + 1) * p->ngroup * nn * 32;
-  cudaError_t e = cudaMalloc(&p->d_gt, elems * sizeof(float));
+  e = dalloc(&p->d_gt, (size_t)es * (p->mmax + 1) * p->ngroup * rba * kw);
   if (e != cudaSuccess) return e;
-  p->bytes += elems * sizeof(float);
   // synthesis operand: chunk offsets of each m, then At
   std::vector<long long> ach(p->mmax + 2);
   ach[0] = 0;
-  for (int m = 0; m <= p->mmax; ++m) ach[m + 1] = ach[m] + (p->lmax - m) / 32 + 1;
-  e = cudaMalloc((void**)&p->d_achunk, sizeof(long long) * (p->mmax + 2));
+  for (int m = 0; m <= p->mmax; ++m) ach[m + 1] = ach[m] + (p->lmax - m) / kw + 1;
+  e = dalloc((void**)&p->d_achunk, sizeof(long long) * (p->mmax + 2));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_achunk, ach.data(), sizeof(long long) * (p->mmax + 2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&p->d_at, (size_t)es * ach[p->mmax + 1] * rbs * kw);
+  if (e == cudaSuccess) e = dalloc((void**)&p->d_bmax, sizeof(unsigned) * p->nbatch);
   if (e != cudaSuccess) return e;
-  p->bytes += sizeof(long long) * (p->mmax + 2);
-  e = cudaMemcpy(p->d_achunk, ach.data(), sizeof(long long) * (p->mmax + 2), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return e;
-  elems = (size_t)ach[p->mmax + 1] * nn * 32;
-  e = cudaMalloc(&p->d_at, elems * sizeof(float));
-  if (e != cudaSuccess) return e;
-  p->bytes += elems * sizeof(float);
   // column table
   p->nptile = (p->npair + 127) / 128;
   const long long nent = (long long)(p->mmax + 1) * p->nptile;
-  e = cudaMalloc((void**)&p->d_stab_lstart, sizeof(int) * nent);
+  e = dalloc((void**)&p->d_stab_lstart, sizeof(int) * nent);
+  if (e == cudaSuccess) e = dalloc((void**)&p->d_stab_off, sizeof(long long) * nent);
   if (e != cudaSuccess) return e;
-  p->bytes += sizeof(int) * nent;
-  e = cudaMalloc((void**)&p->d_stab_off, sizeof(long long) * nent);
-  if (e != cudaSuccess) return e;
-  p->bytes += sizeof(long long) * nent;
-  k_stab_tiles<<<dim3((p->nptile + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, p->nptile,
+  k_ctab_tiles<<<dim3((p->nptile + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, kw, p->nptile,
                                                                            p->d_stab_lstart, p->d_stab_off);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -753,64 +1034,90 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   for (long long i = 0; i < nent; ++i) {
     const long long nb = off[i];
     off[i] = acc;
-    acc += nb * 128 * 32;
+    acc += nb * 128 * kw;
   }
   p->stab_elems = acc;
   e = cudaMemcpy(p->d_stab_off, off.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&p->d_stab, (size_t)es * acc);
+  if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_stab_lo, (size_t)es * acc);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&p->d_stab, sizeof(float) * (acc > 0 ? acc : 32));
-  if (e != cudaSuccess) return e;
-  p->bytes += sizeof(float) * (acc > 0 ? acc : 32);
-  k_stab_fill<<<dim3(p->nptile, p->mmax + 1), 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
-                                                           p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair,
-                                                           p->nptile, static_cast<float*>(p->d_stab));
+  const dim3 g(p->nptile, p->mmax + 1);
+  if (mode == 0)
+    k_ctab_fill<float><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_stab_lstart,
+                                         p->d_stab_off, p->lmax, p->npair, p->nptile, (float*)p->d_stab, nullptr);
+  else if (p->tc_fmt == 1)
+    k_ctab_fill<__nv_bfloat16><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
+                                                 p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair, p->nptile,
+                                                 (__nv_bfloat16*)p->d_stab, (__nv_bfloat16*)p->d_stab_lo);
+  else
+    k_ctab_fill<__half><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_stab_lstart,
+                                          p->d_stab_off, p->lmax, p->npair, p->nptile, (__half*)p->d_stab,
+                                          (__half*)p->d_stab_lo);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const unsigned long long at_rows = (unsigned long long)ach[p->mmax + 1] * nn;
-  if (!encode_rows32(p->tm_tab, p->d_tab, (unsigned long long)(p->tab_elems / 32), kTcTile) ||
-      !encode_rows32(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * nn, nn) ||
-      !encode_rows32(p->tm_stab, p->d_stab, (unsigned long long)(acc > 0 ? acc / 32 : 1), 128) ||
-      !encode_rows32(p->tm_at, p->d_at, at_rows, nn)) {
+  // descriptors (the lo maps point at hi where there is no lo table; unused)
+  const void* tablo = p->d_tab_lo ? p->d_tab_lo : p->d_tab;
+  const void* stablo = p->d_stab_lo ? p->d_stab_lo : p->d_stab;
+  const unsigned long long trows = (unsigned long long)(p->tab_elems / kw), srows = (unsigned long long)(acc / kw);
+  if (!encode_rows128(p->tm_tab, p->d_tab, trows, kTcTile, es) ||
+      !encode_rows128(p->tm_tablo, tablo, trows, kTcTile, es) ||
+      !encode_rows128(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * rba, nna, es) ||
+      !encode_rows128(p->tm_stab, p->d_stab, srows, 128, es) ||
+      !encode_rows128(p->tm_stablo, stablo, srows, 128, es) ||
+      !encode_rows128(p->tm_at, p->d_at, (unsigned long long)ach[p->mmax + 1] * rbs, nns, es)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return cudaErrorInvalidValue;
   }
-  p->tc_nn = nn;
+  p->tc_nn_a = nna;
+  p->tc_nn_s = nns;
   return cudaSuccess;
 }
 
-cudaError_t launch_pack_tc(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
-  switch (p->tc_nn) {
-    case 32: return launch_pack_cp<8>(p, b0, nb, use_w, s);
-    case 64: return launch_pack_cp<16>(p, b0, nb, use_w, s);
-    case 128: return launch_pack_cp<32>(p, b0, nb, use_w, s);
+cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
+  if (p->tc_mode) {  // channel scales from the spectra: |S|, |A| <= 2 sqrt(2) w max|component|
+    p->tc_sfac_a = 3.0f * (use_w ? (float)(4.0 * 3.14159265358979323846 / (double)p->npix) : 1.0f);
+    cudaError_t e = absmax(p, (const float*)p->d_spec, 2 * p->nspec, 2 * p->nspec, b0, nb, s);
+    if (e != cudaSuccess) return e;
+  }
+  switch (p->tc_nn_a) {
+    case 32: return pack_gt_t<8>(p, b0, nb, use_w, s);
+    case 64: return pack_gt_t<16>(p, b0, nb, use_w, s);
+    case 128: return pack_gt_t<32>(p, b0, nb, use_w, s);
+    case 256: return pack_gt_t<64>(p, b0, nb, use_w, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
-  switch (p->tc_nn) {
-    case 32: return launch_tile_cp<8, false>(p, alm, b0, nb, mfac, s);
-    case 64: return launch_tile_cp<16, false>(p, alm, b0, nb, mfac, s);
-    case 128: return launch_tile_cp<32, false>(p, alm, b0, nb, mfac, s);
+  switch (p->tc_nn_a) {
+    case 32: return tile_t<8, false>(p, alm, b0, nb, mfac, s);
+    case 64: return tile_t<16, false>(p, alm, b0, nb, mfac, s);
+    case 128: return tile_t<32, false>(p, alm, b0, nb, mfac, s);
+    case 256: return tile_t<64, false>(p, alm, b0, nb, mfac, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_pack_at_tc(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
-  switch (p->tc_nn) {
-    case 32: return launch_pack_at_cp<8>(p, alm, b0, nb, mfac, s);
-    case 64: return launch_pack_at_cp<16>(p, alm, b0, nb, mfac, s);
-    case 128: return launch_pack_at_cp<32>(p, alm, b0, nb, mfac, s);
+cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  if (p->tc_mode) {  // channel scales from alm: |P_l mfac a| <= 1.2 max(mfac, 1) max|component|
+    p->tc_sfac_s = 1.2f * (float)(mfac > 1.0 ? mfac : 1.0);
+    cudaError_t e = absmax(p, alm, 2 * p->nalm, 2 * p->nalm, b0, nb, s);
+    if (e != cudaSuccess) return e;
+  }
+  switch (p->tc_nn_s) {
+    case 32: return pack_at_t<8>(p, alm, b0, nb, mfac, s);
+    case 64: return pack_at_t<16>(p, alm, b0, nb, mfac, s);
+    case 128: return pack_at_t<32>(p, alm, b0, nb, mfac, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s) {
   float* F = static_cast<float*>(p->d_F);
-  switch (p->tc_nn) {
-    case 32: return launch_tile_cp<8, true>(p, F, b0, nb, 1.0, s);
-    case 64: return launch_tile_cp<16, true>(p, F, b0, nb, 1.0, s);
-    case 128: return launch_tile_cp<32, true>(p, F, b0, nb, 1.0, s);
+  switch (p->tc_nn_s) {
+    case 32: return tile_t<8, true>(p, F, b0, nb, 1.0, s);
+    case 64: return tile_t<16, true>(p, F, b0, nb, 1.0, s);
+    case 128: return tile_t<32, true>(p, F, b0, nb, 1.0, s);
     default: return cudaErrorInvalidValue;
   }
 }
