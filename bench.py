@@ -416,15 +416,18 @@ def legendre_roofline(plan, stages, table: bool):
     # tensor-core analysis: the pack reads the spectra and writes the operand
     # Gt[m][group][4 x channels][32] once; the tile kernel reads the table,
     # Gt and writes alm
-    gt_bytes = 4 * (MMAX + 1) * ((2 * NSIDE + 31) // 32) * 32 * 4 * min(64, max(8, 1 << (NBATCH - 1).bit_length()))
+    gt_bytes = 4 * (MMAX + 1) * ((2 * NSIDE + 31) // 32) * 32 * 4 * min(32, max(8, 1 << (NBATCH - 1).bit_length()))
     for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes),
                   ("analysis_operand_pack", spec_bytes + gt_bytes)):
         if k in stages:
             s = stages[k]
             s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
     fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
+    # the tensor-core synthesis reads the column copy of the table and its packed operand
+    ctab_bytes = plan.column_table_bytes if (table and tc) else tab_bytes
+    at_bytes = 4 * sum((LMAX - m) // 32 + 1 for m in range(MMAX + 1)) * 32 * 4 * min(32, max(8, 1 << (NBATCH - 1).bit_length()))
     leg_bytes = {"legendre_analysis": tab_bytes + (gt_bytes if tc else spec_bytes) + alm_bytes,
-                 "legendre_synthesis": tab_bytes + alm_bytes + f_bytes}
+                 "legendre_synthesis": (ctab_bytes + at_bytes + f_bytes) if tc else tab_bytes + alm_bytes + f_bytes}
     for k in ("legendre_analysis", "legendre_synthesis"):
         s = stages[k]
         sec = s["ms_per_launch"] / 1e3
@@ -436,12 +439,15 @@ def legendre_roofline(plan, stages, table: bool):
     dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k]["ms_per_launch"])
     kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
     if table:
-        kname = "k_analysis_tc" if (tc and dom == "legendre_analysis") else kname + "<table>"
+        kname = f"k_legendre_tc<{'analysis' if dom == 'legendre_analysis' else 'synthesis'}>" if tc \
+            else kname + "<table>"
         achieved = stages[dom]["hbm_gbs_algorithmic"]
         return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": HBM_PEAK_GBS,
                 "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": kernel_traffic(kname),
                 "peak_source": HBM_PEAK_SOURCE,
-                "work": f"lambda table {tab_bytes} B + compulsory inputs/outputs {leg_bytes[dom] - tab_bytes} B "
+                "work": f"lambda table {ctab_bytes if (tc and dom == 'legendre_synthesis') else tab_bytes} B "
+                        f"+ compulsory inputs/outputs "
+                        f"{leg_bytes[dom] - (ctab_bytes if (tc and dom == 'legendre_synthesis') else tab_bytes)} B "
                         f"per launch"}
     achieved = stages[dom]["fp64_tflops"]
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,

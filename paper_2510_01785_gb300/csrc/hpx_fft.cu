@@ -148,22 +148,17 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
 
 // Length-2^logm FFT of buf (positions pad8), natural order in and out; needs
 // blockDim.x * 16 >= 2^logm.  Caller has synchronised after filling buf.
+// The radix-2 or radix-4 pass comes last: there Ns R = 2^logm, so its writes
+// are contiguous (as a first pass, with Ns = 1, they would conflict).
 template <bool INV, typename V>
 __device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw) {
-  int Ns = 1, rest = logm;
-  if (rest % 3 == 1) {
-    stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw);
-    Ns <<= 1;
-    rest -= 1;
-  } else if (rest % 3 == 2) {
-    stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw);
-    Ns <<= 2;
-    rest -= 2;
-  }
-  for (; rest > 0; rest -= 3) {
+  int Ns = 1;
+  for (int rest = logm; rest >= 3; rest -= 3) {
     stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw);
     Ns <<= 3;
   }
+  if (logm % 3 == 1) stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw);
+  else if (logm % 3 == 2) stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw);
 }
 
 // DFT of length H of buf[0..H) (positions pad8) in place, natural order:

@@ -449,7 +449,13 @@ struct TcShape {
   static constexpr int kLo = MODE == 0 ? kA : 0;  // lambda remainder buffers (two, alternating by K block)
   static constexpr int kBuf = MODE == 0 ? 2 * NN : NN;  // TMEM columns of one block accumulator
   static constexpr int kTmemCols = 2 * kBuf;
-  static constexpr int kNStage = (200 * 1024 - 2 * kLo) / kStage < 8 ? (200 * 1024 - 2 * kLo) / kStage : 8;
+  // two CTAs per SM where half the tensor memory and half the shared memory
+  // (with at least two stages) suffice: the second CTA's prologue, tail and
+  // epilogue then overlap the first's streaming
+  static constexpr int kStages2 = (110 * 1024 - 2 * kLo) / kStage;
+  static constexpr int kCtas = (kTmemCols <= 256 && kStages2 >= 2 && NN <= 64) ? 2 : 1;
+  static constexpr int kBudget = kCtas == 2 ? 110 * 1024 : 200 * 1024;
+  static constexpr int kNStage = (kBudget - 2 * kLo) / kStage < 8 ? (kBudget - 2 * kLo) / kStage : 8;
   static constexpr size_t kSmem =
       (size_t)kNStage * kStage + 2 * kLo + 1024 /* base alignment */ + 2048 /* barriers, lists */;
   static_assert(kNStage >= 2 && kTmemCols <= 512 && kTmemCols >= 32, "shape");
@@ -503,7 +509,7 @@ struct TcArgs {
 // warp-collective tcgen05.ld stays convergent), waits for what it started,
 // and the CTA records the timeout.
 template <int NN, bool SYN, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, TcShape<NN, MODE>::kCtas)
 k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   using S = TcShape<NN, MODE>;
