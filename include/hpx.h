@@ -189,6 +189,19 @@ hpx_status hpx_alm2map_grad(hpx_plan plan, const void* grad_map, void* grad_alm,
 hpx_status hpx_map2alm_grad(hpx_plan plan, const void* grad_alm, void* grad_map,
                             hpx_stream_t stream);
 
+/* Analysis with iterative refinement (Sec. II-A Eq. 4): a^0 = A f, then
+ * niter times r = f - S a^k, a^{k+1} = a^k + A r, with A = map2alm and S =
+ * alm2map of this plan.  Each step reduces the residual of a band-limited
+ * map; the cost is (1 + 2 niter) transforms.
+ *   map : device, [nbatch][npix] real (input f).
+ *   alm : device, [nbatch][nalm] complex (output a^niter).
+ *   niter : 0 .. 1000 (0: plain hpx_map2alm).
+ * A map-sized and an alm-sized plan-owned buffer are allocated on the first
+ * call with niter > 0 and counted by hpx_plan_device_bytes.  Same stream
+ * semantics as the transforms. */
+hpx_status hpx_map2alm_iter(hpx_plan plan, const void* map, void* alm, int niter,
+                            hpx_stream_t stream);
+
 /* Host-buffer forms of the two transforms: copy the input from host memory
  * (pinned or pageable) into plan-owned device buffers, run the transform on
  * the stream, copy the result back and wait for the stream.  The device I/O
@@ -264,6 +277,36 @@ size_t hpx_plan_column_table_bytes(hpx_plan plan);
  * clears the record; HPX_OK otherwise.  The host-buffer entry points check
  * it themselves. */
 hpx_status hpx_plan_device_status(hpx_plan plan);
+
+/* Pixel layouts (Sec. III-B).
+ *   HPX_RING   : rings north to south, pixels by increasing longitude.
+ *   HPX_NESTED : face f (0..11) times nside^2 plus the Morton (Z-order)
+ *                interleave of the face coordinates x (even bits) and y
+ *                (odd bits); x + y grows northward, x - y eastward.
+ *   HPX_FLAT   : f nside^2 + y nside + x (row-major face images).
+ * Face f's rings and longitudes follow Gorski et al. 2005 (faces 0-3 north,
+ * 4-7 equatorial, 8-11 south, each ordered eastward from longitude 0). */
+typedef enum { HPX_RING = 0, HPX_NESTED = 1, HPX_FLAT = 2 } hpx_layout;
+
+/* Reorders nbatch maps of 12 nside^2 elements of elem_bytes (4, 8 or 16)
+ * bytes from layout `from` to layout `to` through the (x, y, f)
+ * representation: out[b][t] = in[b][s(t)], s(t) the `from` index of the
+ * pixel with `to` index t.  in, out: device, distinct, aligned to the
+ * element size.  nside: power of two, 1..8192.  Allocates nothing, needs no
+ * plan; stream-ordered. */
+hpx_status hpx_reorder(int nside, int nbatch, size_t elem_bytes, hpx_layout from,
+                       hpx_layout to, const void* in, void* out,
+                       hpx_stream_t stream);
+
+/* index[t] (device, 12 nside^2 int64) = the `from` index of the pixel whose
+ * `to` index is t (the gather map hpx_reorder applies). */
+hpx_status hpx_layout_index(int nside, hpx_layout from, hpx_layout to,
+                            int64_t* index, hpx_stream_t stream);
+
+/* Synchronises the current device and reports (HPX_ERR_INVALID) whether any
+ * reorder or index kernel since the last call met an index without an
+ * (x, y, f) representation (impossible for valid arguments); clears it. */
+hpx_status hpx_layout_status(void);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* hpx_last_error(void);

@@ -258,6 +258,21 @@ def alm2map(alm, nside, lmax, mmax, tier="sep", nthreads=0):
     return synthesis_sep(alm, nside, lmax, mmax, None, None, nthreads)
 
 
+def map2alm_iter(maps, lmax, mmax, niter, nthreads=0):
+    """Iterative refinement (Sec. II-A Eq. 4): a^0 = A f, then niter times
+    r = f - S a^k and a^{k+1} = a^k + A r, with A = map2alm and S = alm2map.
+    Returns the list [a^0, ..., a^niter]."""
+    maps = _as_maps(maps)
+    nside = int(round(np.sqrt(maps.shape[1] / 12)))
+    a = map2alm(maps, lmax, mmax, nthreads=nthreads)
+    out = [a]
+    for _ in range(niter):
+        r = maps - alm2map(a, nside, lmax, mmax, nthreads=nthreads)
+        a = a + map2alm(r, lmax, mmax, nthreads=nthreads)
+        out.append(a)
+    return out
+
+
 def alm2map_adjoint(maps, lmax, mmax, tier="sep", nthreads=0):
     """Y^dagger p: the adjoint of synthesis (Sec. III-F), i.e. the analysis
     sum with unit weights."""
@@ -279,3 +294,67 @@ def inner_full(a, b, lmax, mmax):
     _, ms = lm_arrays(lmax, mmax)
     wt = np.where(ms == 0, 1.0, 2.0)
     return float(np.sum(wt * np.real(np.conj(a) * b)))
+
+
+# ---------------------------------------------------------------------------
+# pixel layouts (Sec. III-B), by geometry
+# ---------------------------------------------------------------------------
+_FACE_RING = np.array([2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4])
+_FACE_LON = np.array([1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7])
+
+
+def face_pixel_centres(nside):
+    """(z, phi) of the centres of face pixels, array order [f][y][x] (the
+    flat layout), from the inverse HEALPix projection (Gorski et al. 2005;
+    Calabretta & Roukema 2007): the face is a square turned by 45 degrees in
+    the (t, u) plane, centred at t = pi/4 * lon_f, u = pi/4 * (3 - ring_f),
+    with x + y northward and x - y eastward; |u| <= pi/4 is the equatorial
+    zone z = 8u / (3 pi), phi = t; beyond it sigma = 2 - 4|u|/pi,
+    |z| = 1 - sigma^2/3 and phi = t_c + (t - t_c)/sigma about the face's
+    central meridian t_c."""
+    f, y, x = np.meshgrid(np.arange(12), np.arange(nside), np.arange(nside), indexing="ij")
+    a, b = (x + 0.5) / nside, (y + 0.5) / nside
+    tc = _FACE_LON[f] * np.pi / 4
+    t = tc + np.pi / 4 * (a - b)
+    u = (3 - _FACE_RING[f]) * np.pi / 4 + np.pi / 4 * (a + b - 1)
+    z = 8 * u / (3 * np.pi)
+    phi = t.copy()
+    pol = np.abs(u) > np.pi / 4
+    sig = 2 - 4 * np.abs(u[pol]) / np.pi
+    z[pol] = np.sign(u[pol]) * (1 - sig ** 2 / 3)
+    phi[pol] = tc[pol] + (t[pol] - tc[pol]) / sig
+    return z.ravel(), np.mod(phi.ravel(), 2 * np.pi)
+
+
+def _morton(x, y):
+    """Interleave: x to the even bits, y to the odd bits."""
+    out = np.zeros_like(x)
+    for bit in range(16):
+        out |= ((x >> bit) & 1) << (2 * bit)
+        out |= ((y >> bit) & 1) << (2 * bit + 1)
+    return out
+
+
+def layout_permutations(nside):
+    """For every flat-order pixel [f][y][x]: its RING index (by matching its
+    geometric centre to the ring pixel centres of Sec. III-A), its NESTED
+    index (f nside^2 + Morton(x, y)) and its FLAT index."""
+    z, phi = face_pixel_centres(nside)
+    g = ring_geometry(nside)
+    zr = np.asarray(g["z"])
+    ring = np.argmin(np.abs(z[:, None] - zr[None, :]), axis=1)
+    N, sig = np.asarray(g["nphi"])[ring], np.asarray(g["sigma"])[ring]
+    k = np.mod(np.rint((phi * N / np.pi - sig) / 2).astype(np.int64), N)
+    ring_idx = np.asarray(g["start"])[ring] + k
+    f, y, x = np.meshgrid(np.arange(12), np.arange(nside), np.arange(nside), indexing="ij")
+    nest_idx = (f * nside * nside + _morton(x, y)).ravel()
+    flat_idx = np.arange(12 * nside * nside)
+    return {"ring": ring_idx.astype(np.int64), "nested": nest_idx.astype(np.int64), "flat": flat_idx}
+
+
+def layout_index(nside, src, dst):
+    """index[t] = the src index of the pixel whose dst index is t."""
+    perm = layout_permutations(nside)
+    idx = np.empty(12 * nside * nside, np.int64)
+    idx[perm[dst]] = perm[src]
+    return idx

@@ -25,7 +25,7 @@ import torch
 from . import _lib
 from ._lib import check, lib
 
-__all__ = ["Plan", "nalm", "get_plan", "DTYPES"]
+__all__ = ["Plan", "nalm", "get_plan", "DTYPES", "reorder", "layout_index", "LAYOUTS"]
 
 DTYPES = {
     "f64": _lib.HPX_F64,
@@ -196,6 +196,16 @@ class Plan:
                                   ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_alm2map_n")
         return dst
 
+    def map2alm_iter(self, maps: torch.Tensor, niter: int, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        """Analysis with niter steps of iterative refinement (Sec. II-A Eq. 4)."""
+        maps = self._map(maps, "maps")
+        out = self.empty_alm() if out is None else self._alm(out, "out")
+        check(lib().hpx_map2alm_iter(self._h, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     int(niter), ctypes.c_void_p(_stream_handle(stream, self.device))),
+              "hpx_map2alm_iter")
+        return out
+
     def alm2map_grad(self, grad_map: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Backward of alm2map: D Y^dagger g (dL/dRe + i dL/dIm per coefficient)."""
         src = self._map(grad_map, "grad_map")
@@ -263,6 +273,36 @@ class Plan:
         check(lib().hpx_plan_ring_table(self._h, P(start.ctypes.data), P(nphi.ctypes.data), P(z.ctypes.data),
                                         P(sinth.ctypes.data), P(sigma.ctypes.data)), "hpx_plan_ring_table")
         return {"start": start, "nphi": nphi, "z": z, "sinth": sinth, "sigma": sigma}
+
+
+LAYOUTS = {"ring": _lib.HPX_RING, "nested": _lib.HPX_NESTED, "flat": _lib.HPX_FLAT}
+
+
+def reorder(maps: torch.Tensor, nside: int, src: str, dst: str, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Maps [..., 12 nside^2] on the GPU from layout src to dst (Sec. III-B,
+    through the (x, y, f) representation)."""
+    if not (isinstance(maps, torch.Tensor) and maps.is_cuda and maps.is_contiguous()):
+        raise ValueError("maps must be a contiguous CUDA tensor")
+    npix = 12 * nside * nside
+    if maps.shape[-1] != npix:
+        raise ValueError(f"last dimension must be {npix}")
+    out = torch.empty_like(maps) if out is None else out
+    nb = maps.numel() // npix
+    check(lib().hpx_reorder(nside, nb, maps.element_size(), LAYOUTS[src], LAYOUTS[dst],
+                            ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                            ctypes.c_void_p(_stream_handle(stream, maps.device))), "hpx_reorder")
+    return out
+
+
+def layout_index(nside: int, src: str, dst: str, device=None) -> torch.Tensor:
+    """int64 [12 nside^2]: index[t] = the src index of the pixel whose dst index is t."""
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    idx = torch.empty(12 * nside * nside, dtype=torch.int64, device=device)
+    check(lib().hpx_layout_index(nside, LAYOUTS[src], LAYOUTS[dst], ctypes.c_void_p(idx.data_ptr()),
+                                 ctypes.c_void_p(_stream_handle(None, device))), "hpx_layout_index")
+    check(lib().hpx_layout_status(), "hpx_layout_status")
+    return idx
 
 
 _plan_cache: dict = {}

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libhpx.so")
 
 HPX_F64, HPX_F32, HPX_F32_BF16, HPX_F32_BF16X3, HPX_F32_FP16, HPX_F32_FP16X3 = range(6)
 HPX_PLAN_LAMBDA_RECOMPUTE, HPX_PLAN_LAMBDA_TABLE, HPX_PLAN_TENSOR_CORES = 0, 1, 2
+HPX_RING, HPX_NESTED, HPX_FLAT = 0, 1, 2
 STATUS = {0: "HPX_OK", 1: "HPX_ERR_INVALID", 2: "HPX_ERR_NOMEM", 3: "HPX_ERR_CUDA",
           4: "HPX_ERR_TIMEOUT", 5: "HPX_ERR_UNSUPPORTED"}
 
@@ -35,6 +36,7 @@ SIGNATURES = {
     "hpx_alm2map_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_host": (_I, [_P, _P, _P, _P]),
+    "hpx_map2alm_iter": (_I, [_P, _P, _P, _I, _P]),
     "hpx_alm2map_host": (_I, [_P, _P, _P, _P]),
     "hpx_plan_device_bytes": (_SZ, [_P]),
     "hpx_plan_ring_table": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -45,6 +47,9 @@ SIGNATURES = {
     "hpx_plan_column_table_bytes": (_SZ, [_P]),
     "hpx_plan_estimate_bytes": (_SZ, [_I, _I, _I, _I, _I, _U]),
     "hpx_plan_device_status": (_I, [_P]),
+    "hpx_reorder": (_I, [_I, _I, _SZ, _I, _I, _P, _P, _P]),
+    "hpx_layout_index": (_I, [_I, _I, _I, _P, _P]),
+    "hpx_layout_status": (_I, []),
     "hpx_last_error": (ctypes.c_char_p, []),
 }
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(LIBDIR, "libhpx.so")
-SOURCES = ["hpx_plan.cu", "hpx_fft.cu", "hpx_legendre.cu", "hpx_tc.cu", "hpx_noalloc.cu"]
+SOURCES = ["hpx_plan.cu", "hpx_fft.cu", "hpx_legendre.cu", "hpx_tc.cu", "hpx_reorder.cu", "hpx_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

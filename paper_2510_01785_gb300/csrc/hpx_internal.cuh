@@ -72,6 +72,8 @@ struct hpx_plan_s {
   void* d_F;           // workspace [nbatch][nring][mmax+1] C2<T>
   void* d_io_map;      // device I/O buffers of the host-buffer entry points (lazy)
   void* d_io_alm;
+  void* d_it_map;      // iterative refinement: synthesis / residual map and correction (lazy)
+  void* d_it_alm;
   void* timing;        // per-stage CUDA events while timing is enabled
   void* d_tab;         // plan-resident lambda table (HPX_PLAN_LAMBDA_TABLE), C2<T>'s real type
   long long* d_tab_off;  // [mmax+1][ngroup] first element of each (m, 32-pair group)

@@ -121,7 +121,8 @@ static void plan_free(hpx_plan_s* p) {
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
-                  p->d_stab, p->d_stab_off, p->d_stab_lstart, p->d_tab_lo, p->d_stab_lo, p->d_bmax};
+                  p->d_stab, p->d_stab_off, p->d_stab_lstart, p->d_tab_lo, p->d_stab_lo, p->d_bmax,
+                  p->d_it_map, p->d_it_alm};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->timing) {
@@ -243,6 +244,25 @@ static hpx_status transform(hpx_plan p, const void* in, void* out, hpx_stream_t 
                             : run_synthesis<float>(p, in, out, weighted, mfac, s);
   if (e != cudaSuccess) return cuda_fail(e, name);
   return HPX_OK;
+}
+
+// Iterative refinement (Sec. II-A Eq. 4): r = f - S a, then a += A r.
+template <typename T>
+__global__ void k_residual(const T* __restrict__ f, T* __restrict__ r, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = f[i] - r[i];
+}
+template <typename T>
+__global__ void k_accumulate(T* __restrict__ a, const T* __restrict__ d, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] += d[i];
+}
+template <typename T>
+static cudaError_t elementwise(bool residual, const void* x, void* y, long long n, cudaStream_t s) {
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (residual) k_residual<T><<<grid, 256, 0, s>>>(static_cast<const T*>(x), static_cast<T*>(y), n);
+  else k_accumulate<T><<<grid, 256, 0, s>>>(static_cast<T*>(y), static_cast<const T*>(x), n);
+  return cudaGetLastError();
 }
 
 }  // namespace hpx
@@ -528,6 +548,45 @@ static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
   return read_status(p);
+}
+
+hpx_status hpx_map2alm_iter(hpx_plan p, const void* map, void* alm, int niter, hpx_stream_t stream) {
+  hpx_status st = check_call(p, map, alm);
+  if (st != HPX_OK) return st;
+  if (niter < 0 || niter > 1000) {
+    set_error("hpx_map2alm_iter: niter must be in [0, 1000], got %d", niter);
+    return HPX_ERR_INVALID;
+  }
+  st = hpx_map2alm(p, map, alm, stream);
+  if (st != HPX_OK || niter == 0) return st;
+  DeviceGuard g(p->device);
+  const size_t rs = real_size(p);
+  const long long nmap = (long long)p->nbatch * p->npix, nalm2 = 2LL * p->nbatch * p->nalm;
+  if (!p->d_it_map) {
+    cudaError_t e = cudaMalloc(&p->d_it_map, rs * nmap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (refinement buffer)");
+    p->bytes += rs * nmap;
+  }
+  if (!p->d_it_alm) {
+    cudaError_t e = cudaMalloc(&p->d_it_alm, rs * nalm2);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (refinement buffer)");
+    p->bytes += rs * nalm2;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool f64 = p->dtype == HPX_F64;
+  for (int k = 0; k < niter; ++k) {
+    st = hpx_alm2map(p, alm, p->d_it_map, stream);  // S a
+    if (st != HPX_OK) return st;
+    cudaError_t e = f64 ? elementwise<double>(true, map, p->d_it_map, nmap, s)
+                        : elementwise<float>(true, map, p->d_it_map, nmap, s);  // r = f - S a
+    if (e != cudaSuccess) return cuda_fail(e, "hpx_map2alm_iter");
+    st = hpx_map2alm(p, p->d_it_map, p->d_it_alm, stream);  // A r
+    if (st != HPX_OK) return st;
+    e = f64 ? elementwise<double>(false, p->d_it_alm, alm, nalm2, s)
+            : elementwise<float>(false, p->d_it_alm, alm, nalm2, s);  // a += A r
+    if (e != cudaSuccess) return cuda_fail(e, "hpx_map2alm_iter");
+  }
+  return HPX_OK;
 }
 
 hpx_status hpx_plan_device_status(hpx_plan plan) {
