@@ -271,6 +271,16 @@ size_t hpx_plan_table_bytes(hpx_plan plan);
  * (0 without the tensor-core path). */
 size_t hpx_plan_column_table_bytes(hpx_plan plan);
 
+/* Per-ring quadrature weights (Sec. IV-A; NEXT to Eq. 1's equal 4 pi/Npix):
+ * w[y] for the 4 nside - 1 rings, north to south (host array, copied).
+ * Replaces the weight every later hpx_map2alm / hpx_map2alm_adjoint /
+ * hpx_map2alm_grad of this plan applies to ring y (the unweighted operators
+ * are unaffected).  Synchronises the device.  Pixel weights are applied by
+ * weighting the map and calling hpx_alm2map_adjoint.
+ * Errors: HPX_ERR_INVALID (count differs from the ring count, a weight not
+ * finite). */
+hpx_status hpx_plan_set_ring_weights(hpx_plan plan, const double* w, int n);
+
 /* Status of the plan's device-side waits.  Synchronises the plan's device,
  * returns HPX_ERR_TIMEOUT if a bounded wait inside one of the plan's kernels
  * expired since the last call (that transform's output is incomplete) and

@@ -102,6 +102,13 @@ class Plan:
     def device_bytes(self) -> int:
         return int(lib().hpx_plan_device_bytes(self._h))
 
+    def set_ring_weights(self, w) -> None:
+        """Per-ring quadrature weights (4 nside - 1 values, north to south) for
+        the weighted operators; see weights.ring_weights for a computed set."""
+        w = np.ascontiguousarray(np.asarray(w, np.float64))
+        check(lib().hpx_plan_set_ring_weights(self._h, ctypes.c_void_p(w.ctypes.data), int(w.size)),
+              "hpx_plan_set_ring_weights")
+
     def device_status(self) -> None:
         """Synchronise and raise HpxError(HPX_ERR_TIMEOUT) if a bounded
         device-side wait of this plan's kernels expired since the last check."""

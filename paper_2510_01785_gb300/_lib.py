@@ -47,6 +47,7 @@ SIGNATURES = {
     "hpx_plan_column_table_bytes": (_SZ, [_P]),
     "hpx_plan_estimate_bytes": (_SZ, [_I, _I, _I, _I, _I, _U]),
     "hpx_plan_device_status": (_I, [_P]),
+    "hpx_plan_set_ring_weights": (_I, [_P, _P, _I]),
     "hpx_reorder": (_I, [_I, _I, _SZ, _I, _I, _P, _P, _P]),
     "hpx_layout_index": (_I, [_I, _I, _I, _P, _P]),
     "hpx_layout_status": (_I, []),

@@ -103,6 +103,7 @@ struct hpx_plan_s {
   alignas(64) unsigned char tm_stablo[128];
   alignas(64) unsigned char tm_at[128];
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
+  double w_max;        // largest ring weight (4 pi / Npix unless set)
   size_t bytes;
 };
 

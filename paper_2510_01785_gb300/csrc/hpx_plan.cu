@@ -1,6 +1,8 @@
 // libhpx C ABI: plans, the device-built ring geometry, and the transform
 // entry points declared in hpx.h.
 #include <cstdarg>
+#include <cstddef>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -322,6 +324,7 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
   p->dtype = dtype;
   p->flags = flags;
   p->nring = 4 * nside - 1;
+  p->w_max = 4.0 * 3.14159265358979323846 / (12.0 * (double)nside * (double)nside);
   p->npair = 2 * nside;
   p->npix = 12LL * nside * nside;
   p->nalm = hpx_nalm(lmax, mmax);
@@ -586,6 +589,34 @@ hpx_status hpx_map2alm_iter(hpx_plan p, const void* map, void* alm, int niter, h
             : elementwise<float>(false, p->d_it_alm, alm, nalm2, s);  // a += A r
     if (e != cudaSuccess) return cuda_fail(e, "hpx_map2alm_iter");
   }
+  return HPX_OK;
+}
+
+hpx_status hpx_plan_set_ring_weights(hpx_plan p, const double* w, int n) {
+  if (!p || !w) {
+    set_error("null argument");
+    return HPX_ERR_INVALID;
+  }
+  if (n != p->nring) {
+    set_error("hpx_plan_set_ring_weights: need %d weights (one per ring), got %d", p->nring, n);
+    return HPX_ERR_INVALID;
+  }
+  double wmax = 0.0;
+  for (int y = 0; y < n; ++y) {
+    if (!(w[y] == w[y]) || w[y] > 1e300 || w[y] < -1e300) {
+      set_error("hpx_plan_set_ring_weights: weight %d is not finite", y);
+      return HPX_ERR_INVALID;
+    }
+    wmax = fmax(wmax, fabs(w[y]));
+  }
+  DeviceGuard g(p->device);
+  // the w field of every RingInfo, one strided copy
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(reinterpret_cast<char*>(p->d_ring) + offsetof(RingInfo, w), sizeof(RingInfo), w, sizeof(double),
+                     sizeof(double), (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "hpx_plan_set_ring_weights");
+  p->w_max = wmax;
   return HPX_OK;
 }
 

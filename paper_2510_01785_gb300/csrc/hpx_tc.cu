@@ -1081,7 +1081,7 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
 
 cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
   if (p->tc_mode) {  // channel scales from the spectra: |S|, |A| <= 2 sqrt(2) w max|component|
-    p->tc_sfac_a = 3.0f * (use_w ? (float)(4.0 * 3.14159265358979323846 / (double)p->npix) : 1.0f);
+    p->tc_sfac_a = 3.0f * (use_w ? (float)p->w_max : 1.0f);
     cudaError_t e = absmax(p, (const float*)p->d_spec, 2 * p->nspec, 2 * p->nspec, b0, nb, s);
     if (e != cudaSuccess) return e;
   }

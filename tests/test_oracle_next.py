@@ -109,3 +109,37 @@ def test_layout_nested_hierarchy(nside):
     sinth = np.sqrt(np.maximum(1 - zpn ** 2, 1e-300))
     assert np.max(np.abs(zmean - zpn)) < 0.25 * size
     assert np.max(dphi * sinth) < 0.25 * size
+
+
+# ---------------------------------------------------------------------------
+# ring quadrature weights (Sec. IV-A)
+# ---------------------------------------------------------------------------
+from paper_2510_01785_gb300 import weights as hw  # noqa: E402
+
+
+@pytest.mark.parametrize("nside", [1, 4, 16, 64])
+def test_ring_latitudes_match_the_oracle_geometry(nside):
+    z, N = hw.ring_latitudes(nside)
+    g = oracle.ring_geometry(nside)
+    assert np.array_equal(N, g["nphi"])
+    assert np.max(np.abs(z - g["z"])) < 1e-15
+
+
+@pytest.mark.parametrize("nside,lmax", [(4, 8), (16, 32), (16, 47), (64, 128)])
+def test_ring_weights_properties(nside, lmax):
+    w = hw.ring_weights(nside, lmax)
+    z, N = hw.ring_latitudes(nside)
+    weq = np.full(4 * nside - 1, 4 * np.pi / (12 * nside * nside))
+    assert np.allclose(w, w[::-1], rtol=0, atol=1e-18)                  # north/south symmetric
+    assert abs(np.sum(N * w) - 4 * np.pi) < 1e-12                        # total area
+    assert hw.quadrature_residual(w, nside, lmax) <= hw.quadrature_residual(weq, nside, lmax)
+    assert np.all(np.abs(w / weq - 1) < 0.25)  # the Tikhonov term keeps them near equal (15% at 16, 47)
+
+
+@pytest.mark.parametrize("nside,lmax", [(16, 32), (64, 128)])
+def test_ring_weights_improve_band_limited_analysis(nside, lmax):
+    a = syn.gaussian_alm(700 + nside, lmax, lmax, 1, power=1.0)
+    f = oracle.alm2map(a, nside, lmax, lmax)
+    e_eq = np.linalg.norm(oracle.map2alm(f, lmax, lmax) - a)
+    e_w = np.linalg.norm(oracle.analysis(f, lmax, lmax, weights=hw.ring_weights(nside, lmax)) - a)
+    assert e_w < e_eq
