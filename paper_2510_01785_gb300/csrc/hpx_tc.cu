@@ -112,6 +112,12 @@ __device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uin
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// A operand in tensor memory (lane = row, one 32-bit column per K element)
+__device__ __forceinline__ void umma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -126,6 +132,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 consecutive columns of this warp's 32 TMEM lanes, complete on return.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 // x rounded to the nearest TF32 value (ties away from zero): the 13 low
 // mantissa bits rounded into the upper 19.  Finite inputs of table and
 // spectrum magnitude only (no overflow to infinity can occur there).
@@ -446,9 +464,14 @@ struct TcShape {
   static constexpr int kA = kTcTile * 128;  // lambda tile bytes: 128 rows x 128 bytes
   static constexpr int kG = NN * 128;       // B tile bytes (Gt or At)
   static constexpr int kStage = MODE == 0 ? kA + 2 * kG : MODE == 1 ? kA + kG : 2 * kA + 2 * kG;
-  static constexpr int kLo = MODE == 0 ? kA : 0;  // lambda remainder buffers (two, alternating by K block)
+  // MODE 0: the lambda remainders go to tensor memory (32 columns per K
+  // block, two buffers) where that keeps the CTA within 256 columns (N = 32),
+  // else to two shared-memory buffers
+  static constexpr bool kLoTmem = MODE == 0 && NN == 32;
+  static constexpr int kLo = MODE == 0 && !kLoTmem ? kA : 0;
   static constexpr int kBuf = MODE == 0 ? 2 * NN : NN;  // TMEM columns of one block accumulator
-  static constexpr int kTmemCols = 2 * kBuf;
+  static constexpr int kLoCol = 2 * kBuf;                // first TMEM column of the remainder buffers
+  static constexpr int kTmemCols = kLoTmem ? 256 : 2 * kBuf;
   // two CTAs per SM where half the tensor memory and half the shared memory
   // (with at least two stages) suffice: the second CTA's prologue, tail and
   // epilogue then overlap the first's streaming
@@ -459,6 +482,7 @@ struct TcShape {
   static constexpr size_t kSmem =
       (size_t)kNStage * kStage + 2 * kLo + 1024 /* base alignment */ + 2048 /* barriers, lists */;
   static_assert(kNStage >= 2 && kTmemCols <= 512 && kTmemCols >= 32, "shape");
+  static_assert(!kLoTmem || kLoCol + 64 <= kTmemCols, "remainder buffers inside the allocation");
 };
 
 constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, warp 5 issues products
@@ -650,7 +674,10 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
           const uint32_t off = 32u * j;
           if constexpr (MODE == 0) {
             umma_tf32(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id2, j > 0 ? 1u : 0u);
-            umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
+            if constexpr (S::kLoTmem)  // lo(L) from tensor memory: lane = row, 8 columns per step
+              umma_tf32_ta(d, tmem + (uint32_t)(S::kLoCol + b * 32 + 8 * j), sdesc_sw128(aB + off), id1, 1u);
+            else
+              umma_tf32(d, sdesc_sw128(aLlo + off), sdesc_sw128(aB + off), id1, 1u);
           } else {
             umma_f16(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id1, j > 0 ? 1u : 0u);
             if constexpr (MODE == 2) {
@@ -712,20 +739,38 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const int s = k % NS, b = k & 1;
       if (MODE == 0) {
         if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
+        if constexpr (S::kLoTmem) alive = __all_sync(0xffffffffu, alive);  // the TMEM store is warp-collective
         if (alive) {
           // elementwise, so the swizzle does not matter; consecutive threads
           // take consecutive 16-byte words.  Remainder buffer b was last read
           // by block k-2's products, complete since this thread drained that
           // block in the previous iteration.
-          const float4* x = reinterpret_cast<const float4*>(sL(s));
-          float4* xlo = reinterpret_cast<float4*>(sLlo(s, b));
+          if constexpr (S::kLoTmem) {
+            // this thread's row t of the tile (128 bytes, 16-byte chunks
+            // permuted by the swizzle: chunk c at c ^ (t mod 8)) to TMEM lane t
+            const unsigned char* row = sL(s) + t * 128;
+            uint32_t v[32];
 #pragma unroll
-          for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
+            for (int c = 0; c < 8; ++c) {
+              const float4 q = tf32_rem4(*reinterpret_cast<const float4*>(row + ((c ^ (t & 7)) << 4)));
+              v[4 * c] = __float_as_uint(q.x);
+              v[4 * c + 1] = __float_as_uint(q.y);
+              v[4 * c + 2] = __float_as_uint(q.z);
+              v[4 * c + 3] = __float_as_uint(q.w);
+            }
+            tmem_st32(trow + (uint32_t)(S::kLoCol + b * 32), v);
+          } else {
+            const float4* x = reinterpret_cast<const float4*>(sL(s));
+            float4* xlo = reinterpret_cast<float4*>(sLlo(s, b));
+#pragma unroll
+            for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
+          }
           const float4* y = reinterpret_cast<const float4*>(sB(s));
           float4* ylo = reinterpret_cast<float4*>(sBlo(s));
 #pragma unroll
           for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if constexpr (S::kLoTmem) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(&conv[s]);
         }
       }
