@@ -303,6 +303,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     plan_s = time.perf_counter() - t0
     plan_bytes = plan.device_bytes
+    tab_bytes_row, tab_bytes_col = plan.table_bytes, plan.column_table_bytes
     tab = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
     plan.device_status()
     roofline = legendre_roofline(plan, tab["stages"], table=True)
@@ -345,6 +346,7 @@ def run_ours(args):
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
+                         "table_bytes": tab_bytes_row, "column_table_bytes": tab_bytes_col,
                          "significant_triples": active, "all_triples": total},
                 "cuda_core_table": {"value": cc["value"], "ms_per_step": cc["t_max"] / args.steps,
                                     "roofline": cc["roofline"], "stages": cc["stages"], "clocks": cc["clocks"]},
