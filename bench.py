@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run (config 5)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run (config 3)")
+    ap.add_argument("--no-next", action="store_true", help="skip the reorder / refinement measurements")
+    ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core table measurement")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-drain", type=float, default=15.0)
@@ -315,6 +317,14 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = measure_e2e(plan, maps, alm_in, dist, dev, args.steps, world)
 
+    next_rows = run_next_rows(plan, maps, args, dev) if not args.no_next else None
+
+    ooc = None
+    if not args.no_ooc:
+        plan.close()
+        torch.cuda.empty_cache()
+        ooc = run_out_of_core(args, dist, dev, world, gpu_index)
+
     mixed = None
     if not args.no_mixed:
         plan.close()
@@ -345,6 +355,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
+                "next_rows": next_rows, "out_of_core": ooc,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "table_bytes": tab_bytes_row, "column_table_bytes": tab_bytes_col,
                          "significant_triples": active, "all_triples": total},
@@ -539,6 +550,100 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
     out["sustainable_point"] = {"offered_rps": len(sreqs) / duration, "wall_s": swall, "batches": ssrv.batches,
                                 "transforms_per_s": sum(r.nch for r in sreqs if r.t_done is not None) / swall,
                                 **srep}
+    return out
+
+
+def run_next_rows(plan, maps, args, dev) -> dict:
+    """The rows after the transforms, on the benchmark's plan and maps:
+    RING -> NESTED -> FLAT -> RING reorders (Sec. III-B; HBM-bound gathers,
+    algorithmic bytes = read + write of the maps) and iterative refinement
+    (Sec. II-A Eq. 4; one step = one synthesis + one analysis)."""
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    nbytes = 2 * maps.numel() * maps.element_size()
+    bufs = [torch.empty_like(maps) for _ in range(3)]
+    hops = (("ring", "nested"), ("nested", "flat"), ("flat", "ring"))
+
+    def chain():
+        src = maps
+        for (a, b), dst in zip(hops, bufs):
+            hpx.reorder(src, NSIDE, a, b, out=dst)
+            src = dst
+    for _ in range(args.warmup):
+        chain()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        chain()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / (3 * args.steps)
+    assert torch.equal(bufs[2], maps)
+    out["reorder"] = {"ms_per_reorder": ms, "bytes_per_reorder": nbytes, "hbm_gbs": nbytes / ms / 1e6,
+                      "frac_of_peak": nbytes / ms / 1e6 / HBM_PEAK_GBS, "channels": int(maps.shape[0]),
+                      "note": "mean of ring->nested, nested->flat, flat->ring gathers"}
+    alm = plan.empty_alm()
+    plan.map2alm_iter(maps, 1, out=alm)
+    torch.cuda.synchronize(dev)
+    times = {}
+    for k in (0, 2):
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.map2alm_iter(maps, k, out=alm)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times[k] = e0.elapsed_time(e1) / args.steps
+    out["refinement"] = {"ms_no_iteration": times[0], "ms_per_iteration": (times[2] - times[0]) / 2,
+                         "note": "one iteration = one synthesis + one analysis + two elementwise kernels"}
+    return out
+
+
+def run_out_of_core(args, dist, dev, world, gpu_index) -> dict:
+    """Out-of-core tables (Sec. III-G) against resident tables and against
+    recomputing lambda, at Nside 512, lmax 1535, 8 FP32 channels (tables of
+    8 GB: small enough to pin on the host here, big enough to stream): one
+    step per plan, same inputs; the streamed plan's tile kernels wait for
+    their table slices, so its step time shows the host-to-device stream."""
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import synthetic as syn
+
+    ns, lmax, nb = 512, 1535, 8
+    alm_in = torch.from_numpy(syn.gaussian_alm(SEED + 41, lmax, lmax, nb, power=2.0).astype(np.complex64)).to(dev)
+    out = {"config": {"nside": ns, "lmax": lmax, "nbatch": nb, "dtype": "f32"}}
+    maps = None
+    ref = None
+    for name, kw in (("resident", dict(lambda_table=True, tensor_cores=True)),
+                     ("out_of_core", dict(out_of_core=True)),
+                     ("recompute", {})):
+        t0 = time.perf_counter()
+        plan = hpx.Plan(ns, lmax, lmax, nb, "f32", device=dev, **kw)
+        torch.cuda.synchronize(dev)
+        build_s = time.perf_counter() - t0
+        if maps is None:
+            maps = plan.alm2map(alm_in)
+        a = plan.map2alm(maps)
+        rec = timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index)
+        r = {"value": rec["value"], "unit": UNIT, "ms_per_step": rec["t_max"] / args.steps,
+             "stages": rec["stages"], "plan_build_s": build_s, "device_bytes": plan.device_bytes,
+             "host_bytes": plan.host_bytes}
+        if name == "resident":
+            ref = a.clone()
+        elif name == "out_of_core":
+            r["equal_to_resident"] = bool(torch.equal(a, ref))
+            tb = plan.table_bytes + plan.column_table_bytes
+            r["table_bytes_streamed_per_step"] = tb
+            r["stream_gbs"] = tb / (rec["t_max"] / args.steps) / 1e6
+        out[name] = r
+        del a
+        plan.close()
+        torch.cuda.empty_cache()
     return out
 
 

@@ -115,6 +115,16 @@ typedef enum {
                                         bit for bit.  Other dtypes or a
                                         missing table flag: HPX_ERR_INVALID. */
 
+#define HPX_PLAN_LAMBDA_HOST 4u      /* with the tensor-core path: both
+                                        lambda tables live in pinned host
+                                        memory (out of core, Sec. III-G) and
+                                        every transform streams them, block
+                                        of m by block, through two device
+                                        staging buffers, copies overlapped
+                                        with the tile kernels.  For tables
+                                        larger than HBM.  Same results as
+                                        the resident plan. */
+
 /* Number of packed coefficients for (lmax, mmax). */
 int64_t hpx_nalm(int lmax, int mmax);
 
@@ -134,6 +144,20 @@ hpx_status hpx_plan_create(int nside, int lmax, int mmax, int nbatch,
 /* As hpx_plan_create, with HPX_PLAN_* flags. */
 hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch,
                               hpx_dtype dtype, unsigned flags, hpx_plan* out);
+
+/* An out-of-core tensor-core plan (HPX_PLAN_LAMBDA_TABLE |
+ * HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST) whose two device staging
+ * buffers hold stage_bytes per table part (hi, and lo for the x3 dtypes);
+ * 0 selects 1 GiB.  dtype: HPX_F32 or a 16-bit dtype.  The tables are built
+ * on the device block by block and copied to pinned host memory
+ * (hpx_plan_host_bytes).  HPX_ERR_INVALID if one m's table slice does not
+ * fit a staging buffer. */
+hpx_status hpx_plan_create_ooc(int nside, int lmax, int mmax, int nbatch,
+                               hpx_dtype dtype, size_t stage_bytes,
+                               hpx_plan* out);
+
+/* Pinned host bytes of an out-of-core plan's tables (0 otherwise). */
+size_t hpx_plan_host_bytes(hpx_plan plan);
 
 /* Release the plan and all device memory it owns (after synchronising its
  * device).  NULL is accepted. */

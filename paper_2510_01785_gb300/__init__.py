@@ -56,7 +56,7 @@ class Plan:
 
     def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,
                  dtype: str = "f32", lambda_table: bool = False, device=None,
-                 tensor_cores: bool = False):
+                 tensor_cores: bool = False, out_of_core: bool = False, stage_bytes: int = 0):
         mmax = lmax if mmax is None else mmax
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
@@ -74,10 +74,15 @@ class Plan:
         flags = _lib.HPX_PLAN_LAMBDA_TABLE if lambda_table else _lib.HPX_PLAN_LAMBDA_RECOMPUTE
         if tensor_cores:
             flags |= _lib.HPX_PLAN_TENSOR_CORES
+        self.out_of_core = out_of_core
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(lib().hpx_plan_create_ex(nside, lmax, mmax, nbatch, DTYPES[dtype], flags,
-                                           ctypes.byref(h)), "hpx_plan_create_ex")
+            if out_of_core:
+                check(lib().hpx_plan_create_ooc(nside, lmax, mmax, nbatch, DTYPES[dtype], int(stage_bytes),
+                                                ctypes.byref(h)), "hpx_plan_create_ooc")
+            else:
+                check(lib().hpx_plan_create_ex(nside, lmax, mmax, nbatch, DTYPES[dtype], flags,
+                                               ctypes.byref(h)), "hpx_plan_create_ex")
         self._h = h
 
     # -- lifetime -----------------------------------------------------------
@@ -118,6 +123,11 @@ class Plan:
     def table_bytes(self) -> int:
         """Bytes of the plan-resident lambda table (0 when recomputing)."""
         return int(lib().hpx_plan_table_bytes(self._h))
+
+    @property
+    def host_bytes(self) -> int:
+        """Pinned host bytes of an out-of-core plan's tables (0 otherwise)."""
+        return int(lib().hpx_plan_host_bytes(self._h))
 
     @property
     def column_table_bytes(self) -> int:

@@ -102,6 +102,25 @@ struct hpx_plan_s {
   alignas(64) unsigned char tm_stab[128];
   alignas(64) unsigned char tm_stablo[128];
   alignas(64) unsigned char tm_at[128];
+  // out-of-core tables (HPX_PLAN_LAMBDA_HOST): pinned host copies, streamed
+  // per block of m through two device staging buffers
+  void* h_tab;
+  void* h_tab_lo;
+  void* h_stab;
+  void* h_stab_lo;
+  size_t host_bytes;   // pinned host memory of the tables
+  void* d_stage[2];    // each: hi part, then (x3) lo part, stage_bytes apiece
+  size_t stage_bytes;
+  int stage_next;      // staging buffer of the next block
+  int nblk_row, nblk_col;
+  int* blk_row;        // host [nblk + 1]: m boundaries of the row-table blocks
+  int* blk_col;
+  long long* blk_row_base;  // host [nblk + 1]: first table element of each block
+  long long* blk_col_base;
+  alignas(64) unsigned char tm_stage[2][128];
+  alignas(64) unsigned char tm_stagelo[2][128];
+  void* copy_stream;   // cudaStream_t
+  void* stage_events;  // cudaEvent_t[4]: copied[2], free[2]
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
   double w_max;        // largest ring weight (4 pi / Npix unless set)
   size_t bytes;
@@ -185,12 +204,13 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 // The 16-bit dtypes (HPX_F32_BF16 ...) have only this path; their tables
 // (row and column, hi and for x3 lo parts) are built here too.
 int tc_columns(int nbatch, int cap);  // N of a tile for nbatch channels, at most cap per launch
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype);
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype, bool host_tables);
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s);
 int tc_channels_per_launch(const hpx_plan_s* p, bool synthesis);
 cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);
-cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s);
+cudaError_t launch_tile_tc(hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s);
 cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s);
-cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s);
+cudaError_t launch_synthesis_tc(hpx_plan_s* p, int b0, int nb, cudaStream_t s);
+void free_tc_host(hpx_plan_s* p);  // out-of-core resources (pinned tables, stream, events)
 
 }  // namespace hpx

@@ -120,6 +120,7 @@ struct TimingState {
 
 static void plan_free(hpx_plan_s* p) {
   if (!p) return;
+  free_tc_host(p);
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
@@ -280,8 +281,22 @@ int64_t hpx_nalm(int lmax, int mmax) {
 
 const char* hpx_last_error(void) { return g_err.c_str(); }
 
+static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
+                              size_t stage_bytes, hpx_plan* out);
+
 hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
                               hpx_plan* out) {
+  return create_plan(nside, lmax, mmax, nbatch, dtype, flags, 0, out);
+}
+
+hpx_status hpx_plan_create_ooc(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, size_t stage_bytes,
+                               hpx_plan* out) {
+  return create_plan(nside, lmax, mmax, nbatch, dtype,
+                     HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST, stage_bytes, out);
+}
+
+static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
+                              size_t stage_bytes, hpx_plan* out) {
   if (!out) {
     set_error("null output pointer");
     return HPX_ERR_INVALID;
@@ -303,15 +318,19 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("unknown dtype %d", (int)dtype);
     return HPX_ERR_INVALID;
   }
-  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES)) {
+  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST)) {
     set_error("unknown plan flags 0x%x", flags);
     return HPX_ERR_INVALID;
   }
   const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
   if (mixed) {
-    flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES;  // the 16-bit dtypes' only path
+    flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | (flags & HPX_PLAN_LAMBDA_HOST);  // their only path
   } else if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
     set_error("HPX_PLAN_TENSOR_CORES needs an HPX_F32 plan with HPX_PLAN_LAMBDA_TABLE");
+    return HPX_ERR_INVALID;
+  }
+  if ((flags & HPX_PLAN_LAMBDA_HOST) && !(flags & HPX_PLAN_TENSOR_CORES)) {
+    set_error("HPX_PLAN_LAMBDA_HOST needs the tensor-core path (HPX_PLAN_TENSOR_CORES or a 16-bit dtype)");
     return HPX_ERR_INVALID;
   }
   hpx_plan_s* p = new hpx_plan_s();
@@ -323,6 +342,7 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
   p->nbatch = nbatch;
   p->dtype = dtype;
   p->flags = flags;
+  p->stage_bytes = stage_bytes;
   p->nring = 4 * nside - 1;
   p->w_max = 4.0 * 3.14159265358979323846 / (12.0 * (double)nside * (double)nside);
   p->npair = 2 * nside;
@@ -382,7 +402,7 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch, hpx_dty
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
-  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && !mixed)
+  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && !mixed && !(flags & HPX_PLAN_LAMBDA_HOST))
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
@@ -434,28 +454,32 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
              cs * (size_t)nbatch * nring * (mmax + 1);
   const size_t ngroup = (npair + 31) / 32;
   const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
-  if (mixed) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype);
+  if (flags & HPX_PLAN_LAMBDA_HOST)  // tables on the host; two staging buffers (1 GiB parts) on the device
+    return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, true);
+  if (mixed) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, false);
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
     b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ngroup;
   if (flags & HPX_PLAN_TENSOR_CORES)  // row-table starts padded to the tile grid; column table; operands
     b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) +
-         tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype);
+         tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, false);
   return b + sizeof(int);
 }
 
 size_t hpx_plan_table_bytes(hpx_plan plan) {
-  if (!plan || !plan->d_tab) return 0;
+  if (!plan || (!plan->d_tab && !plan->h_tab)) return 0;
   const size_t es = plan->dtype == HPX_F64 ? sizeof(double) : plan->dtype == HPX_F32 ? sizeof(float) : 2;
-  const size_t parts = plan->d_tab_lo ? 2 : 1;
+  const size_t parts = (plan->d_tab_lo || plan->h_tab_lo) ? 2 : 1;
   return (size_t)plan->tab_elems * es * parts;
 }
 
 size_t hpx_plan_column_table_bytes(hpx_plan plan) {
-  if (!plan || !plan->d_stab) return 0;
+  if (!plan || (!plan->d_stab && !plan->h_stab)) return 0;
   const size_t es = plan->dtype == HPX_F32 ? sizeof(float) : 2;
-  const size_t parts = plan->d_stab_lo ? 2 : 1;
+  const size_t parts = (plan->d_stab_lo || plan->h_stab_lo) ? 2 : 1;
   return (size_t)plan->stab_elems * es * parts;
 }
+
+size_t hpx_plan_host_bytes(hpx_plan plan) { return plan ? plan->host_bytes : 0; }
 
 hpx_status hpx_map2alm(hpx_plan plan, const void* map, void* alm, hpx_stream_t stream) {
   return transform(plan, map, alm, stream, true, true, "hpx_map2alm");

@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -383,18 +384,21 @@ __global__ void k_rtab_groups(const int* __restrict__ lc_tab, int lmax, int npai
   rows[(long long)m * ngroup + g] = lmax + 1 - ls;
 }
 
+// Fills m = m0 + blockIdx.y; element e of the table goes to hi[e - base]
+// (base > 0 when the table is built block by block through a staging buffer).
 template <typename E>
 __global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
-                            const long long* __restrict__ off, int lmax, int npair, int ngroup, E* hi, E* lo) {
+                            const long long* __restrict__ off, int lmax, int npair, int ngroup, int m0,
+                            long long base, E* hi, E* lo) {
   constexpr int KW = Elt<E>::kw;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = m0 + blockIdx.y;
   const int g = p / KW;
   if (g >= ngroup) return;
   const long long mg = (long long)m * ngroup + g;
   const int ls = lstart[mg];
-  const long long o = off[mg] + (p % KW);
+  const long long o = off[mg] - base + (p % KW);
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
   for (int l = ls; l <= lmax; ++l) {
     const double mu = p < npair ? ch.step(l) : 0.0;
@@ -426,16 +430,17 @@ template <typename E>
 __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
-                            const long long* __restrict__ off, int lmax, int npair, int nptile, E* hi, E* lo) {
+                            const long long* __restrict__ off, int lmax, int npair, int nptile, int m0,
+                            long long base, E* hi, E* lo) {
   constexpr int KW = Elt<E>::kw, V = 16 / (int)sizeof(E);  // values per 16-byte store
-  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, m = m0 + blockIdx.y;
   const int T = p >> 7;
   if (T >= nptile) return;
   const long long mT = (long long)m * nptile + T;
   const int ls = lstart[mT];
   if (ls > lmax) return;
   const int lend = ls + ((lmax - ls) / KW + 1) * KW;  // end of the last block
-  const long long o = off[mT] + (long long)(p & 127) * KW;
+  const long long o = off[mT] - base + (long long)(p & 127) * KW;
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
   for (int lv = ls; lv < lend; lv += V) {
     alignas(16) E h[V];
@@ -502,6 +507,8 @@ struct TcArgs {
   double mfac;
   uint32_t fmt;             // 16-bit modes: operand format of kind::f16 (0 FP16, 1 BF16)
   int* status;
+  int m0;                   // first m of the launch (blockIdx.y = m - m0)
+  long long tbase;          // table element at row 0 of the lambda descriptor (streamed blocks)
 };
 
 // One CTA: a 128-row tile of one m, all channels of the launch.
@@ -542,7 +549,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   constexpr int NSUM = SYN ? NN : C2N;
   static_assert(NN % 32 == 0 && NN <= (MODE == 0 || SYN ? 128 : 256), "N tile");
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int m = blockIdx.y;
+  const int m = a.m0 + blockIdx.y;
   const int l0 = m + kTcTile * blockIdx.x;  // analysis tile
   if (!SYN && l0 > a.lmax) return;          // whole CTA, before any shared state
 
@@ -584,7 +591,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const long long mg = (long long)m * a.ngroup + t;
       const int ls = a.lstart[mg];
       act = ls <= l0;
-      ra = (int)(a.off[mg] / KW) + (l0 - ls);
+      ra = (int)((a.off[mg] - a.tbase) / KW) + (l0 - ls);
       rb = (int)(mg * RB);
     }
     bal = __ballot_sync(0xffffffffu, act);
@@ -596,7 +603,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const int ls = a.lstart[mT];
     if (ls <= a.lmax) {
       na = (a.lmax - ls) / KW + 1;
-      ra0 = (int)(a.off[mT] / KW);
+      ra0 = (int)((a.off[mT] - a.tbase) / KW);
       rb0 = (int)((a.achunk[m] + (ls - m) / KW) * RB);
     }
   }
@@ -894,8 +901,19 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.mfac = mfac;
   a.fmt = (uint32_t)p->tc_fmt;
   a.status = p->d_status;
+  a.m0 = 0;
+  a.tbase = 0;
   return a;
 }
+
+// One tile launch: the lambda descriptors (resident table or a staging
+// buffer), the m range, and the table element at the descriptors' row 0.
+struct TileRange {
+  const void* tmA;
+  const void* tmAlo;
+  int m0, nm;
+  long long tbase;
+};
 
 template <int CP, typename E>
 cudaError_t pack_gt_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
@@ -917,16 +935,18 @@ cudaError_t pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, do
 }
 
 template <int CP, bool SYN, int MODE>
-cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
+cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, const TileRange& r,
+                    cudaStream_t s) {
   constexpr int NN = 4 * CP;
   cudaError_t e = allow_max_smem(k_legendre_tc<NN, SYN, MODE>);
   if (e != cudaSuccess) return e;
-  const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_stab : p->tm_tab);
-  const CUtensorMap* tmAlo = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_stablo : p->tm_tablo);
   const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_at : p->tm_gt);
-  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, p->mmax + 1);
+  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, r.nm);
+  TcArgs a = tc_args(p, SYN, out, b0, nb, mfac);
+  a.m0 = r.m0;
+  a.tbase = r.tbase;
   k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, MODE>::kSmem, s>>>(
-      *tmA, *tmAlo, *tmB, tc_args(p, SYN, out, b0, nb, mfac));
+      *reinterpret_cast<const CUtensorMap*>(r.tmA), *reinterpret_cast<const CUtensorMap*>(r.tmAlo), *tmB, a);
   return cudaGetLastError();
 }
 
@@ -944,13 +964,66 @@ cudaError_t pack_at_t(const hpx_plan_s* p, const float* alm, int b0, int nb, dou
                         : pack_at_cp<CP, __half>(p, alm, b0, nb, mfac, s);
 }
 template <int CP, bool SYN>
-cudaError_t tile_t(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
+cudaError_t tile_t(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, const TileRange& r,
+                   cudaStream_t s) {
   switch (p->tc_mode) {
-    case 0: if constexpr (CP <= 32) return tile_cp<CP, SYN, 0>(p, out, b0, nb, mfac, s); break;
-    case 1: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 1>(p, out, b0, nb, mfac, s); break;
-    case 2: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 2>(p, out, b0, nb, mfac, s); break;
+    case 0: if constexpr (CP <= 32) return tile_cp<CP, SYN, 0>(p, out, b0, nb, mfac, r, s); break;
+    case 1: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 1>(p, out, b0, nb, mfac, r, s); break;
+    case 2: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 2>(p, out, b0, nb, mfac, r, s); break;
   }
   return cudaErrorInvalidValue;
+}
+
+template <bool SYN>
+cudaError_t tile_nn(const hpx_plan_s* p, float* out, int b0, int nb, double mfac, const TileRange& r,
+                    cudaStream_t s) {
+  switch (SYN ? p->tc_nn_s : p->tc_nn_a) {
+    case 32: return tile_t<8, SYN>(p, out, b0, nb, mfac, r, s);
+    case 64: return tile_t<16, SYN>(p, out, b0, nb, mfac, r, s);
+    case 128: return tile_t<32, SYN>(p, out, b0, nb, mfac, r, s);
+    case 256: if constexpr (!SYN) return tile_t<64, SYN>(p, out, b0, nb, mfac, r, s); break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The tile kernel over all m: one launch on the resident table, or, for an
+// out-of-core plan, one launch per m block with the block's slice of the
+// host table copied into a staging buffer on the plan's copy stream.  Two
+// staging buffers alternate; a copy waits until the launch that last read
+// its buffer is done, and a launch waits for its copy.
+template <bool SYN>
+cudaError_t tile_all(hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
+  if (!p->h_tab) {
+    const TileRange r{SYN ? p->tm_stab : p->tm_tab, SYN ? p->tm_stablo : p->tm_tablo, 0, p->mmax + 1, 0};
+    return tile_nn<SYN>(p, out, b0, nb, mfac, r, s);
+  }
+  cudaStream_t cs = static_cast<cudaStream_t>(p->copy_stream);
+  cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(p->stage_events);  // [0, 1] copied, [2, 3] free
+  const int nblk = SYN ? p->nblk_col : p->nblk_row;
+  const int* bm = SYN ? p->blk_col : p->blk_row;                    // [nblk + 1] m boundaries
+  const long long* bb = SYN ? p->blk_col_base : p->blk_row_base;    // [nblk + 1] element boundaries
+  const char* hhi = static_cast<const char*>(SYN ? p->h_stab : p->h_tab);
+  const char* hlo = static_cast<const char*>(SYN ? p->h_stab_lo : p->h_tab_lo);
+  const size_t es = p->tc_mode ? 2 : 4;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < nblk && e == cudaSuccess; ++j) {
+    const int buf = p->stage_next;
+    p->stage_next ^= 1;
+    const size_t bytes = (size_t)(bb[j + 1] - bb[j]) * es;
+    char* d = static_cast<char*>(p->d_stage[buf]);
+    e = cudaStreamWaitEvent(cs, ev[2 + buf], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, hhi + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && hlo)
+      e = cudaMemcpyAsync(d + p->stage_bytes, hlo + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[buf], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[buf], 0);
+    if (e == cudaSuccess) {
+      const TileRange r{p->tm_stage[buf], p->tm_stagelo[buf], bm[j], bm[j + 1] - bm[j], bb[j]};
+      e = tile_nn<SYN>(p, out, b0, nb, mfac, r, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + buf], s);
+  }
+  return e;
 }
 
 int tc_mode_of(int dtype) {
@@ -981,7 +1054,7 @@ int tc_columns(int nbatch, int cap) {
 
 int tc_channels_per_launch(const hpx_plan_s* p, bool syn) { return (syn ? p->tc_nn_s : p->tc_nn_a) / 4; }
 
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype) {
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype, bool host_tables) {
   const int mode = tc_mode_of(dtype);
   if (mode < 0) return 0;
   const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
@@ -994,11 +1067,90 @@ size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dt
   }
   size_t b = es * (size_t)(mmax + 1) * ngroup * nna * kw * parts  // Gt
              + es * chunks * nns * kw * parts                     // At
-             + es * parts * chunks * nptile * 128 * kw            // column table (upper bound)
              + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * (nptile + ngroup) +
              sizeof(long long) * (mmax + 2) + sizeof(unsigned) * nbatch;
-  if (mode) b += es * parts * rows * ngroup * kw;  // 16-bit row table (upper bound)
+  if (host_tables) return b + 2 * parts * (size_t(1) << 30);      // staging buffers at the default size
+  b += es * parts * chunks * nptile * 128 * kw;                    // column table (upper bound)
+  if (mode) b += es * parts * rows * ngroup * kw;                  // 16-bit row table (upper bound)
   return b;
+}
+
+namespace {
+
+// Exclusive prefix sums of per-entry row counts times the row width; returns the total.
+long long offsets_from_rows(std::vector<long long>& v, long long width) {
+  long long acc = 0;
+  for (auto& x : v) {
+    const long long r = x;
+    x = acc;
+    acc += width * r;
+  }
+  return acc;
+}
+
+// Blocks of consecutive m whose slice of an m-major table (per-m first
+// element off[m * per_m], total `total`) fits `cap` elements.  False if one m
+// alone exceeds it.
+bool make_blocks(const std::vector<long long>& off, int per_m, int mmax, long long total, long long cap,
+                 std::vector<int>& bm, std::vector<long long>& bb) {
+  bm.assign(1, 0);
+  bb.assign(1, 0);
+  for (int m = 0; m <= mmax; ++m) {
+    const long long end = m < mmax ? off[(size_t)(m + 1) * per_m] : total;
+    if (end - bb.back() > cap) {
+      if (bm.back() == m) return false;
+      bm.push_back(m);
+      bb.push_back(off[(size_t)m * per_m]);
+      if (end - bb.back() > cap) return false;
+    }
+  }
+  bm.push_back(mmax + 1);
+  bb.push_back(total);
+  return true;
+}
+
+template <typename E>
+cudaError_t fill_row_table(hpx_plan_s* p, int m0, int nm, long long base, void* hi, void* lo, cudaStream_t s) {
+  constexpr int KW = Elt<E>::kw;
+  k_rtab_fill<E><<<dim3((p->ngroup * KW + 127) / 128, nm), 128, 0, s>>>(
+      p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
+      p->ngroup, m0, base, static_cast<E*>(hi), static_cast<E*>(lo));
+  return cudaGetLastError();
+}
+template <typename E>
+cudaError_t fill_col_table(hpx_plan_s* p, int m0, int nm, long long base, void* hi, void* lo, cudaStream_t s) {
+  k_ctab_fill<E><<<dim3(p->nptile, nm), 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
+                                                     p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair,
+                                                     p->nptile, m0, base, static_cast<E*>(hi), static_cast<E*>(lo));
+  return cudaGetLastError();
+}
+cudaError_t fill_table(hpx_plan_s* p, bool col, int m0, int nm, long long base, void* hi, void* lo,
+                       cudaStream_t s) {
+  if (p->tc_mode == 0) return col ? fill_col_table<float>(p, m0, nm, base, hi, nullptr, s)
+                                  : fill_row_table<float>(p, m0, nm, base, hi, nullptr, s);
+  if (p->tc_fmt == 1) return col ? fill_col_table<__nv_bfloat16>(p, m0, nm, base, hi, lo, s)
+                                 : fill_row_table<__nv_bfloat16>(p, m0, nm, base, hi, lo, s);
+  return col ? fill_col_table<__half>(p, m0, nm, base, hi, lo, s) : fill_row_table<__half>(p, m0, nm, base, hi, lo, s);
+}
+
+}  // namespace
+
+void free_tc_host(hpx_plan_s* p) {
+  for (void* h : {p->h_tab, p->h_tab_lo, p->h_stab, p->h_stab_lo})
+    if (h) cudaFreeHost(h);
+  for (void* d : p->d_stage)
+    if (d) cudaFree(d);
+  delete[] p->blk_row;
+  delete[] p->blk_col;
+  delete[] p->blk_row_base;
+  delete[] p->blk_col_base;
+  if (p->stage_events) {
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->stage_events);
+    for (int i = 0; i < 4; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+    delete[] ev;
+  }
+  if (p->copy_stream) cudaStreamDestroy(static_cast<cudaStream_t>(p->copy_stream));
 }
 
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
@@ -1006,7 +1158,8 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   if (mode < 0) return cudaErrorInvalidValue;
   p->tc_mode = mode;
   p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;
-  const int kw = mode ? 64 : 32, es = mode ? 2 : 4;
+  const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
+  const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
   const int nna = tc_columns(p->nbatch, mode ? 64 : 32), nns = tc_columns(p->nbatch, 32);
   const int rba = mode == 2 ? 2 * nna : nna, rbs = mode == 2 ? 2 * nns : nns;
   auto dalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
@@ -1014,9 +1167,11 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
     if (e == cudaSuccess) p->bytes += bytes > 0 ? bytes : 16;
     return e;
   };
-  // 16-bit row table (the FP32 one is built with the plan's CUDA-core table)
   cudaError_t e = cudaSuccess;
-  if (mode) {
+  // row table layout: built here for the 16-bit types and for out-of-core
+  // plans (the resident FP32 one comes with the CUDA-core table)
+  std::vector<long long> roff;
+  if (mode || host) {
     const int ng = (p->npair + kw - 1) / kw;
     p->ngroup = ng;
     const long long nent = (long long)(p->mmax + 1) * ng;
@@ -1027,31 +1182,11 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
                                                                        p->d_tab_lstart, p->d_tab_off);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    roff.resize(nent);
+    if (e == cudaSuccess) e = cudaMemcpy(roff.data(), p->d_tab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return e;
-    std::vector<long long> off(nent);
-    e = cudaMemcpy(off.data(), p->d_tab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    long long acc = 0;
-    for (long long i = 0; i < nent; ++i) {
-      const long long r = off[i];
-      off[i] = acc;
-      acc += (long long)kw * r;
-    }
-    p->tab_elems = acc;
-    e = cudaMemcpy(p->d_tab_off, off.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = dalloc(&p->d_tab, (size_t)es * acc);
-    if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_tab_lo, (size_t)es * acc);
-    if (e != cudaSuccess) return e;
-    const dim3 g((ng * kw + 127) / 128, p->mmax + 1);
-    if (p->tc_fmt == 1)
-      k_rtab_fill<__nv_bfloat16><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
-                                                   p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair, ng,
-                                                   (__nv_bfloat16*)p->d_tab, (__nv_bfloat16*)p->d_tab_lo);
-    else
-      k_rtab_fill<__half><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart,
-                                            p->d_tab_off, p->lmax, p->npair, ng, (__half*)p->d_tab,
-                                            (__half*)p->d_tab_lo);
-    e = cudaGetLastError();
+    p->tab_elems = offsets_from_rows(roff, kw);
+    e = cudaMemcpy(p->d_tab_off, roff.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
   }
   // analysis operand
@@ -1067,54 +1202,117 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&p->d_at, (size_t)es * ach[p->mmax + 1] * rbs * kw);
   if (e == cudaSuccess) e = dalloc((void**)&p->d_bmax, sizeof(unsigned) * p->nbatch);
   if (e != cudaSuccess) return e;
-  // column table
+  // column table layout
   p->nptile = (p->npair + 127) / 128;
-  const long long nent = (long long)(p->mmax + 1) * p->nptile;
-  e = dalloc((void**)&p->d_stab_lstart, sizeof(int) * nent);
-  if (e == cudaSuccess) e = dalloc((void**)&p->d_stab_off, sizeof(long long) * nent);
+  const long long cent = (long long)(p->mmax + 1) * p->nptile;
+  e = dalloc((void**)&p->d_stab_lstart, sizeof(int) * cent);
+  if (e == cudaSuccess) e = dalloc((void**)&p->d_stab_off, sizeof(long long) * cent);
   if (e != cudaSuccess) return e;
   k_ctab_tiles<<<dim3((p->nptile + 127) / 128, p->mmax + 1), 128, 0, s>>>(p->d_lc, p->lmax, p->npair, kw, p->nptile,
                                                                            p->d_stab_lstart, p->d_stab_off);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  std::vector<long long> coff(cent);
+  if (e == cudaSuccess) e = cudaMemcpy(coff.data(), p->d_stab_off, sizeof(long long) * cent, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return e;
-  std::vector<long long> off(nent);
-  e = cudaMemcpy(off.data(), p->d_stab_off, sizeof(long long) * nent, cudaMemcpyDeviceToHost);
+  p->stab_elems = offsets_from_rows(coff, 128LL * kw);
+  e = cudaMemcpy(p->d_stab_off, coff.data(), sizeof(long long) * cent, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  long long acc = 0;
-  for (long long i = 0; i < nent; ++i) {
-    const long long nb = off[i];
-    off[i] = acc;
-    acc += nb * 128 * kw;
+
+  if (!host) {
+    // resident tables
+    if (mode) {
+      e = dalloc(&p->d_tab, (size_t)es * p->tab_elems);
+      if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_tab_lo, (size_t)es * p->tab_elems);
+      if (e == cudaSuccess) e = fill_table(p, false, 0, p->mmax + 1, 0, p->d_tab, p->d_tab_lo, s);
+      if (e != cudaSuccess) return e;
+    }
+    e = dalloc(&p->d_stab, (size_t)es * p->stab_elems);
+    if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_stab_lo, (size_t)es * p->stab_elems);
+    if (e == cudaSuccess) e = fill_table(p, true, 0, p->mmax + 1, 0, p->d_stab, p->d_stab_lo, s);
+    if (e != cudaSuccess) return e;
+    const void* tablo = p->d_tab_lo ? p->d_tab_lo : p->d_tab;
+    const void* stablo = p->d_stab_lo ? p->d_stab_lo : p->d_stab;
+    const unsigned long long trows = (unsigned long long)(p->tab_elems / kw);
+    const unsigned long long srows = (unsigned long long)(p->stab_elems / kw);
+    if (!encode_rows128(p->tm_tab, p->d_tab, trows, kTcTile, es) ||
+        !encode_rows128(p->tm_tablo, tablo, trows, kTcTile, es) ||
+        !encode_rows128(p->tm_stab, p->d_stab, srows, 128, es) ||
+        !encode_rows128(p->tm_stablo, stablo, srows, 128, es)) {
+      set_error("cuTensorMapEncodeTiled failed or is unavailable");
+      return cudaErrorInvalidValue;
+    }
+  } else {
+    // out-of-core tables: m blocks that fit a staging buffer, filled block by
+    // block on the device and copied to pinned host memory
+    if (p->stage_bytes == 0) p->stage_bytes = size_t(1) << 30;
+    p->stage_bytes = (p->stage_bytes / 128) * 128;
+    const long long cap = (long long)(p->stage_bytes / es);
+    std::vector<int> rbm, cbm;
+    std::vector<long long> rbb, cbb;
+    if (!make_blocks(roff, p->ngroup, p->mmax, p->tab_elems, cap, rbm, rbb) ||
+        !make_blocks(coff, p->nptile, p->mmax, p->stab_elems, cap, cbm, cbb)) {
+      set_error("staging buffers of %zu bytes cannot hold the table slice of a single m", p->stage_bytes);
+      return cudaErrorInvalidValue;
+    }
+    p->nblk_row = (int)rbm.size() - 1;
+    p->nblk_col = (int)cbm.size() - 1;
+    p->blk_row = new int[rbm.size()];
+    p->blk_col = new int[cbm.size()];
+    p->blk_row_base = new long long[rbb.size()];
+    p->blk_col_base = new long long[cbb.size()];
+    std::copy(rbm.begin(), rbm.end(), p->blk_row);
+    std::copy(cbm.begin(), cbm.end(), p->blk_col);
+    std::copy(rbb.begin(), rbb.end(), p->blk_row_base);
+    std::copy(cbb.begin(), cbb.end(), p->blk_col_base);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dalloc(&p->d_stage[b], p->stage_bytes * parts);
+    if (e != cudaSuccess) return e;
+    auto halloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+      cudaError_t r = cudaHostAlloc(ptr, bytes > 0 ? bytes : 16, cudaHostAllocDefault);
+      if (r == cudaSuccess) p->host_bytes += bytes;
+      return r;
+    };
+    e = halloc(&p->h_tab, (size_t)es * p->tab_elems);
+    if (e == cudaSuccess) e = halloc(&p->h_stab, (size_t)es * p->stab_elems);
+    if (e == cudaSuccess && mode == 2) e = halloc(&p->h_tab_lo, (size_t)es * p->tab_elems);
+    if (e == cudaSuccess && mode == 2) e = halloc(&p->h_stab_lo, (size_t)es * p->stab_elems);
+    if (e != cudaSuccess) return e;
+    char* shi = static_cast<char*>(p->d_stage[0]);
+    char* slo = mode == 2 ? shi + p->stage_bytes : nullptr;
+    for (int col = 0; col < 2 && e == cudaSuccess; ++col) {
+      const std::vector<int>& bm = col ? cbm : rbm;
+      const std::vector<long long>& bb = col ? cbb : rbb;
+      char* hhi = static_cast<char*>(col ? p->h_stab : p->h_tab);
+      char* hlo = static_cast<char*>(col ? p->h_stab_lo : p->h_tab_lo);
+      for (size_t j = 0; j + 1 < bm.size() && e == cudaSuccess; ++j) {
+        const size_t bytes = (size_t)(bb[j + 1] - bb[j]) * es;
+        e = fill_table(p, col != 0, bm[j], bm[j + 1] - bm[j], bb[j], shi, slo, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hhi + (size_t)bb[j] * es, shi, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && slo)
+          e = cudaMemcpyAsync(hlo + (size_t)bb[j] * es, slo, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      }
+    }
+    if (e != cudaSuccess) return e;
+    const unsigned long long srows = (unsigned long long)(p->stage_bytes / 128);
+    for (int b = 0; b < 2; ++b) {
+      char* base = static_cast<char*>(p->d_stage[b]);
+      if (!encode_rows128(p->tm_stage[b], base, srows, 128, es) ||
+          !encode_rows128(p->tm_stagelo[b], mode == 2 ? base + p->stage_bytes : base, srows, 128, es)) {
+        set_error("cuTensorMapEncodeTiled failed or is unavailable");
+        return cudaErrorInvalidValue;
+      }
+    }
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    p->copy_stream = cs;
+    cudaEvent_t* ev = new cudaEvent_t[4]();
+    p->stage_events = ev;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
   }
-  p->stab_elems = acc;
-  e = cudaMemcpy(p->d_stab_off, off.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = dalloc(&p->d_stab, (size_t)es * acc);
-  if (e == cudaSuccess && mode == 2) e = dalloc(&p->d_stab_lo, (size_t)es * acc);
-  if (e != cudaSuccess) return e;
-  const dim3 g(p->nptile, p->mmax + 1);
-  if (mode == 0)
-    k_ctab_fill<float><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_stab_lstart,
-                                         p->d_stab_off, p->lmax, p->npair, p->nptile, (float*)p->d_stab, nullptr);
-  else if (p->tc_fmt == 1)
-    k_ctab_fill<__nv_bfloat16><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
-                                                 p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair, p->nptile,
-                                                 (__nv_bfloat16*)p->d_stab, (__nv_bfloat16*)p->d_stab_lo);
-  else
-    k_ctab_fill<__half><<<g, 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_stab_lstart,
-                                          p->d_stab_off, p->lmax, p->npair, p->nptile, (__half*)p->d_stab,
-                                          (__half*)p->d_stab_lo);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // descriptors (the lo maps point at hi where there is no lo table; unused)
-  const void* tablo = p->d_tab_lo ? p->d_tab_lo : p->d_tab;
-  const void* stablo = p->d_stab_lo ? p->d_stab_lo : p->d_stab;
-  const unsigned long long trows = (unsigned long long)(p->tab_elems / kw), srows = (unsigned long long)(acc / kw);
-  if (!encode_rows128(p->tm_tab, p->d_tab, trows, kTcTile, es) ||
-      !encode_rows128(p->tm_tablo, tablo, trows, kTcTile, es) ||
-      !encode_rows128(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * rba, nna, es) ||
-      !encode_rows128(p->tm_stab, p->d_stab, srows, 128, es) ||
-      !encode_rows128(p->tm_stablo, stablo, srows, 128, es) ||
+  if (!encode_rows128(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * rba, nna, es) ||
       !encode_rows128(p->tm_at, p->d_at, (unsigned long long)ach[p->mmax + 1] * rbs, nns, es)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return cudaErrorInvalidValue;
@@ -1139,14 +1337,8 @@ cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream
   }
 }
 
-cudaError_t launch_tile_tc(const hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
-  switch (p->tc_nn_a) {
-    case 32: return tile_t<8, false>(p, alm, b0, nb, mfac, s);
-    case 64: return tile_t<16, false>(p, alm, b0, nb, mfac, s);
-    case 128: return tile_t<32, false>(p, alm, b0, nb, mfac, s);
-    case 256: return tile_t<64, false>(p, alm, b0, nb, mfac, s);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_tile_tc(hpx_plan_s* p, float* alm, int b0, int nb, double mfac, cudaStream_t s) {
+  return tile_all<false>(p, alm, b0, nb, mfac, s);
 }
 
 cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
@@ -1163,14 +1355,8 @@ cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, d
   }
 }
 
-cudaError_t launch_synthesis_tc(const hpx_plan_s* p, int b0, int nb, cudaStream_t s) {
-  float* F = static_cast<float*>(p->d_F);
-  switch (p->tc_nn_s) {
-    case 32: return tile_t<8, true>(p, F, b0, nb, 1.0, s);
-    case 64: return tile_t<16, true>(p, F, b0, nb, 1.0, s);
-    case 128: return tile_t<32, true>(p, F, b0, nb, 1.0, s);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_synthesis_tc(hpx_plan_s* p, int b0, int nb, cudaStream_t s) {
+  return tile_all<true>(p, static_cast<float*>(p->d_F), b0, nb, 1.0, s);
 }
 
 }  // namespace hpx
