@@ -213,6 +213,24 @@ hpx_status hpx_alm2map_grad(hpx_plan plan, const void* grad_map, void* grad_alm,
 hpx_status hpx_map2alm_grad(hpx_plan plan, const void* grad_alm, void* grad_map,
                             hpx_stream_t stream);
 
+/* Pipelined host-buffer forms: the same transforms, queued without waiting.
+ * The input is uploaded on a plan-owned host-to-device stream into one of
+ * two plan-owned I/O slots (alternating per call; a slot is reused once its
+ * previous result has been downloaded), the transform runs on `stream`
+ * after the upload, and the result is downloaded on a plan-owned
+ * device-to-host stream.  Consecutive calls thus overlap one call's copies
+ * with the neighbouring calls' kernels.  host buffers: pinned, left
+ * untouched (input) or unread (output) until hpx_plan_host_sync returns.
+ * The slots (two map- and two alm-sized device buffers) are allocated on
+ * the first call and counted by hpx_plan_device_bytes. */
+hpx_status hpx_map2alm_host_async(hpx_plan plan, const void* host_map,
+                                  void* host_alm, hpx_stream_t stream);
+hpx_status hpx_alm2map_host_async(hpx_plan plan, const void* host_alm,
+                                  void* host_map, hpx_stream_t stream);
+/* Waits for every pipelined call's download (and reports the plan's
+ * device-side wait status, as hpx_plan_device_status does). */
+hpx_status hpx_plan_host_sync(hpx_plan plan);
+
 /* Analysis with iterative refinement (Sec. II-A Eq. 4): a^0 = A f, then
  * niter times r = f - S a^k, a^{k+1} = a^k + A r, with A = map2alm and S =
  * alm2map of this plan.  Each step reduces the residual of a band-limited

@@ -246,6 +246,31 @@ class Plan:
                                      ctypes.c_void_p(_stream_handle(stream, self.device))), "hpx_map2alm_host")
         return dst
 
+    def map2alm_host_async(self, maps: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Pipelined host-buffer analysis: queued, complete after host_sync().
+        maps and out: pinned CPU tensors kept alive until then."""
+        assert maps.is_pinned() and out.is_pinned() and maps.is_contiguous() and out.is_contiguous()
+        assert tuple(maps.shape) == (self.nbatch, self.npix) and maps.dtype == self.real_dtype
+        assert tuple(out.shape) == (self.nbatch, self.nalm) and out.dtype == self.complex_dtype
+        check(lib().hpx_map2alm_host_async(self._h, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(_stream_handle(stream, self.device))),
+              "hpx_map2alm_host_async")
+        return out
+
+    def alm2map_host_async(self, alm: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Pipelined host-buffer synthesis: queued, complete after host_sync()."""
+        assert alm.is_pinned() and out.is_pinned() and alm.is_contiguous() and out.is_contiguous()
+        assert tuple(alm.shape) == (self.nbatch, self.nalm) and alm.dtype == self.complex_dtype
+        assert tuple(out.shape) == (self.nbatch, self.npix) and out.dtype == self.real_dtype
+        check(lib().hpx_alm2map_host_async(self._h, ctypes.c_void_p(alm.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(_stream_handle(stream, self.device))),
+              "hpx_alm2map_host_async")
+        return out
+
+    def host_sync(self) -> None:
+        """Wait for every pipelined host-buffer call."""
+        check(lib().hpx_plan_host_sync(self._h), "hpx_plan_host_sync")
+
     def alm2map_host(self, alm: np.ndarray | torch.Tensor, out=None, stream=None):
         """Host coefficients in, host map out (copies inside the call)."""
         src = alm if isinstance(alm, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(alm))

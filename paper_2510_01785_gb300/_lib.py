@@ -39,6 +39,9 @@ SIGNATURES = {
     "hpx_map2alm_grad": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_host": (_I, [_P, _P, _P, _P]),
     "hpx_map2alm_iter": (_I, [_P, _P, _P, _I, _P]),
+    "hpx_map2alm_host_async": (_I, [_P, _P, _P, _P]),
+    "hpx_alm2map_host_async": (_I, [_P, _P, _P, _P]),
+    "hpx_plan_host_sync": (_I, [_P]),
     "hpx_alm2map_host": (_I, [_P, _P, _P, _P]),
     "hpx_plan_device_bytes": (_SZ, [_P]),
     "hpx_plan_ring_table": (_I, [_P, _P, _P, _P, _P, _P]),

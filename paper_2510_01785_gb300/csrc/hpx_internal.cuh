@@ -72,6 +72,11 @@ struct hpx_plan_s {
   void* d_F;           // workspace [nbatch][nring][mmax+1] C2<T>
   void* d_io_map;      // device I/O buffers of the host-buffer entry points (lazy)
   void* d_io_alm;
+  void* d_aio_map[2];  // pipelined host-buffer calls: two I/O slots (lazy)
+  void* d_aio_alm[2];
+  int aio_next;        // slot of the next pipelined call
+  void* aio_streams;   // cudaStream_t[2]: host-to-device, device-to-host
+  void* aio_events;    // cudaEvent_t[6]: uploaded[2], computed[2], slot free[2]
   void* d_it_map;      // iterative refinement: synthesis / residual map and correction (lazy)
   void* d_it_alm;
   void* timing;        // per-stage CUDA events while timing is enabled

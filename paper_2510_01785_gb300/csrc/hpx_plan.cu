@@ -121,6 +121,22 @@ struct TimingState {
 static void plan_free(hpx_plan_s* p) {
   if (!p) return;
   free_tc_host(p);
+  for (int k = 0; k < 2; ++k) {
+    if (p->d_aio_map[k]) cudaFree(p->d_aio_map[k]);
+    if (p->d_aio_alm[k]) cudaFree(p->d_aio_alm[k]);
+  }
+  if (p->aio_events) {
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->aio_events);
+    for (int i = 0; i < 6; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+    delete[] ev;
+  }
+  if (p->aio_streams) {
+    cudaStream_t* st = static_cast<cudaStream_t*>(p->aio_streams);
+    for (int i = 0; i < 2; ++i)
+      if (st[i]) cudaStreamDestroy(st[i]);
+    delete[] st;
+  }
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
@@ -577,6 +593,59 @@ static hpx_status host_call(hpx_plan p, const void* hin, void* hout, hpx_stream_
   return read_status(p);
 }
 
+// Pipelined host-buffer call: the upload of the input goes on the plan's
+// host-to-device stream into I/O slot k (once the call that last used slot k
+// has downloaded its result), the transform on `stream` after the upload, and
+// the download of the result on the device-to-host stream after the
+// transform.  Consecutive calls alternate slots, so one call's copies overlap
+// the neighbouring calls' kernels in both directions.
+static hpx_status host_call_async(hpx_plan p, const void* hin, void* hout, hpx_stream_t stream, bool analysis) {
+  if (!p || !hin || !hout) {
+    set_error("null argument");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(p->device);
+  const size_t rs = real_size(p);
+  const size_t map_bytes = rs * (size_t)p->nbatch * p->npix;
+  const size_t alm_bytes = 2 * rs * (size_t)p->nbatch * p->nalm;
+  cudaError_t e = cudaSuccess;
+  if (!p->aio_streams) {
+    cudaStream_t* st = new cudaStream_t[2]();
+    p->aio_streams = st;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+    cudaEvent_t* ev = new cudaEvent_t[6]();
+    p->aio_events = ev;
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&p->d_aio_map[k], map_bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&p->d_aio_alm[k], alm_bytes);
+      if (e == cudaSuccess) p->bytes += map_bytes + alm_bytes;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined I/O set-up");
+  }
+  cudaStream_t* st = static_cast<cudaStream_t*>(p->aio_streams);
+  cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->aio_events);  // uploaded[2], computed[2], free[2]
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int k = p->aio_next;
+  p->aio_next ^= 1;
+  void* din = analysis ? p->d_aio_map[k] : p->d_aio_alm[k];
+  void* dout = analysis ? p->d_aio_alm[k] : p->d_aio_map[k];
+  const size_t in_bytes = analysis ? map_bytes : alm_bytes, out_bytes = analysis ? alm_bytes : map_bytes;
+  e = cudaStreamWaitEvent(st[0], ev[4 + k], 0);  // slot k's previous result downloaded
+  if (e == cudaSuccess) e = cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, st[0]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[k], st[0]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[k], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipelined upload");
+  hpx_status r = analysis ? hpx_map2alm(p, din, dout, stream) : hpx_alm2map(p, din, dout, stream);
+  if (r != HPX_OK) return r;
+  e = cudaEventRecord(ev[2 + k], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[2 + k], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hout, dout, out_bytes, cudaMemcpyDeviceToHost, st[1]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[4 + k], st[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "pipelined download");
+  return HPX_OK;
+}
+
 hpx_status hpx_map2alm_iter(hpx_plan p, const void* map, void* alm, int niter, hpx_stream_t stream) {
   hpx_status st = check_call(p, map, alm);
   if (st != HPX_OK) return st;
@@ -652,6 +721,30 @@ hpx_status hpx_plan_device_status(hpx_plan plan) {
   DeviceGuard g(plan->device);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "device synchronise");
+  return read_status(plan);
+}
+
+hpx_status hpx_map2alm_host_async(hpx_plan plan, const void* host_map, void* host_alm, hpx_stream_t stream) {
+  return host_call_async(plan, host_map, host_alm, stream, true);
+}
+
+hpx_status hpx_alm2map_host_async(hpx_plan plan, const void* host_alm, void* host_map, hpx_stream_t stream) {
+  return host_call_async(plan, host_alm, host_map, stream, false);
+}
+
+hpx_status hpx_plan_host_sync(hpx_plan plan) {
+  if (!plan) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  DeviceGuard g(plan->device);
+  if (plan->aio_streams) {
+    cudaStream_t* st = static_cast<cudaStream_t*>(plan->aio_streams);
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaStreamSynchronize(st[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "hpx_plan_host_sync");
+    }
+  }
   return read_status(plan);
 }
 
