@@ -109,7 +109,8 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
 // handles butterflies threadIdx.x + q blockDim.x, q < Q (blockDim.x * Q * R
 // >= M).  tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1).
 template <int R, int Q, bool INV, typename V>
-__device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw) {
+__device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw,
+                                              const V* __restrict__ pre = nullptr) {
   const int nb = (1 << logm) / R;
   V v[Q][R];
 #pragma unroll
@@ -117,7 +118,10 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
     const int j = threadIdx.x + q * blockDim.x;
     if (j < nb) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = buf[pad8(j + r * nb)];
+      for (int r = 0; r < R; ++r) {
+        v[q][r] = buf[pad8(j + r * nb)];
+        if (pre) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
+      }
     }
   }
   __syncthreads();
@@ -150,44 +154,35 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
 // blockDim.x * 16 >= 2^logm.  Caller has synchronised after filling buf.
 // The radix-2 or radix-4 pass comes last: there Ns R = 2^logm, so its writes
 // are contiguous (as a first pass, with Ns = 1, they would conflict).
+// `pre`, if given, multiplies the input pointwise as the first pass reads it.
 template <bool INV, typename V>
-__device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw) {
+__device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, const V* __restrict__ pre = nullptr) {
   int Ns = 1;
   for (int rest = logm; rest >= 3; rest -= 3) {
-    stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw);
+    stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
     Ns <<= 3;
   }
-  if (logm % 3 == 1) stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw);
-  else if (logm % 3 == 2) stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw);
+  if (logm % 3 == 1) stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
+  else if (logm % 3 == 2) stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
 }
 
-// DFT of length H of buf[0..H) (positions pad8) in place, natural order:
-// the power-of-two FFT when H = 2^logm, else Bluestein with the kernel
-// spectrum Bk (length 2^logm, natural order, scaled 1/2^logm).  E is the
-// ring's table exp(-i pi r / N), N = 2H, so the chirp exp(-pi i n^2 / H) is
-// E[2 n^2 mod 2N].  Caller has synchronised after filling buf.
+// DFT of length H of buf[0..H) (positions pad8) in place, natural order: the
+// power-of-two FFT when H = 2^logm; otherwise Bluestein's convolution with the
+// kernel spectrum Bk (length 2^logm, natural order, scaled 1/2^logm), where
+// the caller has already multiplied buf[n] by the chirp C[n] = exp(-pi i n^2 /
+// H) and zero-filled [H, 2^logm), and multiplies output k by C[k] as it
+// reads it.  Caller has synchronised after filling buf.
 template <typename V>
-__device__ void ring_dft(V* buf, int H, int logm, bool bluestein, const V* __restrict__ E,
-                         const V* __restrict__ Bk, const V* __restrict__ tw, int logtw) {
-  if (!bluestein) {
-    fft_pow2<false>(buf, logm, tw, logtw);
-    return;
-  }
-  // chirp index 2 n^2 mod 2N: n < H <= 8192, so 32-bit unsigned arithmetic is exact
-  const unsigned twoN = 4u * (unsigned)H;
-  const int M = 1 << logm;
-  for (int n = threadIdx.x; n < M; n += blockDim.x) {
-    if (n < H) buf[pad8(n)] = cmul(buf[pad8(n)], E[(2u * (unsigned)n * (unsigned)n) % twoN]);
-    else buf[pad8(n)] = cmk<V>(0, 0);
-  }
-  __syncthreads();
+__device__ void ring_dft(V* buf, int logm, bool bluestein, const V* __restrict__ Bk, const V* __restrict__ tw,
+                         int logtw) {
   fft_pow2<false>(buf, logm, tw, logtw);
-  for (int j = threadIdx.x; j < M; j += blockDim.x) buf[pad8(j)] = cmul(buf[pad8(j)], Bk[j]);
-  __syncthreads();
-  fft_pow2<true>(buf, logm, tw, logtw);
-  for (int k = threadIdx.x; k < H; k += blockDim.x)
-    buf[pad8(k)] = cmul(buf[pad8(k)], E[(2u * (unsigned)k * (unsigned)k) % twoN]);
-  __syncthreads();
+  if (bluestein) fft_pow2<true>(buf, logm, tw, logtw, Bk);
+}
+
+// Offset of the chirp table of the cap ring of length N = 4i: i (i - 1).
+__device__ __forceinline__ long long chirp_offset(int N) {
+  const long long i = N >> 2;
+  return i * (i - 1);
 }
 
 // Ring of launch slot q: belt launches take y = y0 + q; cap launches take the
@@ -203,7 +198,7 @@ __device__ __forceinline__ int slot_ring(int q, int caps, int nside) {
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* __restrict__ rings,
-           const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab,
+           const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab, const C2<T>* __restrict__ chirp,
            const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec, int caps, int nside) {
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -213,18 +208,22 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   const int H = R.nphi >> 1, logm = R.logm;
   const bool blue = R.btab >= 0;
   const V* E = etab + R.etab;
-  // (x[2n], x[2n+1]) as one complex sample z[n]
+  const V* C = blue ? chirp + chirp_offset(R.nphi) : nullptr;
+  // (x[2n], x[2n+1]) as one complex sample z[n]; Bluestein: times the chirp,
+  // zero-padded to 2^logm
   const V* x2 = reinterpret_cast<const V*>(map + (long long)b * npix + R.start);
-  for (int n = threadIdx.x; n < H; n += blockDim.x) buf[pad8(n)] = x2[n];
+  const int M = blue ? 1 << logm : H;
+  for (int n = threadIdx.x; n < M; n += blockDim.x)
+    buf[pad8(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
   __syncthreads();
-  ring_dft(buf, H, logm, blue, E, blue ? btab + R.btab : nullptr, tw, logtw);
+  ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
   V* out = spec + (long long)b * nspec + R.specoff;
   for (int k = threadIdx.x; k <= H; k += blockDim.x) {
     const int k1 = (k == H) ? 0 : k;
     const int k2 = (k == 0) ? 0 : H - k;
-    const V zk = buf[pad8(k1)];
-    const V zc = cconj(buf[pad8(k2)]);
+    const V zk = blue ? cmul(buf[pad8(k1)], C[k1]) : buf[pad8(k1)];
+    const V zc = cconj(blue ? cmul(buf[pad8(k2)], C[k2]) : buf[pad8(k2)]);
     const V e = cscale(cadd(zk, zc), (T)0.5);
     const V d = cscale(csub(zk, zc), (T)0.5);
     const V o = cmk<V>(d.y, -d.x);
@@ -241,7 +240,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __restrict__ rings,
-           const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab,
+           const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab, const C2<T>* __restrict__ chirp,
            const C2<T>* __restrict__ tw, int logtw, long long npix, int nring, int mmax,
            int scale_by_weight, int caps, int nside) {
   using V = C2<T>;
@@ -253,6 +252,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   const unsigned twoN = 2u * (unsigned)N;  // sigma m < 2^15: 32-bit arithmetic is exact
   const bool blue = R.btab >= 0;
   const V* E = etab + R.etab;
+  const V* C = blue ? chirp + chirp_offset(N) : nullptr;
   const V* Fy = F + ((long long)b * nring + y) * (mmax + 1);
 
   auto term = [&](int m) -> V {  // F_m exp(+i pi sigma m / N)
@@ -285,7 +285,8 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   __syncthreads();
   // Z[k] = (D[k] + conj D[H-k]) + i exp(2 pi i k / N) (D[k] - conj D[H-k]), k < H;
   // the ring is then z = IDFT_H(Z) with p[2n] = Re z[n], p[2n+1] = Im z[n].
-  // Computed as conj(DFT_H(conj Z)), so conj Z is stored.
+  // Computed as conj(DFT_H(conj Z)), so conj Z (Bluestein: times the chirp,
+  // zero-padded to 2^logm) is stored.
   for (int k = threadIdx.x; k <= H / 2; k += blockDim.x) {
     const int kc = H - k;
     const V dk = buf[pad8(k)], dc = buf[pad8(kc)];
@@ -295,16 +296,21 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
     if (k > 0 && kc != k) {
       const V s2 = cadd(dc, cconj(dk)), d2 = csub(dc, cconj(dk));
       const V t2 = cmul(cconj(E[2 * kc]), d2);
-      buf[pad8(kc)] = cmk<V>(s2.x - t2.y, -(s2.y + t2.x));
+      const V zc = cmk<V>(s2.x - t2.y, -(s2.y + t2.x));
+      buf[pad8(kc)] = blue ? cmul(zc, C[kc]) : zc;
     }
-    buf[pad8(k)] = cconj(zk);
+    buf[pad8(k)] = blue ? cmul(cconj(zk), C[k]) : cconj(zk);
   }
+  // zero padding; position H (read above as D[H] for k = 0) is cleared by
+  // thread 0 after its own read
+  if (blue)
+    for (int n = H + threadIdx.x; n < (1 << logm); n += blockDim.x) buf[pad8(n)] = cmk<V>(0, 0);
   __syncthreads();
-  ring_dft(buf, H, logm, blue, E, blue ? btab + R.btab : nullptr, tw, logtw);
+  ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   const T sc = scale_by_weight ? (T)R.w : (T)1;
   V* out = reinterpret_cast<V*>(map + (long long)b * npix + R.start);
   for (int n = threadIdx.x; n < H; n += blockDim.x) {
-    const V r = buf[pad8(n)];
+    const V r = blue ? cmul(buf[pad8(n)], C[n]) : buf[pad8(n)];
     out[n] = cmk<V>(r.x * sc, -r.y * sc);
   }
 }
@@ -325,6 +331,21 @@ __global__ void k_build_etab(int nside, C2<T>* etab) {
     double sn, cs;
     sincospi((double)r / (double)N, &sn, &cs);
     etab[off + r] = cmk<C2<T>>((T)cs, (T)(-sn));
+  }
+}
+
+// Chirp of the cap ring i (H = 2i, N = 4i): C[n] = E_N[2 n^2 mod 2N] =
+// exp(-pi i n^2 / H), n < H, at offset i (i - 1) -- the same values the
+// E_N table holds, contiguous.
+template <typename T>
+__global__ void k_build_chirp(int nside, C2<T>* chirp) {
+  const int i = blockIdx.y + 1;
+  const long long N = 4LL * i, H = 2LL * i;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < H; n += (long long)gridDim.x * blockDim.x) {
+    const long long r = (2 * n * n) % (2 * N);
+    double sn, cs;
+    sincospi((double)r / (double)N, &sn, &cs);
+    chirp[(long long)i * (i - 1) + n] = cmk<C2<T>>((T)cs, (T)(-sn));
   }
 }
 
@@ -375,6 +396,7 @@ cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s) {
   using V = C2<T>;
   const int ns = p->nside;
   k_build_etab<T><<<dim3(32, ns), 256, 0, s>>>(ns, (V*)p->d_etab);
+  if (ns > 1) k_build_chirp<T><<<dim3(8, ns - 1), 256, 0, s>>>(ns, (V*)p->d_chirp);
   k_build_twiddles<T><<<32, 256, 0, s>>>(p->logtw, (V*)p->d_tw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -420,8 +442,8 @@ cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
     if (e != cudaSuccess || L.nslots <= 0) continue;
     k_ring_r2c<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
-        map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw, p->logtw,
-        p->npix, p->nspec, L.caps, p->nside);
+        map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_chirp,
+        (const V*)p->d_tw, p->logtw, p->npix, p->nspec, L.caps, p->nside);
     e = cudaGetLastError();
   }
   return e;
@@ -434,8 +456,8 @@ cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaSt
   for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
     if (e != cudaSuccess || L.nslots <= 0) continue;
     k_ring_c2r<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
-        (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_tw, p->logtw,
-        p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0, L.caps, p->nside);
+        (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_chirp,
+        (const V*)p->d_tw, p->logtw, p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0, L.caps, p->nside);
     e = cudaGetLastError();
   }
   return e;

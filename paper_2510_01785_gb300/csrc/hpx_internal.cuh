@@ -59,7 +59,8 @@ struct hpx_plan_s {
   long long netab, nbtab;
   hpx::RingInfo* d_ring;
   void* d_etab;        // C2<T> per distinct ring length
-  void* d_btab;        // C2<T> Bluestein kernel spectra, DIF output order, scaled 1/M
+  void* d_btab;        // C2<T> Bluestein kernel spectra, natural order, scaled 1/M
+  void* d_chirp;       // C2<T> per cap ring i (offset i (i - 1)): exp(-pi i n^2 / H), n < H = 2i
   void* d_tw;          // C2<T> tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1)
   double* d_cmm;       // [mmax+1] lambda_mm / sin^m(theta) (sign included)
   double* d_coef_c;    // [nalm] recurrence coefficient c_l of mu_l = c_l z mu_{l-1} - mu_{l-2}
