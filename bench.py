@@ -289,6 +289,9 @@ def run_ours(args):
     rec = timed_steps(plan_r, maps, alm_in, args, dist, dev, world, gpu_index)
     rec["roofline"] = legendre_roofline(plan_r, rec["stages"], table=False)
     active, total = plan_r.chain_stats()
+    # FP64 results on the same inputs: the accuracy of every FP32 plan
+    ref64 = f64_reference(maps, alm_in, dev)
+    rec["accuracy"] = plan_accuracy(plan_r, maps, alm_in, ref64)
     plan_r.close()
 
     # plan-resident lambda table (built by the same FP64 recurrence at plan
@@ -296,7 +299,17 @@ def run_ours(args):
     plan_c = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
     cc = timed_steps(plan_c, maps, alm_in, args, dist, dev, world, gpu_index)
     cc["roofline"] = legendre_roofline(plan_c, cc["stages"], table=True)
+    cc["accuracy"] = plan_accuracy(plan_c, maps, alm_in, ref64)
     plan_c.close()
+    torch.cuda.empty_cache()
+
+    # the same table on the tensor cores with 3xTF32 split products
+    plan_x = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, tensor_cores=True, tf32x3=True,
+                      device=dev)
+    tx = timed_steps(plan_x, maps, alm_in, args, dist, dev, world, gpu_index)
+    tx["roofline"] = legendre_roofline(plan_x, tx["stages"], table=True)
+    tx["accuracy"] = plan_accuracy(plan_x, maps, alm_in, ref64)
+    plan_x.close()
     torch.cuda.empty_cache()
 
     # headline: the same table, Legendre analysis on the tensor cores
@@ -311,6 +324,8 @@ def run_ours(args):
     roofline = legendre_roofline(plan, tab["stages"], table=True)
     t_max, value, stage_report, clk = tab["t_max"], tab["value"], tab["stages"], tab["clocks"]
     launches = tab["launches"]
+    acc = plan_accuracy(plan, maps, alm_in, ref64)
+    del ref64
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
@@ -350,25 +365,51 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX,
                            "nbatch": NBATCH, "step": "map2alm + alm2map of the batch",
                            "lambda": "plan-resident table generated once by the FP64 recurrence",
-                           "analysis": "tensor cores (tcgen05, 3xTF32 split products, FP32 group sums)",
+                           "analysis": "tensor cores (tcgen05 kind::f16): table and operands as FP16 hi/lo "
+                                       "pairs (operands scaled per channel by a power of two), "
+                                       "hi*hi + hi*lo + lo*hi per term, FP32 sums per 64-pair block",
                            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "stages": stage_report, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "stages": stage_report, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
                 "next_rows": next_rows, "out_of_core": ooc,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "table_bytes": tab_bytes_row, "column_table_bytes": tab_bytes_col,
                          "significant_triples": active, "all_triples": total},
-                "cuda_core_table": {"value": cc["value"], "ms_per_step": cc["t_max"] / args.steps,
-                                    "roofline": cc["roofline"], "stages": cc["stages"], "clocks": cc["clocks"]},
-                "lambda_recompute": {"value": rec["value"], "ms_per_step": rec["t_max"] / args.steps,
-                                     "roofline": rec["roofline"], "stages": rec["stages"],
-                                     "clocks": rec["clocks"]}}
+                "tensor_core_tf32x3": {k: tx[k] for k in ("value", "roofline", "stages", "accuracy", "clocks")}
+                | {"ms_per_step": tx["t_max"] / args.steps},
+                "cuda_core_table": {k: cc[k] for k in ("value", "roofline", "stages", "accuracy", "clocks")}
+                | {"ms_per_step": cc["t_max"] / args.steps},
+                "lambda_recompute": {k: rec[k] for k in ("value", "roofline", "stages", "accuracy", "clocks")}
+                | {"ms_per_step": rec["t_max"] / args.steps}}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist.is_available() and dist.is_initialized():
         dist.destroy_process_group()
     return 0
+
+
+def f64_reference(maps, alm_in, dev):
+    """map2alm(maps) and alm2map(alm_in) by an FP64 plan (the CUDA-core FP64
+    path, itself held to 1e-12 of the oracle by the tests)."""
+    import torch
+    import paper_2510_01785_gb300 as hpx
+    with hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f64", device=dev) as p:
+        return p.map2alm(maps.double()), p.alm2map(alm_in.to(torch.complex128))
+
+
+def plan_accuracy(plan, maps, alm_in, ref64):
+    """Largest per-channel relative L2 error of the plan's map2alm and
+    alm2map against the FP64 results."""
+    import torch
+
+    def err(got, ref):
+        d = (got.to(ref.dtype) - ref).reshape(NBATCH, -1)
+        return float((torch.linalg.vector_norm(d, dim=1) /
+                      torch.linalg.vector_norm(ref.reshape(NBATCH, -1), dim=1)).max())
+
+    return {"map2alm_max_rel_l2_vs_f64": err(plan.map2alm(maps), ref64[0]),
+            "alm2map_max_rel_l2_vs_f64": err(plan.alm2map(alm_in), ref64[1])}
 
 
 def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):

@@ -105,15 +105,27 @@ typedef enum {
 #define HPX_PLAN_TENSOR_CORES 2u     /* with HPX_PLAN_LAMBDA_TABLE on an
                                         HPX_F32 plan: both Legendre stages
                                         (Eq. 24-27) run as tensor-core
-                                        matrix products (tcgen05, three TF32
-                                        split products per term, "3xTF32"),
-                                        fed by TMA from the table and from a
-                                        second, transposed copy of it made
-                                        at plan time (about twice the table
-                                        memory).  Results agree with the
-                                        CUDA-core path to FP32 rounding, not
-                                        bit for bit.  Other dtypes or a
+                                        matrix products (tcgen05), fed by TMA
+                                        from the table and from a second,
+                                        transposed copy of it made at plan
+                                        time (about twice the table memory).
+                                        FP32 accuracy from split products:
+                                        every table value and operand is
+                                        stored as an FP16 pair hi + lo (4
+                                        bytes, as a float; the operands per
+                                        channel scaled by a power of two into
+                                        FP16 range) and each term is
+                                        hi*hi + hi*lo + lo*hi with FP32
+                                        accumulation.  Results agree with
+                                        the CUDA-core path to FP32 rounding,
+                                        not bit for bit.  Other dtypes or a
                                         missing table flag: HPX_ERR_INVALID. */
+#define HPX_PLAN_TC_TF32X3 8u        /* with HPX_PLAN_TENSOR_CORES: the
+                                        products from TF32 splits instead
+                                        ("3xTF32": the FP32 table, read as
+                                        TF32 hi, with the TF32 remainders
+                                        formed in the kernel); slower, kept
+                                        for comparison. */
 
 #define HPX_PLAN_LAMBDA_HOST 4u      /* with the tensor-core path: both
                                         lambda tables live in pinned host
@@ -269,6 +281,10 @@ hpx_status hpx_alm2map_host(hpx_plan plan, const void* host_alm,
  *   before any stream capture.
  *   All calls share the array: calls whose work overlaps on the GPU race and
  *   must be ordered by the caller.  Nothing in it needs to start at zero.
+ *   The Legendre stage runs on the CUDA cores: on the plan's table if it
+ *   holds one in the plan's real type, else recomputing lambda (FP32 plans
+ *   with the FP16-split tensor-core tables).  16-bit dtypes:
+ *   HPX_ERR_UNSUPPORTED.
  *   map : device input [nbatch][npix]; alm : device output [nbatch][nalm]. */
 hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* alm,
                                hpx_stream_t stream);

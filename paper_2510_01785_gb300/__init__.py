@@ -56,7 +56,8 @@ class Plan:
 
     def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,
                  dtype: str = "f32", lambda_table: bool = False, device=None,
-                 tensor_cores: bool = False, out_of_core: bool = False, stage_bytes: int = 0):
+                 tensor_cores: bool = False, out_of_core: bool = False, stage_bytes: int = 0,
+                 tf32x3: bool = False):
         mmax = lmax if mmax is None else mmax
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
@@ -74,6 +75,9 @@ class Plan:
         flags = _lib.HPX_PLAN_LAMBDA_TABLE if lambda_table else _lib.HPX_PLAN_LAMBDA_RECOMPUTE
         if tensor_cores:
             flags |= _lib.HPX_PLAN_TENSOR_CORES
+        if tf32x3:  # 3xTF32 split products instead of FP16 hi/lo
+            flags |= _lib.HPX_PLAN_TC_TF32X3
+        self.tf32x3 = tf32x3
         self.out_of_core = out_of_core
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

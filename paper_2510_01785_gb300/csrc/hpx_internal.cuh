@@ -88,7 +88,7 @@ struct hpx_plan_s {
   long long tab_elems;
   // tensor-core Legendre stages (HPX_PLAN_TENSOR_CORES and the 16-bit dtypes)
   int tc_nn_a, tc_nn_s;  // N columns of the analysis / synthesis tiles (0: not used)
-  int tc_mode;         // 0 FP32 (3xTF32), 1 one 16-bit product, 2 16-bit x3
+  int tc_mode;         // 0 FP32 table (3xTF32), 1 one 16-bit product, 2 16-bit x3 (hi, lo)
   int tc_fmt;          // 16-bit operand format: 0 FP16, 1 BF16
   float tc_sfac_a, tc_sfac_s;  // channel-scale bound factors of the current transform
   void* d_tab_lo;      // 16-bit x3: remainders of the row table
@@ -210,7 +210,8 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 // The 16-bit dtypes (HPX_F32_BF16 ...) have only this path; their tables
 // (row and column, hi and for x3 lo parts) are built here too.
 int tc_columns(int nbatch, int cap);  // N of a tile for nbatch channels, at most cap per launch
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype, bool host_tables);
+int tc_mode_of(int dtype, unsigned flags);  // 0 3xTF32, 1 one 16-bit product, 2 16-bit x3; -1 none
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mode, bool host_tables);
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s);
 int tc_channels_per_launch(const hpx_plan_s* p, bool synthesis);
 cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_weight, cudaStream_t s);

@@ -204,7 +204,7 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 4, s, [&](int* n) {
-        *n = 1;
+        *n = p->tc_mode ? 2 : 1;  // 16-bit operands: channel maxima, then the pack
         return launch_pack_tc(p, b0, nb, weighted, s);
       });
       if (e == cudaSuccess)
@@ -228,7 +228,7 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 5, s, [&](int* n) {
-        *n = 1;
+        *n = p->tc_mode ? 2 : 1;
         return launch_pack_at_tc(p, static_cast<const float*>(alm), b0, nb, mfac, s);
       });
       if (e == cudaSuccess)
@@ -334,11 +334,15 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("unknown dtype %d", (int)dtype);
     return HPX_ERR_INVALID;
   }
-  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST)) {
+  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST | HPX_PLAN_TC_TF32X3)) {
     set_error("unknown plan flags 0x%x", flags);
     return HPX_ERR_INVALID;
   }
   const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
+  if ((flags & HPX_PLAN_TC_TF32X3) && (mixed || !(flags & HPX_PLAN_TENSOR_CORES))) {
+    set_error("HPX_PLAN_TC_TF32X3 needs an HPX_F32 plan with HPX_PLAN_TENSOR_CORES");
+    return HPX_ERR_INVALID;
+  }
   if (mixed) {
     flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | (flags & HPX_PLAN_LAMBDA_HOST);  // their only path
   } else if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
@@ -419,7 +423,10 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = build_recurrence_tables(p, s);
-  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && !mixed && !(flags & HPX_PLAN_LAMBDA_HOST))
+  // the CUDA-core table, also the 3xTF32 path's row table; the 16-bit
+  // tensor-core paths build their own
+  if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && tc_mode_of(dtype, flags) <= 0 &&
+      !(flags & HPX_PLAN_LAMBDA_HOST))
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
@@ -471,28 +478,28 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
              (sizeof(int) + 2 * sizeof(double)) * nchain + cs * (size_t)nbatch * nspec +
              cs * (size_t)nbatch * nring * (mmax + 1);
   const size_t ngroup = (npair + 31) / 32;
-  const bool mixed = dtype != HPX_F64 && dtype != HPX_F32;
+  const int mode = tc_mode_of(dtype, flags);
   if (flags & HPX_PLAN_LAMBDA_HOST)  // tables on the host; two staging buffers (1 GiB parts) on the device
-    return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, true);
-  if (mixed) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, false);
+    return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, mode, true);
+  if (mode > 0) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, mode, false);
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored
     b += rs * nalm * npair + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * ngroup;
   if (flags & HPX_PLAN_TENSOR_CORES)  // row-table starts padded to the tile grid; column table; operands
     b += rs * (size_t)(mmax + 1) * ngroup * 32 * (kTcTile - 1) +
-         tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, dtype, false);
+         tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, mode, false);
   return b + sizeof(int);
 }
 
 size_t hpx_plan_table_bytes(hpx_plan plan) {
   if (!plan || (!plan->d_tab && !plan->h_tab)) return 0;
-  const size_t es = plan->dtype == HPX_F64 ? sizeof(double) : plan->dtype == HPX_F32 ? sizeof(float) : 2;
+  const size_t es = plan->dtype == HPX_F64 ? sizeof(double) : plan->tc_mode > 0 ? 2 : sizeof(float);
   const size_t parts = (plan->d_tab_lo || plan->h_tab_lo) ? 2 : 1;
   return (size_t)plan->tab_elems * es * parts;
 }
 
 size_t hpx_plan_column_table_bytes(hpx_plan plan) {
   if (!plan || (!plan->d_stab && !plan->h_stab)) return 0;
-  const size_t es = plan->dtype == HPX_F32 ? sizeof(float) : 2;
+  const size_t es = plan->tc_mode > 0 ? 2 : sizeof(float);
   const size_t parts = (plan->d_stab_lo || plan->h_stab_lo) ? 2 : 1;
   return (size_t)plan->stab_elems * es * parts;
 }

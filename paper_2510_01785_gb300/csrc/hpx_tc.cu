@@ -48,6 +48,11 @@ namespace hpx {
 namespace {
 
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
+// 16-bit lambda tables hold 2^9 lambda (|lambda_lm| <= sqrt((2l+1)/4pi) < 64
+// for l < 25000, so 2^9 |lambda| < 2^15 stays in FP16 range), which keeps
+// the FP16 remainder parts of small values out of the subnormal range; the
+// epilogues multiply by 2^-9.
+constexpr double kLamScale = 512.0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -212,7 +217,7 @@ __device__ __forceinline__ float chan_scale(const unsigned* bmax, int b, float s
   if (!(amax > 0.f) || !(amax < 3.0e38f)) return 1.f;
   int e;
   frexpf(amax, &e);  // amax < 2^e
-  return ldexpf(1.f, 14 - e);
+  return ldexpf(1.f, min(14 - e, 126));  // 2^126 at most, so that the scale and its inverse are normal
 }
 
 // Largest |component| of each channel b0 .. b0+nb-1 of x ([b][stride] floats,
@@ -400,8 +405,9 @@ __global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __
   const int ls = lstart[mg];
   const long long o = off[mg] - base + (p % KW);
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
+  constexpr double kS = sizeof(E) == 2 ? kLamScale : 1.0;
   for (int l = ls; l <= lmax; ++l) {
-    const double mu = p < npair ? ch.step(l) : 0.0;
+    const double mu = p < npair ? kS * ch.step(l) : 0.0;
     const E h = Elt<E>::from_double(mu);
     hi[o + (long long)(l - ls) * KW] = h;
     if (lo) lo[o + (long long)(l - ls) * KW] = Elt<E>::from_double(mu - Elt<E>::to_double(h));
@@ -442,13 +448,14 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
   const int lend = ls + ((lmax - ls) / KW + 1) * KW;  // end of the last block
   const long long o = off[mT] - base + (long long)(p & 127) * KW;
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
+  constexpr double kS = sizeof(E) == 2 ? kLamScale : 1.0;
   for (int lv = ls; lv < lend; lv += V) {
     alignas(16) E h[V];
     alignas(16) E r[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       const int l = lv + u;
-      const double mu = (l <= lmax && p < npair) ? ch.step(l) : 0.0;
+      const double mu = (l <= lmax && p < npair) ? kS * ch.step(l) : 0.0;
       h[u] = Elt<E>::from_double(mu);
       r[u] = Elt<E>::from_double(mu - Elt<E>::to_double(h[u]));
     }
@@ -500,6 +507,7 @@ struct TcArgs {
   const double* coef_p;     // analysis: P_l
   const unsigned* bmax;     // 16-bit operands: per-channel largest component
   float sfac;               // bound factor for the channel scale
+  float lscale;             // 1 / the table's lambda scale
   float* out;               // analysis: alm [b][nalm] complex; synthesis: F [b][nring][mmax+1] complex
   int lmax, mmax, npair, nring;
   long long nalm;
@@ -818,7 +826,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
           for (int c = 0; c < C2N / 2; ++c) {
             if (c < a.nb) {
-              const float inv = 1.f / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
+              const float inv = a.lscale / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
               const float er = sum[2 * c] * inv, ei = sum[2 * c + 1] * inv;
               const float orr = sum[C2N + 2 * c] * inv, oi = sum[C2N + 2 * c + 1] * inv;
               const long long fb = (long long)(a.b0 + c) * a.nring;
@@ -829,7 +837,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       } else if (l <= a.lmax) {
         const long long base = alm_base(a.lmax, m);
-        const double scale = a.coef_p[base + l] * (m > 0 ? a.mfac : 1.0);
+        const double scale = a.coef_p[base + l] * (m > 0 ? a.mfac : 1.0) * (double)a.lscale;
         float2* out = reinterpret_cast<float2*>(a.out) + (long long)a.b0 * a.nalm + base + l;
 #pragma unroll
         for (int c = 0; c < C2N / 2; ++c)
@@ -890,6 +898,7 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.coef_p = p->d_coef_p;
   a.bmax = p->tc_mode ? p->d_bmax : nullptr;
   a.sfac = syn ? p->tc_sfac_s : p->tc_sfac_a;
+  a.lscale = p->tc_mode ? (float)(1.0 / kLamScale) : 1.f;
   a.out = out;
   a.lmax = p->lmax;
   a.mmax = p->mmax;
@@ -1026,14 +1035,20 @@ cudaError_t tile_all(hpx_plan_s* p, float* out, int b0, int nb, double mfac, cud
   return e;
 }
 
-int tc_mode_of(int dtype) {
+}  // namespace
+
+int tc_mode_of(int dtype, unsigned flags) {
   switch (dtype) {
-    case HPX_F32: return 0;
+    case HPX_F32:
+      if (!(flags & HPX_PLAN_TENSOR_CORES)) return -1;
+      return (flags & HPX_PLAN_TC_TF32X3) ? 0 : 2;  // FP32 plans: FP16 hi/lo unless 3xTF32 is asked for
     case HPX_F32_BF16: case HPX_F32_FP16: return 1;
     case HPX_F32_BF16X3: case HPX_F32_FP16X3: return 2;
     default: return -1;
   }
 }
+
+namespace {
 
 cudaError_t absmax(hpx_plan_s const* p, const float* x, long long n, long long stride, int b0, int nb,
                    cudaStream_t s) {
@@ -1054,8 +1069,7 @@ int tc_columns(int nbatch, int cap) {
 
 int tc_channels_per_launch(const hpx_plan_s* p, bool syn) { return (syn ? p->tc_nn_s : p->tc_nn_a) / 4; }
 
-size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int dtype, bool host_tables) {
-  const int mode = tc_mode_of(dtype);
+size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mode, bool host_tables) {
   if (mode < 0) return 0;
   const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
   const size_t npair = 2 * (size_t)nside, ngroup = (npair + kw - 1) / kw, nptile = (npair + 127) / 128;
@@ -1154,10 +1168,10 @@ void free_tc_host(hpx_plan_s* p) {
 }
 
 cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
-  const int mode = tc_mode_of(p->dtype);
+  const int mode = tc_mode_of(p->dtype, p->flags);
   if (mode < 0) return cudaErrorInvalidValue;
   p->tc_mode = mode;
-  p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;
+  p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;  // FP32 plans: FP16
   const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
   const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
   const int nna = tc_columns(p->nbatch, mode ? 64 : 32), nns = tc_columns(p->nbatch, 32);

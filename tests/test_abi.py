@@ -69,7 +69,7 @@ def test_null_plan_calls_are_rejected(hpxlib):
     assert L.hpx_plan_device_status(None) == 1
 
 
-@pytest.mark.parametrize("dtype,flags", [(0, 3), (1, 2), (0, 2), (1, 4)])
+@pytest.mark.parametrize("dtype,flags", [(0, 3), (1, 2), (0, 2), (1, 4), (1, 9), (0, 11), (2, 8)])
 def test_tensor_core_flag_needs_an_f32_table_plan(hpxlib, dtype, flags):
     L = hpxlib.lib()
     h = ctypes.c_void_p()

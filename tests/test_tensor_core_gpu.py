@@ -1,8 +1,9 @@
-"""Tensor-core (tcgen05, 3xTF32) Legendre stages against the FP64 oracle
-and against the CUDA-core path on the same table.
+"""Tensor-core (tcgen05) Legendre stages of the FP32 plan, in both split
+schemes (FP16 hi/lo, the default, and 3xTF32), against the FP64 oracle and
+against the CUDA-core path on the same table.
 
 The tensor-core plan computes the same sums as the CUDA-core FP32 path, in a
-different order and from TF32 split products, so it is held to the FP32
+different order and from split products, so it is held to the FP32
 tolerance against the oracle (relative L2 per channel <= 1e-5) and its
 error may not exceed twice that of the CUDA-core FP32 path (plus 1e-6).
 Cases cover every N tile (8, 16 and 32 channels per launch), more channels
@@ -50,14 +51,19 @@ CASES = [
 ]
 
 
+SCHEMES = {"fp16-split": False, "tf32x3": True}
+
+
+@pytest.mark.parametrize("scheme", list(SCHEMES))
 @pytest.mark.parametrize("case", CASES, ids=[f"ns{c[0]}-l{c[1]}-m{c[2]}-b{c[3]}" for c in CASES])
-def test_tensor_core_parity(case):
+def test_tensor_core_parity(case, scheme):
     nside, lmax, mmax, nb = case
     maps = syn.white_maps(syn.SEED_BASE + 300 + nside, nside, nb).astype(np.float32)
     alm = syn.gaussian_alm(syn.SEED_BASE + 400 + nside, lmax, mmax, nb, power=1.0).astype(np.complex64)
     m64, a64 = maps.astype(np.float64), alm.astype(np.complex128)
     h = hpx()
-    with h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True, tensor_cores=True) as pc, \
+    with h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True, tensor_cores=True,
+                tf32x3=SCHEMES[scheme]) as pc, \
             h.Plan(nside, lmax, mmax, nb, "f32", lambda_table=True) as pt:
         dm, da = torch.from_numpy(maps).cuda(), torch.from_numpy(alm).cuda()
         ops = (("map2alm", dm), ("alm2map_adjoint", dm), ("alm2map", da), ("map2alm_adjoint", da))
@@ -77,6 +83,26 @@ def test_tensor_core_parity(case):
                 assert e <= 2.0 * e_cc + 1e-6, (k, e, e_cc)
         a = got["map2alm"].cpu().numpy()
         assert np.all(a[:, : lmax + 1].imag == 0.0)
+
+
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_tensor_core_dynamic_range(scheme):
+    """Channels scaled by 1e-30 .. 1e30 (FP32's range; far outside FP16's):
+    every channel keeps the FP32 tolerance, so the per-channel power-of-two
+    scaling of the 16-bit operands covers the whole float range."""
+    nside, lmax, nb = 32, 95, 7
+    sc = np.array([1e-30, 1e-12, 1e-3, 1.0, 1e5, 1e18, 1e30])
+    maps = (syn.white_maps(syn.SEED_BASE + 61, nside, nb) * sc[:, None]).astype(np.float32)
+    alm = (syn.gaussian_alm(syn.SEED_BASE + 62, lmax, lmax, nb, power=2.0) * sc[:, None]).astype(np.complex64)
+    with hpx().Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True,
+                    tf32x3=SCHEMES[scheme]) as pc:
+        a = pc.map2alm(torch.from_numpy(maps).cuda()).cpu().numpy()
+        s = pc.alm2map(torch.from_numpy(alm).cuda()).cpu().numpy()
+        pc.device_status()
+    ea = rel_err(a, oracle.map2alm(maps.astype(np.float64), lmax, lmax))
+    es = rel_err(s, oracle.alm2map(alm.astype(np.complex128), nside, lmax, lmax))
+    print(scheme, ea, es)
+    assert ea <= 1e-5 and es <= 1e-5
 
 
 def test_tensor_core_gradient_scaling():
@@ -116,8 +142,9 @@ NS2, L2, B2 = 1024, 3071, 8
 
 
 def test_cfg2_tensor_core_sampled():
-    """Nside 1024, lmax 3071, 8 channels: sampled coefficients and rings
-    against the oracle, and whole outputs against the CUDA-core table plan."""
+    """Nside 1024, lmax 3071, 8 channels (the default FP16 hi/lo scheme, as
+    benchmarked): sampled coefficients and rings against the oracle, and
+    whole outputs against the CUDA-core table plan."""
     maps = syn.white_maps(syn.SEED_BASE + 2, NS2, B2).astype(np.float32)
     alm_in = syn.gaussian_alm(syn.SEED_BASE + 3, L2, L2, B2, power=2.0).astype(np.complex64)
     h = hpx()

@@ -41,6 +41,26 @@ def test_noalloc_matches_map2alm_twice(dtype, nside, lmax, nbatch):
             assert rel(out, ref) <= TOL[dtype], (call, rel(out, ref))
 
 
+@pytest.mark.parametrize("tf32x3", [False, True])
+def test_noalloc_on_tensor_core_plans(tf32x3):
+    """On a tensor-core plan the call runs the CUDA-core analysis: on the
+    plan's FP32 table (3xTF32 plans) or recomputing lambda (FP16-split
+    plans, whose 16-bit table the CUDA-core kernels cannot read)."""
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300._lib import lib
+    nside, lmax, nb = 64, 191, 3
+    maps = torch.from_numpy(syn.white_maps(13, nside, nb)).to("cuda", torch.float32)
+    with hpx.Plan(nside, lmax, lmax, nb, "f32") as pr:
+        ref = pr.map2alm(maps)
+    with hpx.Plan(nside, lmax, lmax, nb, "f32", lambda_table=True, tensor_cores=True, tf32x3=tf32x3) as p:
+        out = p.empty_alm()
+        st = lib().hpx_map2alm_noalloc(p._h, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == 0, lib().hpx_last_error()
+        torch.cuda.synchronize()
+        assert rel(out, ref) <= TOL["f32"]
+
+
 def test_noalloc_rejects_plans_beyond_its_array():
     import paper_2510_01785_gb300 as hpx
     from paper_2510_01785_gb300._lib import lib
