@@ -450,7 +450,7 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
     report = {}
     for k, (ms, n) in stages.items():
         if n > 0 or k != "analysis_operand_pack":
-            report[k] = {"ms_per_launch": ms / max(n, 1), "launches": n}
+            report[k] = {"ms_per_step": ms / args.steps, "ms_per_launch": ms / max(n, 1), "launches": n}
     return {"t_max": t_max, "value": throughput(world, args.steps, t_max), "stages": report,
             "clocks": clk, "launches": sum(n for _, n in stages.values())}
 
@@ -475,7 +475,7 @@ def legendre_roofline(plan, stages, table: bool):
                   ("analysis_operand_pack", spec_bytes + gt_bytes)):
         if k in stages:
             s = stages[k]
-            s["hbm_gbs_algorithmic"] = by / (s["ms_per_launch"] / 1e3) / 1e9
+            s["hbm_gbs_algorithmic"] = by / (s["ms_per_step"] / 1e3) / 1e9
     fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
     # the tensor-core synthesis reads the column copy of the table and its packed operand
     ctab_bytes = plan.column_table_bytes if (table and tc) else tab_bytes

@@ -199,7 +199,8 @@ template <typename T>
 __global__ void __launch_bounds__(512)
 k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* __restrict__ rings,
            const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab, const C2<T>* __restrict__ chirp,
-           const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec, int caps, int nside) {
+           const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec, int caps, int nside,
+           unsigned* __restrict__ bmax) {
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -219,6 +220,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
   V* out = spec + (long long)b * nspec + R.specoff;
+  T amax = 0;  // largest |component| written by this thread
   for (int k = threadIdx.x; k <= H; k += blockDim.x) {
     const int k1 = (k == H) ? 0 : k;
     const int k2 = (k == 0) ? 0 : H - k;
@@ -227,7 +229,18 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
     const V e = cscale(cadd(zk, zc), (T)0.5);
     const V d = cscale(csub(zk, zc), (T)0.5);
     const V o = cmk<V>(d.y, -d.x);
-    out[k] = cadd(e, cmul(E[2 * k], o));
+    const V X = cadd(e, cmul(E[2 * k], o));
+    out[k] = X;
+    amax = fmax(amax, fmax(fabs(X.x), fabs(X.y)));
+  }
+  // the channel's largest spectrum component, for the 16-bit operand scale
+  // of the tensor-core analysis (float plans only; blockDim is a multiple of 32)
+  if constexpr (sizeof(T) == 4) {
+    if (bmax) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+      if ((threadIdx.x & 31) == 0) atomicMax(bmax + b, __float_as_uint(amax));
+    }
   }
 }
 
@@ -439,11 +452,15 @@ template <typename T>
 cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   using V = C2<T>;
   cudaError_t e = allow_max_smem(k_ring_r2c<T>);
+  // tensor-core plans with 16-bit operands record each channel's largest
+  // spectrum component here (zeroed first)
+  unsigned* bmax = (sizeof(T) == 4 && p->tc_mode > 0) ? p->d_bmax : nullptr;
+  if (e == cudaSuccess && bmax) e = cudaMemsetAsync(bmax, 0, sizeof(unsigned) * p->nbatch, s);
   for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
     if (e != cudaSuccess || L.nslots <= 0) continue;
     k_ring_r2c<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
         map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_chirp,
-        (const V*)p->d_tw, p->logtw, p->npix, p->nspec, L.caps, p->nside);
+        (const V*)p->d_tw, p->logtw, p->npix, p->nspec, L.caps, p->nside, bmax);
     e = cudaGetLastError();
   }
   return e;

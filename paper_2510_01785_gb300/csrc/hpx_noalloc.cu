@@ -93,6 +93,7 @@ extern "C" hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* 
     view.d_spec = scratch;
     view.timing = nullptr;
     if (plan->tc_mode > 0) view.d_tab = nullptr;  // a 16-bit tensor-core table: recompute lambda instead
+    view.d_bmax = nullptr;                         // no operand scales: the plan's own calls own them
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int nlaunch = 0;
     cudaError_t e;

@@ -195,7 +195,7 @@ template <typename T>
 static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool weighted, double mfac,
                                 cudaStream_t s) {
   cudaError_t e = staged(p, 0, s, [&](int* n) {
-    *n = 1;
+    *n = p->nside > 1 ? 2 : 1;  // belt and cap rings
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e != cudaSuccess) return e;
@@ -204,7 +204,7 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 4, s, [&](int* n) {
-        *n = p->tc_mode ? 2 : 1;  // 16-bit operands: channel maxima, then the pack
+        *n = 1;
         return launch_pack_tc(p, b0, nb, weighted, s);
       });
       if (e == cudaSuccess)
@@ -228,7 +228,7 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
       e = staged(p, 5, s, [&](int* n) {
-        *n = p->tc_mode ? 2 : 1;
+        *n = p->tc_mode ? 2 : 1;  // 16-bit operands: channel maxima, then the pack
         return launch_pack_at_tc(p, static_cast<const float*>(alm), b0, nb, mfac, s);
       });
       if (e == cudaSuccess)
@@ -242,7 +242,7 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
   }
   if (e == cudaSuccess)
     e = staged(p, 3, s, [&](int* n) {
-      *n = 1;
+      *n = p->nside > 1 ? 2 : 1;
       return launch_c2r<T>(p, static_cast<T*>(map), weighted, s);
     });
   return e;

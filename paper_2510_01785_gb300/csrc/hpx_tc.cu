@@ -220,14 +220,17 @@ __device__ __forceinline__ float chan_scale(const unsigned* bmax, int b, float s
   return ldexpf(1.f, min(14 - e, 126));  // 2^126 at most, so that the scale and its inverse are normal
 }
 
-// Largest |component| of each channel b0 .. b0+nb-1 of x ([b][stride] floats,
-// n per channel), as float bits, into bmax[b] (atomic max; zeroed first).
-__global__ void k_absmax(const float* __restrict__ x, long long n, long long stride, int b0, unsigned* bmax) {
+// Largest |component| of each channel b0 .. b0+nb-1 of x ([b][stride]
+// complex values, n per channel), as float bits, into bmax[b] (atomic max;
+// zeroed first).
+__global__ void k_absmax(const float2* __restrict__ x, long long n, long long stride, int b0, unsigned* bmax) {
   const int b = b0 + blockIdx.y;
-  const float* xb = x + (long long)b * stride;
+  const float2* xb = x + (long long)b * stride;
   float v = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    v = fmaxf(v, fabsf(xb[i]));
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 q = xb[i];
+    v = fmaxf(v, fmaxf(fabsf(q.x), fabsf(q.y)));
+  }
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) atomicMax(bmax + b, __float_as_uint(v));
 }
@@ -306,8 +309,8 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
 // NN .. 2 NN - 1.  Only Re a_l0 enters (real maps).
 template <int CP, typename E>
 __global__ void __launch_bounds__(128)
-k_pack_at(const float2* __restrict__ alm, const double* __restrict__ coef_p, const long long* __restrict__ achunk,
-          E* __restrict__ at, int lmax, int mmax, long long nalm, int b0, int nb, double mfac, int x3,
+k_pack_at(const float2* __restrict__ alm, const float* __restrict__ coef_pf, const long long* __restrict__ achunk,
+          E* __restrict__ at, int lmax, int mmax, long long nalm, int b0, int nb, float mfac, int x3,
           const unsigned* __restrict__ bmax, float sfac) {
   constexpr int KW = Elt<E>::kw, C2N = 2 * CP, NN = 2 * C2N;
   const int rb = x3 ? 2 * NN : NN;
@@ -318,14 +321,15 @@ k_pack_at(const float2* __restrict__ alm, const double* __restrict__ coef_p, con
   const bool in = l <= lmax;
   const bool odd = ((l - m) & 1) != 0;
   const long long base = alm_base(lmax, m);
-  const double s = in ? coef_p[base + l] * (m > 0 ? mfac : 1.0) : 0.0;
+  // P_l (FP32) times factors of two (mfac, the channel scale): exact
+  const float s = in ? coef_pf[base + l] * (m > 0 ? mfac : 1.f) : 0.f;
 #pragma unroll 4
   for (int c = 0; c < CP; ++c) {
     float2 a = make_float2(0.f, 0.f);
     if (in && c < nb) {
       a = alm[(long long)(b0 + c) * nalm + base + l];
-      const double sc = s * (double)chan_scale(bmax, b0 + c, sfac);
-      a = make_float2((float)(sc * a.x), m == 0 ? 0.f : (float)(sc * a.y));
+      const float sc = s * chan_scale(bmax, b0 + c, sfac);
+      a = make_float2(sc * a.x, m == 0 ? 0.f : sc * a.y);
     }
     const float2 e = odd ? make_float2(0.f, 0.f) : a, o = odd ? a : make_float2(0.f, 0.f);
     put(out, 2 * c, NN, e.x, x3);
@@ -504,7 +508,7 @@ struct TcArgs {
   const int* lstart;        // first l stored, same indexing
   int ngroup;               // groups (analysis) or p tiles (synthesis) per m
   const long long* achunk;  // synthesis: first At chunk of each m
-  const double* coef_p;     // analysis: P_l
+  const float* coef_pf;     // analysis: P_l (FP32)
   const unsigned* bmax;     // 16-bit operands: per-channel largest component
   float sfac;               // bound factor for the channel scale
   float lscale;             // 1 / the table's lambda scale
@@ -837,13 +841,14 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       } else if (l <= a.lmax) {
         const long long base = alm_base(a.lmax, m);
-        const double scale = a.coef_p[base + l] * (m > 0 ? a.mfac : 1.0) * (double)a.lscale;
+        // P_l (FP32) times powers of two (mfac, the table and channel scales)
+        const float scale = a.coef_pf[base + l] * (m > 0 ? (float)a.mfac : 1.f) * a.lscale;
         float2* out = reinterpret_cast<float2*>(a.out) + (long long)a.b0 * a.nalm + base + l;
 #pragma unroll
         for (int c = 0; c < C2N / 2; ++c)
-          if (c < a.nb) {
-            const double sc = scale / (double)chan_scale(a.bmax, a.b0 + c, a.sfac);
-            out[(long long)c * a.nalm] = make_float2((float)(sc * sum[2 * c]), (float)(sc * sum[2 * c + 1]));
+          if (c < a.nb) {  // the channel scale last: exact unless the result itself is subnormal
+            const float inv = 1.f / chan_scale(a.bmax, a.b0 + c, a.sfac);
+            out[(long long)c * a.nalm] = make_float2(scale * sum[2 * c] * inv, scale * sum[2 * c + 1] * inv);
           }
       }
     }
@@ -895,7 +900,7 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.lstart = syn ? p->d_stab_lstart : p->d_tab_lstart;
   a.ngroup = syn ? p->nptile : p->ngroup;
   a.achunk = p->d_achunk;
-  a.coef_p = p->d_coef_p;
+  a.coef_pf = p->d_coef_pf;
   a.bmax = p->tc_mode ? p->d_bmax : nullptr;
   a.sfac = syn ? p->tc_sfac_s : p->tc_sfac_a;
   a.lscale = p->tc_mode ? (float)(1.0 / kLamScale) : 1.f;
@@ -938,7 +943,7 @@ cudaError_t pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, do
   constexpr int KW = Elt<E>::kw;
   const int nchunk0 = p->lmax / KW + 1;  // chunks of m = 0, the most
   k_pack_at<CP, E><<<dim3((nchunk0 + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
-      (const float2*)alm, p->d_coef_p, p->d_achunk, (E*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, mfac,
+      (const float2*)alm, p->d_coef_pf, p->d_achunk, (E*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, (float)mfac,
       p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_s);
   return cudaGetLastError();
 }
@@ -1050,12 +1055,12 @@ int tc_mode_of(int dtype, unsigned flags) {
 
 namespace {
 
-cudaError_t absmax(hpx_plan_s const* p, const float* x, long long n, long long stride, int b0, int nb,
+cudaError_t absmax(hpx_plan_s const* p, const float2* x, long long n, long long stride, int b0, int nb,
                    cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p->d_bmax + b0, 0, sizeof(unsigned) * nb, s);
   if (e != cudaSuccess) return e;
-  const long long blocks = (n + 255) / 256;
-  k_absmax<<<dim3((unsigned)(blocks < 256 ? blocks : 256), nb), 256, 0, s>>>(x, n, stride, b0, p->d_bmax);
+  const long long blocks = (n + 1023) / 1024;  // about four values per thread
+  k_absmax<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), nb), 256, 0, s>>>(x, n, stride, b0, p->d_bmax);
   return cudaGetLastError();
 }
 
@@ -1337,11 +1342,9 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
 }
 
 cudaError_t launch_pack_tc(hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
-  if (p->tc_mode) {  // channel scales from the spectra: |S|, |A| <= 2 sqrt(2) w max|component|
-    p->tc_sfac_a = 3.0f * (use_w ? (float)p->w_max : 1.0f);
-    cudaError_t e = absmax(p, (const float*)p->d_spec, 2 * p->nspec, 2 * p->nspec, b0, nb, s);
-    if (e != cudaSuccess) return e;
-  }
+  // channel scales from the spectra (their largest components were recorded
+  // by the ring transform): |S|, |A| <= 2 sqrt(2) w max|component|
+  if (p->tc_mode) p->tc_sfac_a = 3.0f * (use_w ? (float)p->w_max : 1.0f);
   switch (p->tc_nn_a) {
     case 32: return pack_gt_t<8>(p, b0, nb, use_w, s);
     case 64: return pack_gt_t<16>(p, b0, nb, use_w, s);
@@ -1358,7 +1361,7 @@ cudaError_t launch_tile_tc(hpx_plan_s* p, float* alm, int b0, int nb, double mfa
 cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
   if (p->tc_mode) {  // channel scales from alm: |P_l mfac a| <= 1.2 max(mfac, 1) max|component|
     p->tc_sfac_s = 1.2f * (float)(mfac > 1.0 ? mfac : 1.0);
-    cudaError_t e = absmax(p, alm, 2 * p->nalm, 2 * p->nalm, b0, nb, s);
+    cudaError_t e = absmax(p, reinterpret_cast<const float2*>(alm), p->nalm, p->nalm, b0, nb, s);
     if (e != cudaSuccess) return e;
   }
   switch (p->tc_nn_s) {
