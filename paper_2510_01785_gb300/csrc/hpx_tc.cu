@@ -242,61 +242,96 @@ __global__ void k_absmax(const float2* __restrict__ x, long long n, long long st
 // nothing) G(y) = W_y X_y[m mod N] exp(-i m phi_0) as in the CUDA-core
 // analysis; row n < 2 CP holds part n%2 of S = G(north) + G(south) for channel
 // n/2, row 2 CP + n that of A = G(north) - G(south), times the channel's
-// scale; for x3 rows NN .. 2 NN - 1 hold the remainders.  KW consecutive
-// threads per group (one tile column each).
-template <int CP, typename E>
-__global__ void __launch_bounds__(128)
+// scale; for x3 rows NN .. 2 NN - 1 hold the remainders.
+//
+// One CTA: group g (KW pairs) x kPackM consecutive m x kPackC channels.  The
+// spectra are read along m (kPackM consecutive bins of one ring and channel
+// are contiguous), the values go to shared memory in the operand's row
+// layout, and each m's rows leave as contiguous 128-byte lines.  A thread
+// takes one (m, pair) at a time -- ring data, bin and phases once -- and
+// all the CTA's channels of it.
+constexpr int kPackM = 8, kPackC = 8;
+
+__host__ __device__ constexpr int pack_rows(bool x3) { return (x3 ? 8 : 4) * kPackC; }  // shared rows per m
+__host__ __device__ constexpr int pack_slab(int rows) { return rows * 128 + 16; }  // bytes; 16 against bank conflicts
+
+template <typename E>
+__global__ void __launch_bounds__(256)
 k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, const RingInfo* __restrict__ rings,
-          E* __restrict__ gt, int npair, int nring, int ngroup, long long nspec, int b0, int nb, int use_w, int x3,
-          const unsigned* __restrict__ bmax, float sfac) {
-  constexpr int KW = Elt<E>::kw, C2N = 2 * CP, NN = 2 * C2N;
-  const int rb = x3 ? 2 * NN : NN;
-  const int g = blockIdx.x * (128 / KW) + threadIdx.x / KW, m = blockIdx.y, lane = threadIdx.x % KW;
-  if (g >= ngroup) return;
-  const int p = g * KW + lane;
-  E* out = gt + ((long long)m * ngroup + g) * rb * KW + lane;
-  const bool active = p < npair;
-  const bool has_south = active && p != npair - 1;
-  int k = 0, N = 2;
-  float2 en = make_float2(0.f, 0.f), es = en;
-  long long on = 0, os = 0;
-  float wn = 1.f, ws = 1.f;
-  if (active) {
-    const RingInfo Rn = rings[p];
-    N = Rn.nphi;
-    k = m % N;
-    en = etab[Rn.etab + ((long long)Rn.sigma * m) % (2LL * N)];
-    on = Rn.specoff;
-    if (use_w) wn = (float)Rn.w;
-    if (has_south) {  // mirror ring: same length, same table
-      const RingInfo Rs = rings[nring - 1 - p];
-      es = etab[Rs.etab + ((long long)Rs.sigma * m) % (2LL * N)];
-      os = Rs.specoff;
-      if (use_w) ws = (float)Rs.w;
+          E* __restrict__ gt, int npair, int nring, int ngroup, long long nspec, int mmax, int NN, int b0, int nb,
+          int use_w, int x3, const unsigned* __restrict__ bmax, float sfac) {
+  constexpr int KW = Elt<E>::kw;
+  // dynamic shared memory only (the launch may raise its limit to the
+  // device maximum): kPackM slabs, then the channel scales
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = blockIdx.x, m0 = blockIdx.y * kPackM, c0 = blockIdx.z * kPackC;
+  const int C2N = NN / 2, rb = x3 ? 2 * NN : NN;
+  const int rows = pack_rows(x3 != 0), slab = pack_slab(rows);
+  float* csc = reinterpret_cast<float*>(smem_raw + kPackM * slab);
+  if (threadIdx.x < kPackC) {
+    const int c = c0 + threadIdx.x;
+    csc[threadIdx.x] = c < nb ? chan_scale(bmax, b0 + c, sfac) : 0.f;
+  }
+  __syncthreads();
+  const int nch = min(kPackC, nb - c0);  // channels with data; the rest are zero rows
+  for (int i = threadIdx.x; i < kPackM * KW; i += blockDim.x) {
+    const int ml = i % kPackM, pl = i / kPackM;
+    const int m = m0 + ml, p = g * KW + pl;
+    const bool act = m <= mmax && p < npair;
+    const bool south = act && p != npair - 1;  // the equator ring has no mirror
+    long long on = 0, os = 0;
+    int kk = 0;
+    bool conj = false;
+    float2 en = make_float2(0.f, 0.f), es = en;
+    if (act) {
+      const RingInfo Rn = rings[p];
+      const unsigned N = (unsigned)Rn.nphi, k = (unsigned)m % N, twoN = 2u * N;
+      conj = k > (N >> 1);
+      kk = (int)(conj ? N - k : k);
+      on = Rn.specoff;  // sigma m < 2^15: the phase index in 32 bits
+      en = cscale(etab[Rn.etab + ((unsigned)Rn.sigma * (unsigned)m) % twoN], use_w ? (float)Rn.w : 1.f);
+      if (south) {  // mirror ring: same length, same table
+        const RingInfo Rs = rings[nring - 1 - p];
+        os = Rs.specoff;
+        es = cscale(etab[Rs.etab + ((unsigned)Rs.sigma * (unsigned)m) % twoN], use_w ? (float)Rs.w : 1.f);
+      }
+    }
+    E* T = reinterpret_cast<E*>(smem_raw + ml * slab) + pl;
+#pragma unroll 2
+    for (int cl = 0; cl < kPackC; ++cl) {
+      float2 gn = make_float2(0.f, 0.f), gs = gn;
+      if (act && cl < nch) {
+        const float2* X = spec + (long long)(b0 + c0 + cl) * nspec;
+        float2 x = X[on + kk];
+        gn = cmul(conj ? cconj(x) : x, en);
+        if (south) {
+          x = X[os + kk];
+          gs = cmul(conj ? cconj(x) : x, es);
+        }
+      }
+      const float sc = csc[cl];
+      const float v[4] = {(gn.x + gs.x) * sc, (gn.y + gs.y) * sc, (gn.x - gs.x) * sc, (gn.y - gs.y) * sc};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = (q >> 1) * 2 * kPackC + 2 * cl + (q & 1);  // S rows, then A rows
+        const E h = Elt<E>::from_float(v[q]);
+        T[r * KW] = h;
+        if (x3) T[(r + 4 * kPackC) * KW] = Elt<E>::from_float(v[q] - Elt<E>::to_float(h));
+      }
     }
   }
-  const bool conj = k > (N >> 1);
-  const int kk = conj ? N - k : k;
-#pragma unroll 4
-  for (int c = 0; c < CP; ++c) {
-    float2 gn = make_float2(0.f, 0.f), gs = gn;
-    float sc = 1.f;
-    if (active && c < nb) {
-      const float2* X = spec + (long long)(b0 + c) * nspec;
-      float2 x = X[on + kk];
-      if (conj) x = cconj(x);
-      gn = cscale(cmul(x, en), wn);
-      if (has_south) {
-        x = X[os + kk];
-        if (conj) x = cconj(x);
-        gs = cscale(cmul(x, es), ws);
-      }
-      sc = chan_scale(bmax, b0 + c, sfac);
-    }
-    put(out, 2 * c, NN, (gn.x + gs.x) * sc, x3);
-    put(out, 2 * c + 1, NN, (gn.y + gs.y) * sc, x3);
-    put(out, C2N + 2 * c, NN, (gn.x - gs.x) * sc, x3);
-    put(out, C2N + 2 * c + 1, NN, (gn.y - gs.y) * sc, x3);
+  __syncthreads();
+  // local row rr: part rr / (2 kPackC) (S hi, A hi, S lo, A lo) at operand
+  // row (A: + C2N) (lo: + NN) + 2 c0 + rr % (2 kPackC)
+  for (int q = threadIdx.x; q < kPackM * rows * 8; q += blockDim.x) {
+    const int ml = q / (rows * 8), rr = (q >> 3) % rows, ch = q & 7;
+    const int m = m0 + ml;
+    if (m > mmax) continue;
+    const int part = rr / (2 * kPackC);
+    const int grow = ((part & 1) ? C2N : 0) + ((part & 2) ? NN : 0) + 2 * c0 + rr % (2 * kPackC);
+    const uint4 val = *reinterpret_cast<const uint4*>(smem_raw + ml * slab + rr * 128 + ch * 16);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(gt) +
+                              (((long long)m * ngroup + g) * rb + grow) * 128 + ch * 16) = val;
   }
 }
 
@@ -503,6 +538,17 @@ struct TcShape {
 
 constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, warp 5 issues products
 
+// Synthesis CTAs of the 16-bit modes take kMq consecutive m of one pair tile:
+// each finished m's outputs wait in spare tensor-memory columns, so that the
+// epilogue writes every ring's kMq values of F (m fastest) as one piece --
+// whole 32-byte sectors at kMq = 4 -- instead of one 8-byte value per CTA.
+// kMq NN staging columns fit beside the accumulators within the allocation.
+template <int NN, bool SYN, int MODE>
+__host__ __device__ constexpr int tc_mq() {
+  return (SYN && MODE != 0) ? (NN == 32 ? 4 : 2) : 1;
+}
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : 2 * pow2_at_least((x + 1) / 2); }
+
 struct TcArgs {
   const long long* off;     // analysis: row table offsets [m][group]; synthesis: column table [m][p tile]
   const int* lstart;        // first l stored, same indexing
@@ -519,7 +565,7 @@ struct TcArgs {
   double mfac;
   uint32_t fmt;             // 16-bit modes: operand format of kind::f16 (0 FP16, 1 BF16)
   int* status;
-  int m0;                   // first m of the launch (blockIdx.y = m - m0)
+  int m0, nm;               // the launch's m range (analysis: blockIdx.y = m - m0)
   long long tbase;          // table element at row 0 of the lambda descriptor (streamed blocks)
 };
 
@@ -559,9 +605,15 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   constexpr int NS = S::kNStage, C2N = NN / 2, KW = MODE == 0 ? 32 : 64;
   constexpr int RB = MODE == 2 ? 2 * NN : NN;  // operand rows per K block in memory
   constexpr int NSUM = SYN ? NN : C2N;
+  constexpr int MQ = tc_mq<NN, SYN, MODE>();
+  constexpr int kStageCol = S::kTmemCols;  // first staging column (MQ > 1)
+  constexpr int kAlloc = MQ > 1 ? pow2_at_least(S::kTmemCols + MQ * NN) : S::kTmemCols;
+  static_assert(kAlloc <= (S::kCtas == 2 ? 256 : 512), "tensor memory");
   static_assert(NN % 32 == 0 && NN <= (MODE == 0 || SYN ? 128 : 256), "N tile");
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int m = a.m0 + blockIdx.y;
+  // analysis: m; synthesis: the first of the CTA's nq consecutive m
+  const int m = a.m0 + blockIdx.y * MQ;
+  const int nq = SYN ? min(MQ, a.m0 + a.nm - m) : 1;
   const int l0 = m + kTcTile * blockIdx.x;  // analysis tile
   if (!SYN && l0 > a.lmax) return;          // whole CTA, before any shared state
 
@@ -579,6 +631,9 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   int* wcount = reinterpret_cast<int*>(tmem_slot + 2);  // [4]
   int* rowA = wcount + 4;   // analysis: [128] TMA row of the lambda tile of active group k
   int* rowB = rowA + 128;   // analysis: [128] TMA row of its operand tile
+  int* qna = rowB + 128;    // synthesis: [MQ] blocks, first lambda row, first operand row of each m
+  int* qra = qna + 4;
+  int* qrb = qra + 4;
   auto sL = [&](int s) { return tiles + (size_t)s * S::kStage; };
   auto sB = [&](int s) { return tiles + (size_t)s * S::kStage + (MODE == 2 ? 2 : 1) * S::kA; };
   auto sBlo = [&](int s) { return tiles + (size_t)s * S::kStage + (MODE == 2 ? 2 : 1) * S::kA + S::kG; };
@@ -588,7 +643,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(S::kTmemCols));
+                 "r"(kAlloc));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // K blocks.  Analysis: groups whose rows reach this tile (group starts lie
@@ -609,15 +664,22 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) wcount[warp] = __popc(bal);
   }
-  int na = 0, ra0 = 0, rb0 = 0;  // synthesis: block count, first rows
-  if (SYN) {
-    const long long mT = (long long)m * a.ngroup + blockIdx.x;
-    const int ls = a.lstart[mT];
-    if (ls <= a.lmax) {
-      na = (a.lmax - ls) / KW + 1;
-      ra0 = (int)((a.off[mT] - a.tbase) / KW);
-      rb0 = (int)((a.achunk[m] + (ls - m) / KW) * RB);
+  int na = 0;  // K blocks of the CTA
+  if (SYN && warp == 1 && lane < MQ) {  // synthesis: per m of the CTA, its block count and first rows
+    int n = 0, ra = 0, rb = 0;
+    if (lane < nq) {
+      const int mj = m + lane;
+      const long long mT = (long long)mj * a.ngroup + blockIdx.x;
+      const int ls = a.lstart[mT];
+      if (ls <= a.lmax) {
+        n = (a.lmax - ls) / KW + 1;
+        ra = (int)((a.off[mT] - a.tbase) / KW);
+        rb = (int)((a.achunk[mj] + (ls - mj) / KW) * RB);
+      }
     }
+    qna[lane] = n;
+    qra[lane] = ra;
+    qrb[lane] = rb;
   }
   if (t == 32) {
     for (int s = 0; s < NS; ++s) {
@@ -645,6 +707,8 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       rowB[k] = rb;
     }
     na = wcount[0] + wcount[1] + wcount[2] + wcount[3];
+  } else {
+    for (int j = 0; j < MQ; ++j) na += qna[j];
   }
   const uint32_t tmem = *tmem_slot;
   __syncthreads();
@@ -654,10 +718,17 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     int issued = 0;
     if (lane == 0) {
       constexpr uint32_t kBytes = MODE == 2 ? 2 * (S::kA + S::kG) : S::kA + S::kG;
+      int j = 0, kj = 0;  // synthesis: m of the CTA and block within it
       for (int k = 0; k < na; ++k) {
         const int s = k % NS;
         if (k >= NS && !wait_phase(&empty[s], (uint32_t)(k / NS - 1) & 1u, abort_flag, true)) break;
-        const int r_a = SYN ? ra0 + k * 128 : rowA[k], r_b = SYN ? rb0 + k * RB : rowB[k];
+        if (SYN)
+          while (kj >= qna[j]) {
+            kj = 0;
+            ++j;
+          }
+        const int r_a = SYN ? qra[j] + kj * 128 : rowA[k], r_b = SYN ? qrb[j] + kj * RB : rowB[k];
+        ++kj;
         mbar_expect_tx(&full[s], kBytes);
         tma_load_2d(sL(s), &tmA, 0, r_a, &full[s]);
         tma_load_2d(sB(s), &tmB, 0, r_b, &full[s]);
@@ -753,6 +824,41 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       }
     };
+    // synthesis with several m per CTA (MQ > 1): when all blocks of the next
+    // m are drained, its outputs go to staging columns and the sums restart
+    int jn = 0, jend = 0;  // next m to finish; blocks before it
+    auto finish = [&]() {  // warp-collective
+      if constexpr (MQ > 1) {
+#pragma unroll
+        for (int g = 0; g < NN / 32; ++g) {  // 8 channels: north re, im, south re, im each
+          uint32_t v[32];
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const int c = 8 * g + cc;
+            const float inv = a.lscale / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
+            const float er = sum[2 * c] * inv, ei = sum[2 * c + 1] * inv;
+            const float orr = sum[C2N + 2 * c] * inv, oi = sum[C2N + 2 * c + 1] * inv;
+            v[4 * cc] = __float_as_uint(er + orr);
+            v[4 * cc + 1] = __float_as_uint(ei + oi);
+            v[4 * cc + 2] = __float_as_uint(er - orr);
+            v[4 * cc + 3] = __float_as_uint(ei - oi);
+          }
+          tmem_st32(trow + (uint32_t)(kStageCol + jn * NN + 32 * g), v);
+        }
+#pragma unroll
+        for (int j = 0; j < NSUM; ++j) sum[j] = 0.f;
+        ++jn;
+      }
+    };
+    auto advance = [&](int drained) {  // `drained` blocks of the CTA are in the sums
+      if constexpr (MQ > 1) {
+        while (jn < MQ && jend + qna[jn] <= drained) {
+          jend += qna[jn];
+          finish();
+        }
+      }
+    };
+    advance(0);  // leading m without blocks
     bool alive = true;
     for (int k = 0; k < na; ++k) {
       const int s = k % NS, b = k & 1;
@@ -804,6 +910,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         } else {
           alive = false;
         }
+        advance(k);
       }
     }
     if (na > 0) {  // the last block
@@ -814,13 +921,51 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         drain((na - 1) & 1);
       }
     }
+    advance(na);
     __syncwarp();
     // the CTA-wide sync below orders these writes after every role finished;
     // results are written only if no wait expired anywhere in the CTA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (*abort_flag == 0) {
-      if constexpr (SYN) {
+      if constexpr (SYN && MQ > 1) {
+        // the staged outputs of the CTA's nq m, 4 channels (16 columns) at a
+        // time; per ring and channel the nq values are adjacent in F
+        const int p = blockIdx.x * 128 + t;
+        const int ys = p == a.npair - 1 ? -1 : a.nring - 1 - p;
+        float2* F = reinterpret_cast<float2*>(a.out);
+        const long long mstride = a.mmax + 1;
+#pragma unroll
+        for (int cg = 0; cg < NN / 16; ++cg) {
+          uint32_t v[MQ][16];
+#pragma unroll
+          for (int j = 0; j < MQ; ++j) tmem_ld16(trow + (uint32_t)(kStageCol + j * NN + 16 * cg), v[j]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = 4 * cg + cc;
+            if (p < a.npair && c < a.nb) {
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const int y = side ? ys : p;
+                if (y < 0) continue;
+                const long long at = ((long long)(a.b0 + c) * a.nring + y) * mstride + m;
+                float2 w[MQ];
+#pragma unroll
+                for (int j = 0; j < MQ; ++j)
+                  w[j] = make_float2(__uint_as_float(v[j][4 * cc + 2 * side]), __uint_as_float(v[j][4 * cc + 2 * side + 1]));
+                if (nq == MQ && (at % MQ) == 0) {  // whole pieces: 16 or 32 bytes
+                  float4* d = reinterpret_cast<float4*>(F + at);
+#pragma unroll
+                  for (int h = 0; h < MQ / 2; ++h) d[h] = make_float4(w[2 * h].x, w[2 * h].y, w[2 * h + 1].x, w[2 * h + 1].y);
+                } else {
+                  for (int j = 0; j < nq; ++j) F[at + j] = w[j];
+                }
+              }
+            }
+          }
+        }
+      } else if constexpr (SYN) {
         // north ring p: E + O; its mirror (none for the equator): E - O
         const int p = blockIdx.x * 128 + t;
         if (p < a.npair) {
@@ -855,7 +1000,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (*abort_flag != 0 && t == 0) atomicExch(a.status, (int)HPX_ERR_TIMEOUT);
     __syncthreads();
     if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAlloc));
     return;
   }
   // warps 4 and 5: meet the split/drain warps at their two CTA-wide syncs
@@ -916,6 +1061,7 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.fmt = (uint32_t)p->tc_fmt;
   a.status = p->d_status;
   a.m0 = 0;
+  a.nm = p->mmax + 1;
   a.tbase = 0;
   return a;
 }
@@ -931,10 +1077,14 @@ struct TileRange {
 
 template <int CP, typename E>
 cudaError_t pack_gt_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStream_t s) {
-  constexpr int KW = Elt<E>::kw;
-  k_pack_gt<CP, E><<<dim3((p->ngroup + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
+  static_assert(CP % kPackC == 0, "channel blocks");  // CP >= 8
+  const bool x3 = p->tc_mode == 2;
+  const size_t smem = (size_t)kPackM * pack_slab(pack_rows(x3)) + kPackC * sizeof(float);
+  cudaError_t e = allow_max_smem(k_pack_gt<E>);
+  if (e != cudaSuccess) return e;
+  k_pack_gt<E><<<dim3(p->ngroup, (p->mmax + kPackM) / kPackM, CP / kPackC), 256, smem, s>>>(
       (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (E*)p->d_gt, p->npair, p->nring, p->ngroup,
-      p->nspec, b0, nb, use_w ? 1 : 0, p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_a);
+      p->nspec, p->mmax, 4 * CP, b0, nb, use_w ? 1 : 0, x3 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_a);
   return cudaGetLastError();
 }
 
@@ -955,9 +1105,11 @@ cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac
   cudaError_t e = allow_max_smem(k_legendre_tc<NN, SYN, MODE>);
   if (e != cudaSuccess) return e;
   const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_at : p->tm_gt);
-  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, r.nm);
+  constexpr int MQ = tc_mq<NN, SYN, MODE>();
+  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, (r.nm + MQ - 1) / MQ);
   TcArgs a = tc_args(p, SYN, out, b0, nb, mfac);
   a.m0 = r.m0;
+  a.nm = r.nm;
   a.tbase = r.tbase;
   k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, MODE>::kSmem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(r.tmA), *reinterpret_cast<const CUtensorMap*>(r.tmAlo), *tmB, a);
