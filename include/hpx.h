@@ -31,9 +31,13 @@
  * Pointers must be 16-byte aligned; map and alm must not overlap.
  *
  * Calls are asynchronous and ordered on the stream passed in (NULL = the
- * legacy default stream).  A plan owns device workspace, so one plan serves
- * one call at a time: calls on one plan from different streams must be
- * ordered by the caller, or use one plan per stream.
+ * legacy default stream).  A plan owns device workspace: one part for its
+ * analyses (hpx_map2alm, hpx_alm2map_adjoint) and one for its syntheses
+ * (hpx_alm2map, hpx_map2alm_adjoint).  So one analysis and one synthesis
+ * may run at the same time on two streams (issued from one host thread);
+ * two analyses, two syntheses, the host-buffer calls, hpx_map2alm_iter and
+ * every call on an out-of-core plan must be ordered by the caller, or use
+ * one plan per stream.
  *
  * Errors: every call returns an hpx_status; on failure hpx_last_error()
  * returns a message for the calling thread.  No exception crosses the ABI.

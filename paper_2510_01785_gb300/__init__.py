@@ -51,7 +51,8 @@ def _stream_handle(stream, device) -> int:
 
 class Plan:
     """A transform setup: ring geometry, recurrence tables and workspace on
-    one GPU.  One plan serves one call at a time (its workspace); use one
+    one GPU.  One analysis and one synthesis may run at once on two streams;
+    otherwise one plan serves one call at a time (its workspace); use one
     plan per concurrently used stream."""
 
     def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,

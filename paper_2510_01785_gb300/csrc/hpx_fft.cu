@@ -112,11 +112,14 @@ template <int R, int Q, bool INV, typename V>
 __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw,
                                               const V* __restrict__ pre = nullptr) {
   const int nb = (1 << logm) / R;
-  V v[Q][R];
+  V v[Q][R], wq[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = threadIdx.x + q * blockDim.x;
     if (j < nb) {
+      // the butterfly's twiddle W^k, k = j mod Ns (k / (Ns R) < 1/2: inside
+      // the stored half of the table), fetched before the barrier
+      if (Ns > 1) wq[q] = tw[(j & (Ns - 1)) << (logtw - __ffs(Ns * R) + 1)];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         v[q][r] = buf[pad8(j + r * nb)];
@@ -131,8 +134,7 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
     if (j < nb) {
       const int k = j & (Ns - 1);
       if (Ns > 1) {
-        // k / (Ns R) < 1/2: inside the stored half of the table
-        V w = tw[k << (logtw - __ffs(Ns * R) + 1)];
+        V w = wq[q];
         if (INV) w.y = -w.y;
         V wr = w;
 #pragma unroll

@@ -176,3 +176,30 @@ def test_cfg2_tensor_core_sampled():
     ls, mm = np.array(ls, np.int32), np.array(mm, np.int32)
     ref = oracle.analysis_sep(maps.astype(np.float64), L2, ls, mm, weights="equal")
     assert rel_err(a[:, oracle.alm_index(L2, ls, mm)], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kw", [dict(lambda_table=True, tensor_cores=True), dict(lambda_table=True, tensor_cores=True,
+                                                                              tf32x3=True), {}],
+                         ids=["fp16-split", "tf32x3", "cuda-cores"])
+def test_analysis_and_synthesis_on_two_streams(kw):
+    """One analysis and one synthesis of a plan running at the same time on
+    two streams (their workspaces are apart) give the results of the same
+    calls in sequence, bit for bit."""
+    nside, lmax, nb = 64, 191, 8
+    maps = torch.from_numpy(syn.white_maps(95, nside, nb).astype(np.float32)).cuda()
+    alm = torch.from_numpy(syn.gaussian_alm(96, lmax, lmax, nb).astype(np.complex64)).cuda()
+    with hpx().Plan(nside, lmax, lmax, nb, "f32", **kw) as p:
+        ra, rm = p.map2alm(maps).clone(), p.alm2map(alm).clone()
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        main = torch.cuda.current_stream()
+        oa, om = p.empty_alm(), p.empty_map()
+        for _ in range(3):
+            sa.wait_stream(main)
+            sb.wait_stream(main)
+            p.map2alm(maps, out=oa, stream=sa)
+            p.alm2map(alm, out=om, stream=sb)
+            main.wait_stream(sa)
+            main.wait_stream(sb)
+            torch.cuda.synchronize()
+            assert torch.equal(oa, ra) and torch.equal(om, rm)
+        p.device_status()
