@@ -13,13 +13,15 @@
 // length 4 nside) and cap rings are launched separately, each launch with the
 // shared memory its longest transform needs.
 //
-// The power-of-two FFT is a Stockham (self-sorting) transform: radix-8
-// passes, then one radix-4 or radix-2 pass if log2 M is not a multiple of 3,
+// The power-of-two FFT is a Stockham (self-sorting) transform: radix-16
+// passes, then one radix-8, -4 or -2 pass if log2 M is not a multiple of 4,
 // natural order in and out.  Each pass reads its butterflies' inputs into
-// registers, synchronises, and writes the outputs; shared-memory element i
-// lives at i + i/8, which keeps every pass's scattered writes free of bank
-// conflicts.  One twiddle per butterfly comes from the table; its powers are
-// formed by multiplication.
+// registers, synchronises, and writes the outputs.  Shared-memory element i
+// lives at i XOR ((i / 16) mod 16) -- each 128-byte row of 16 elements
+// permuted by its row number -- so that reads along i and the passes' writes
+// at power-of-two strides spread over all banks.  One twiddle per butterfly
+// comes from the table; its powers are formed by multiplication, at most four
+// deep.
 //
 // Chirp and phase angles pi r / N are reduced exactly in integers before the
 // FP64 sincospi that fills the tables.
@@ -31,9 +33,10 @@ __device__ __forceinline__ int brev(int k, int logm) {
   return (int)(__brev((unsigned)k) >> (32 - logm));
 }
 
-// shared-memory position of FFT element i
-__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
-__host__ __device__ inline size_t padded_len(size_t n) { return n + n / 8 + 1; }
+// shared-memory position of FFT element i (a permutation within each row of
+// 16 elements)
+__device__ __forceinline__ int spos(int i) { return i ^ ((i >> 4) & 15); }
+__host__ __device__ inline size_t padded_len(size_t n) { return n + 16; }  // one more row: the c2r fold writes element n
 
 // Radix-2 decimation in frequency (natural order in, bit-reversed order out),
 // used once per plan to transform the Bluestein kernels in FP64.
@@ -61,9 +64,9 @@ template <bool INV, typename V> __device__ __forceinline__ V rot90(V x) {
   return INV ? cmk<V>(-x.y, x.x) : cmk<V>(x.y, -x.x);
 }
 
-// In-register DFT of length R in {2, 4, 8} (decimation in frequency: radix-2
-// splits down to length 2), sign -1 (forward) or +1 (INV).  Natural order in
-// and out.
+// In-register DFT of length R in {2, 4, 8, 16} (8: decimation in frequency
+// down to length 2; 16: two levels of length 4), sign -1 (forward) or +1
+// (INV).  Natural order in and out.
 template <int R, bool INV, typename V>
 __device__ __forceinline__ void dft_small(V (&v)[R]) {
   using T = decltype(V::x);
@@ -78,6 +81,36 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
     v[2] = csub(u0, u1);
     v[1] = cadd(w0, w1);
     v[3] = csub(w0, w1);
+  } else if constexpr (R == 16) {
+    // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], times W16^(n2 k1), DFT4
+    // over n2; output k1 + 4 k2
+    const T h = (T)0.70710678118654752440, c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+    V y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+      dft_small<4, INV>(y[n2]);
+    }
+    // W16^e = (cos, -+sin)(pi e / 8) for e = n2 k1 in {1, 2, 3, 4, 6, 9}
+    auto tw16 = [&](V x, T c, T s) { return INV ? cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c)
+                                               : cmk<V>(x.x * c + x.y * s, x.y * c - x.x * s); };
+    y[1][1] = tw16(y[1][1], c1, s1);
+    y[1][2] = tw16(y[1][2], h, h);
+    y[1][3] = tw16(y[1][3], s1, c1);
+    y[2][1] = tw16(y[2][1], h, h);
+    y[2][2] = rot90<INV>(y[2][2]);
+    y[2][3] = tw16(y[2][3], -h, h);
+    y[3][1] = tw16(y[3][1], s1, c1);
+    y[3][2] = tw16(y[3][2], -h, h);
+    y[3][3] = tw16(y[3][3], -c1, -s1);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      V z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      dft_small<4, INV>(z);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
   } else {
     const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
     V u[4], w[4];
@@ -103,7 +136,7 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
 }
 
 // One Stockham pass of radix R over a length-2^logm transform in shared memory
-// (positions pad8): butterfly j (j < M/R) takes elements j + r M/R, multiplies
+// (positions spos): butterfly j (j < M/R) takes elements j + r M/R, multiplies
 // element r by W^(k r) with W = exp(-+ 2 pi i / (Ns R)), k = j mod Ns, does the
 // length-R DFT and writes element r to (j - k) R + k + r Ns.  Each thread
 // handles butterflies threadIdx.x + q blockDim.x, q < Q (blockDim.x * Q * R
@@ -122,7 +155,7 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
       if (Ns > 1) wq[q] = tw[(j & (Ns - 1)) << (logtw - __ffs(Ns * R) + 1)];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        v[q][r] = buf[pad8(j + r * nb)];
+        v[q][r] = buf[spos(j + r * nb)];
         if (pre) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
       }
     }
@@ -136,39 +169,54 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
       if (Ns > 1) {
         V w = wq[q];
         if (INV) w.y = -w.y;
-        V wr = w;
+        if constexpr (R == 16) {  // w^r from w, w^2, w^4, w^8: at most four products deep
+          const V w2 = cmul(w, w), w4 = cmul(w2, w2), w8 = cmul(w4, w4);
+          const V w3 = cmul(w2, w), w5 = cmul(w4, w), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+          const V p[8] = {cmk<V>(1, 0), w, w2, w3, w4, w5, w6, w7};
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          v[q][r] = cmul(v[q][r], wr);
-          if (r + 1 < R) wr = cmul(wr, w);
+          for (int r = 1; r < 8; ++r) {
+            v[q][r] = cmul(v[q][r], p[r]);
+            v[q][r + 8] = cmul(v[q][r + 8], cmul(w8, p[r]));
+          }
+          v[q][8] = cmul(v[q][8], w8);
+        } else {
+          V wr = w;
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            v[q][r] = cmul(v[q][r], wr);
+            if (r + 1 < R) wr = cmul(wr, w);
+          }
         }
       }
       dft_small<R, INV>(v[q]);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad8(base + r * Ns)] = v[q][r];
+      for (int r = 0; r < R; ++r) buf[spos(base + r * Ns)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-// Length-2^logm FFT of buf (positions pad8), natural order in and out; needs
+// Length-2^logm FFT of buf (positions spos), natural order in and out; needs
 // blockDim.x * 16 >= 2^logm.  Caller has synchronised after filling buf.
-// The radix-2 or radix-4 pass comes last: there Ns R = 2^logm, so its writes
-// are contiguous (as a first pass, with Ns = 1, they would conflict).
+// The radix-2, -4 or -8 pass comes last: there Ns R = 2^logm, so its writes
+// are contiguous.
 // `pre`, if given, multiplies the input pointwise as the first pass reads it.
 template <bool INV, typename V>
 __device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, const V* __restrict__ pre = nullptr) {
   int Ns = 1;
-  for (int rest = logm; rest >= 3; rest -= 3) {
-    stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
-    Ns <<= 3;
+  for (int rest = logm; rest >= 4; rest -= 4) {
+    stockham_pass<16, 1, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
+    Ns <<= 4;
   }
-  if (logm % 3 == 1) stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
-  else if (logm % 3 == 2) stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
+  switch (logm & 3) {
+    case 1: stockham_pass<2, 8, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr); break;
+    case 2: stockham_pass<4, 4, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr); break;
+    case 3: stockham_pass<8, 2, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr); break;
+  }
 }
 
-// DFT of length H of buf[0..H) (positions pad8) in place, natural order: the
+// DFT of length H of buf[0..H) (positions spos) in place, natural order: the
 // power-of-two FFT when H = 2^logm; otherwise Bluestein's convolution with the
 // kernel spectrum Bk (length 2^logm, natural order, scaled 1/2^logm), where
 // the caller has already multiplied buf[n] by the chirp C[n] = exp(-pi i n^2 /
@@ -217,7 +265,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   const V* x2 = reinterpret_cast<const V*>(map + (long long)b * npix + R.start);
   const int M = blue ? 1 << logm : H;
   for (int n = threadIdx.x; n < M; n += blockDim.x)
-    buf[pad8(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
+    buf[spos(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
   __syncthreads();
   ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
@@ -226,8 +274,8 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   for (int k = threadIdx.x; k <= H; k += blockDim.x) {
     const int k1 = (k == H) ? 0 : k;
     const int k2 = (k == 0) ? 0 : H - k;
-    const V zk = blue ? cmul(buf[pad8(k1)], C[k1]) : buf[pad8(k1)];
-    const V zc = cconj(blue ? cmul(buf[pad8(k2)], C[k2]) : buf[pad8(k2)]);
+    const V zk = blue ? cmul(buf[spos(k1)], C[k1]) : buf[spos(k1)];
+    const V zc = cconj(blue ? cmul(buf[spos(k2)], C[k2]) : buf[spos(k2)]);
     const V e = cscale(cadd(zk, zc), (T)0.5);
     const V d = cscale(csub(zk, zc), (T)0.5);
     const V o = cmk<V>(d.y, -d.x);
@@ -287,14 +335,14 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
       }
-      if (lane == 0) buf[pad8(k)] = acc;
+      if (lane == 0) buf[spos(k)] = acc;
     }
   } else {
     for (int k = threadIdx.x; k <= H; k += blockDim.x) {
       V acc = cmk<V>(0, 0);
       for (int m = k; m <= mmax; m += N) acc = cadd(acc, term(m));
       for (int m = N - k; m <= mmax; m += N) acc = cadd(acc, cconj(term(m)));
-      buf[pad8(k)] = acc;
+      buf[spos(k)] = acc;
     }
   }
   __syncthreads();
@@ -304,7 +352,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   // zero-padded to 2^logm) is stored.
   for (int k = threadIdx.x; k <= H / 2; k += blockDim.x) {
     const int kc = H - k;
-    const V dk = buf[pad8(k)], dc = buf[pad8(kc)];
+    const V dk = buf[spos(k)], dc = buf[spos(kc)];
     const V s1 = cadd(dk, cconj(dc)), d1 = csub(dk, cconj(dc));
     const V t1 = cmul(cconj(E[2 * k]), d1);
     const V zk = cmk<V>(s1.x - t1.y, s1.y + t1.x);
@@ -312,20 +360,20 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
       const V s2 = cadd(dc, cconj(dk)), d2 = csub(dc, cconj(dk));
       const V t2 = cmul(cconj(E[2 * kc]), d2);
       const V zc = cmk<V>(s2.x - t2.y, -(s2.y + t2.x));
-      buf[pad8(kc)] = blue ? cmul(zc, C[kc]) : zc;
+      buf[spos(kc)] = blue ? cmul(zc, C[kc]) : zc;
     }
-    buf[pad8(k)] = blue ? cmul(cconj(zk), C[k]) : cconj(zk);
+    buf[spos(k)] = blue ? cmul(cconj(zk), C[k]) : cconj(zk);
   }
   // zero padding; position H (read above as D[H] for k = 0) is cleared by
   // thread 0 after its own read
   if (blue)
-    for (int n = H + threadIdx.x; n < (1 << logm); n += blockDim.x) buf[pad8(n)] = cmk<V>(0, 0);
+    for (int n = H + threadIdx.x; n < (1 << logm); n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
   __syncthreads();
   ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   const T sc = scale_by_weight ? (T)R.w : (T)1;
   V* out = reinterpret_cast<V*>(map + (long long)b * npix + R.start);
   for (int n = threadIdx.x; n < H; n += blockDim.x) {
-    const V r = blue ? cmul(buf[pad8(n)], C[n]) : buf[pad8(n)];
+    const V r = blue ? cmul(buf[spos(n)], C[n]) : buf[spos(n)];
     out[n] = cmk<V>(r.x * sc, -r.y * sc);
   }
 }
