@@ -227,7 +227,14 @@ __global__ void k_absmax(const float2* __restrict__ x, long long n, long long st
   const int b = b0 + blockIdx.y;
   const float2* xb = x + (long long)b * stride;
   float v = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long step = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * step < n; i += 4 * step) {  // four loads in flight
+    const float2 q0 = xb[i], q1 = xb[i + step], q2 = xb[i + 2 * step], q3 = xb[i + 3 * step];
+    v = fmaxf(v, fmaxf(fmaxf(fabsf(q0.x), fabsf(q0.y)), fmaxf(fabsf(q1.x), fabsf(q1.y))));
+    v = fmaxf(v, fmaxf(fmaxf(fabsf(q2.x), fabsf(q2.y)), fmaxf(fabsf(q3.x), fabsf(q3.y))));
+  }
+  for (; i < n; i += step) {
     const float2 q = xb[i];
     v = fmaxf(v, fmaxf(fabsf(q.x), fabsf(q.y)));
   }
@@ -297,18 +304,21 @@ k_pack_gt(const float2* __restrict__ spec, const float2* __restrict__ etab, cons
       }
     }
     E* T = reinterpret_cast<E*>(smem_raw + ml * slab) + pl;
-#pragma unroll 2
+    // all the item's spectrum bins first (16 loads in flight), then the operand values
+    float2 xn[kPackC], xs[kPackC];
+#pragma unroll
     for (int cl = 0; cl < kPackC; ++cl) {
-      float2 gn = make_float2(0.f, 0.f), gs = gn;
+      xn[cl] = xs[cl] = make_float2(0.f, 0.f);
       if (act && cl < nch) {
         const float2* X = spec + (long long)(b0 + c0 + cl) * nspec;
-        float2 x = X[on + kk];
-        gn = cmul(conj ? cconj(x) : x, en);
-        if (south) {
-          x = X[os + kk];
-          gs = cmul(conj ? cconj(x) : x, es);
-        }
+        xn[cl] = X[on + kk];
+        if (south) xs[cl] = X[os + kk];
       }
+    }
+#pragma unroll
+    for (int cl = 0; cl < kPackC; ++cl) {
+      const float2 gn = cmul(conj ? cconj(xn[cl]) : xn[cl], en);
+      const float2 gs = cmul(conj ? cconj(xs[cl]) : xs[cl], es);
       const float sc = csc[cl];
       const float v[4] = {(gn.x + gs.x) * sc, (gn.y + gs.y) * sc, (gn.x - gs.x) * sc, (gn.y - gs.y) * sc};
 #pragma unroll
@@ -358,11 +368,11 @@ k_pack_at(const float2* __restrict__ alm, const float* __restrict__ coef_pf, con
   const long long base = alm_base(lmax, m);
   // P_l (FP32) times factors of two (mfac, the channel scale): exact
   const float s = in ? coef_pf[base + l] * (m > 0 ? mfac : 1.f) : 0.f;
-#pragma unroll 4
+#pragma unroll 8
   for (int c = 0; c < CP; ++c) {
     float2 a = make_float2(0.f, 0.f);
+    if (in && c < nb) a = alm[(long long)(b0 + c) * nalm + base + l];
     if (in && c < nb) {
-      a = alm[(long long)(b0 + c) * nalm + base + l];
       const float sc = s * chan_scale(bmax, b0 + c, sfac);
       a = make_float2(sc * a.x, m == 0 ? 0.f : sc * a.y);
     }
