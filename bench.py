@@ -119,9 +119,9 @@ def reduce_max(dist, x: float, device) -> float:
     return float(t.item())
 
 
-def throughput(world: int, steps: int, t_max_ms: float) -> float:
+def throughput(world: int, steps: int, t_max_ms: float, nbatch: int = NBATCH) -> float:
     """channel analysis+synthesis pairs per second, all ranks together."""
-    return world * NBATCH * steps / (t_max_ms / 1e3)
+    return world * nbatch * steps / (t_max_ms / 1e3)
 
 
 # --------------------------------------------------------------------------
@@ -451,7 +451,7 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
     for k, (ms, n) in stages.items():
         if n > 0 or k != "analysis_operand_pack":
             report[k] = {"ms_per_step": ms / args.steps, "ms_per_launch": ms / max(n, 1), "launches": n}
-    return {"t_max": t_max, "value": throughput(world, args.steps, t_max), "stages": report,
+    return {"t_max": t_max, "value": throughput(world, args.steps, t_max, plan.nbatch), "stages": report,
             "clocks": clk, "launches": sum(n for _, n in stages.values())}
 
 

@@ -50,3 +50,13 @@ def test_two_rank_max_timing_and_aggregate_value():
         # all ranks' channels over the slowest rank's time: 2 x 8 x 10 / 0.15 s
         assert v == pytest.approx(2 * 8 * 10 / 0.150)
         assert env == (rank, 2, rank)
+
+
+def test_throughput_counts_the_plans_channels():
+    """pairs/s = ranks x channels x steps / seconds, with the channel count
+    of the plan timed (64 for the mixed-precision workload), not the
+    headline's 8."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.throughput(1, 10, 1000.0) == bench.NBATCH * 10
+    assert bench.throughput(2, 5, 500.0, nbatch=64) == 2 * 64 * 5 / 0.5
