@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run (config 3)")
     ap.add_argument("--no-next", action="store_true", help="skip the reorder / refinement measurements")
     ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core table measurement")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the FP64 Nside-32 and differentiation (Nside 256 / 2048) timings")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-drain", type=float, default=15.0)
@@ -340,6 +342,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         ooc = run_out_of_core(args, dist, dev, world, gpu_index)
 
+    small = None
+    if not args.no_small:
+        plan.close()
+        torch.cuda.empty_cache()
+        small = run_small_configs(dev)
+
     mixed = None
     if not args.no_mixed:
         plan.close()
@@ -372,7 +380,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "stages": stage_report, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
-                "next_rows": next_rows, "out_of_core": ooc,
+                "next_rows": next_rows, "out_of_core": ooc, "other_configs": small,
                 "plan": {"lambda_table_build_s": plan_s, "device_bytes": plan_bytes,
                          "table_bytes": tab_bytes_row, "column_table_bytes": tab_bytes_col,
                          "significant_triples": active, "all_triples": total},
@@ -689,6 +697,76 @@ def run_out_of_core(args, dist, dev, world, gpu_index) -> dict:
 
 
 MIXED_MODES = ("f32", "bf16", "bf16x3", "fp16", "fp16x3")
+
+
+def _event_ms(fn, dev, reps: int, warmup: int = 2) -> float:
+    """Mean milliseconds of fn() over reps calls, CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def run_small_configs(dev) -> dict:
+    """The FP64 round trip at Nside 32 (lmax 95, 1 channel) and the
+    differentiation workloads: loss 1 = sum_l (l+1)^-1 sum_m |a_lm|^2 through
+    map2alm and loss 2 = ||alm2map(a) - t||^2, forward + backward through the
+    autograd functions (lambda recomputed in backward), at Nside 256 / lmax
+    767 / 16 FP32 channels and at Nside 2048 / lmax 6143 / 4 channels."""
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import autograd as hag
+    from paper_2510_01785_gb300 import synthetic as syn
+
+    out = {}
+    with hpx.Plan(32, 95, 95, 1, "f64", device=dev) as p:
+        alm = torch.from_numpy(syn.gaussian_alm(SEED - 1, 95, 95, 1, power=2.0)).to(dev)
+        maps = p.alm2map(alm)
+        am, mm = p.empty_alm(), p.empty_map()
+
+        def pair():
+            p.map2alm(maps, out=am)
+            p.alm2map(alm, out=mm)
+        us = 1e3 * _event_ms(pair, dev, 200, 20)
+        back = p.map2alm(p.alm2map(alm))
+        rt = float(((back - alm).abs().pow(2).sum() / alm.abs().pow(2).sum()).sqrt())
+    out["config1_fp64_nside32"] = {"us_per_map2alm_plus_alm2map": us, "dtype": "f64",
+                                   "round_trip_rel_l2": rt,
+                                   "note": "quadrature error of the grid, not a parity figure"}
+    diff = {}
+    for ns, lmax, nb, reps in ((256, 767, 16, 10), (2048, 6143, 4, 2)):
+        maps = torch.from_numpy(syn.white_maps(SEED - 2, ns, nb).astype(np.float32)).to(dev).requires_grad_(True)
+        alm = torch.from_numpy(syn.gaussian_alm(SEED - 3, lmax, lmax, nb, power=2.0).astype(np.complex64)).to(dev)
+        alm.requires_grad_(True)
+        target = torch.from_numpy(syn.white_maps(SEED - 4, ns, nb).astype(np.float32)).to(dev)
+        ell = torch.from_numpy(np.concatenate([np.arange(m, lmax + 1) for m in range(lmax + 1)])).to(dev)
+        wl = 1.0 / (ell.float() + 1.0)
+
+        def loss1():
+            a = hag.map2alm(maps, lmax)
+            (wl * a.abs().pow(2)).sum().backward()
+
+        def loss2():
+            m = hag.alm2map(alm, ns, lmax)
+            (m - target).pow(2).sum().backward()
+        diff[f"nside{ns}_lmax{lmax}_b{nb}"] = {
+            "loss1_forward_backward_ms": _event_ms(loss1, dev, reps, 1),
+            "loss2_forward_backward_ms": _event_ms(loss2, dev, reps, 1),
+            "dtype": "f32", "lambda": "recomputed by the FP64 recurrence in forward and backward"}
+        del maps, alm, target, ell, wl
+        hpx.clear_plans()
+        torch.cuda.empty_cache()
+    out["config4_differentiation"] = diff
+    return out
 
 
 def run_mixed(args, dist, dev, world, gpu_index) -> dict:

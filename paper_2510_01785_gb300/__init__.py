@@ -368,3 +368,11 @@ def get_plan(nside: int, lmax: int, mmax: int | None, nbatch: int, dtype: str, d
             p = Plan(nside, lmax, mmax, nbatch, dtype, lambda_table, device, tensor_cores)
             _plan_cache[key] = p
     return p
+
+
+def clear_plans() -> None:
+    """Close and forget every cached plan (get_plan, the autograd functions)."""
+    with _plan_lock:
+        for p in _plan_cache.values():
+            p.close()
+        _plan_cache.clear()
