@@ -107,3 +107,55 @@ def test_mixed_deterministic():
             s1 = p.alm2map(a1).clone()
             assert torch.equal(p.map2alm(maps), a1) and torch.equal(p.alm2map(a1), s1)
             p.device_status()
+
+
+NS3, L3, B3 = 1024, 2047, 64
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    """The mixed-precision workload at full size: 64 channels scaled over
+    [1e-2, 1e3], coefficients of variance (l+1)^-3 and white-noise maps (both
+    from the seeded generators; no input comes from the GPU path), and the
+    oracle's values of three channels (the smallest and largest scales and
+    one between) on sampled coefficients and rings."""
+    sc = syn.channel_scales(syn.SEED_BASE + 33, B3)
+    alm = syn.gaussian_alm(syn.SEED_BASE + 34, L3, L3, B3, power=3.0, scales=sc)
+    maps = (syn.white_maps(syn.SEED_BASE + 35, NS3, B3) * sc[:, None]).astype(np.float32).astype(np.float64)
+    alm = alm.astype(np.complex64).astype(np.complex128)
+    chans = [int(np.argmin(sc)), int(np.argmax(sc)), 17]
+    r = syn.rng(79)
+    ms = [0, 1, 2, 127, 128, 1000, 1500, 2046, 2047]
+    ls, mm = [], []
+    for m in ms:
+        cand = sorted(set([m, min(m + 1, L3), min(m + 63, L3), min(m + 64, L3), L3] + list(r.integers(m, L3 + 1, 3))))
+        ls += cand
+        mm += [m] * len(cand)
+    ls, mm = np.array(ls, np.int32), np.array(mm, np.int32)
+    rings = np.array([0, 1, 2, 127, 1023, 2047, 3070, 4 * NS3 - 3, 4 * NS3 - 2], np.int32)
+    ref_a = oracle.analysis_sep(maps[chans], L3, ls, mm, weights="equal")
+    ref_m = oracle.synthesis_sep(alm[chans], NS3, L3, L3, rings)
+    return dict(maps=maps.astype(np.float32), alm=alm.astype(np.complex64), chans=chans, ls=ls, mm=mm,
+                rings=rings, ref_a=ref_a, ref_m=ref_m)
+
+
+@pytest.mark.parametrize("mode", ["f32"] + list(BOUND))
+def test_cfg3_full_size_sampled(mode, cfg3):
+    """Nside 1024, lmax 2047, 64 channels, in the launch configuration the
+    benchmark times: sampled coefficients and rings of three channels against
+    the oracle, each mode within its bound (FP32: 1e-5)."""
+    h = hpx()
+    kw = dict(lambda_table=True, tensor_cores=True) if mode == "f32" else {}
+    with h.Plan(NS3, L3, L3, B3, mode, **kw) as p:
+        a = p.map2alm(torch.from_numpy(cfg3["maps"]).cuda())
+        s = p.alm2map(torch.from_numpy(cfg3["alm"]).cuda())
+        p.device_status()
+        a, s = a.cpu().numpy(), s.cpu().numpy()
+    c = cfg3["chans"]
+    ea = rel_err(a[c][:, oracle.alm_index(L3, cfg3["ls"], cfg3["mm"])], cfg3["ref_a"])
+    g = oracle.ring_geometry(NS3)
+    got = np.concatenate([s[c][:, g["start"][y]: g["start"][y] + g["nphi"][y]] for y in cfg3["rings"]], axis=1)
+    es = rel_err(got, cfg3["ref_m"])
+    bound = 1e-5 if mode == "f32" else BOUND[mode]
+    print(f"cfg3 {mode}: analysis {ea:.3e}, synthesis {es:.3e}")
+    assert ea <= bound and es <= bound, (ea, es)
