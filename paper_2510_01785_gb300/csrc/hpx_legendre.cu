@@ -175,12 +175,13 @@ template <> struct LaneTile<32> { static constexpr int CPL = 8, LPL = 4; };
 
 template <typename T> struct MuStride { static constexpr int v = LB + 16 / (int)sizeof(T); };
 
+// S/A coefficients, mu rows (each warp's partial sums of a block reuse its own
+// 32 rows once it has read them), the double-buffered block partials, c_l
 template <typename T, int CP>
 size_t analysis_smem(int nthr) {
   constexpr int C2N = 2 * CP;
-  const int nwarp = nthr / 32;
-  return sizeof(T) * ((size_t)nthr * 2 * C2N + (size_t)nthr * MuStride<T>::v +
-                      (size_t)nwarp * LB * C2N + 2 * LB * C2N) +
+  static_assert(LB * C2N <= 32 * MuStride<T>::v, "partials fit a warp's mu rows");
+  return sizeof(T) * ((size_t)nthr * 2 * C2N + (size_t)nthr * MuStride<T>::v + 2 * LB * C2N) +
          sizeof(double) * 2 * LB;
 }
 
@@ -228,9 +229,8 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sG = reinterpret_cast<T*>(smem_raw);      // [nthr][2][C2N]  S, A
-  T* sMu = sG + (size_t)nthr * 2 * C2N;        // [nthr][MS]
-  T* sW = sMu + (size_t)nthr * MS;             // [nwarp][LB][C2N]
-  T* sC = sW + (size_t)nwarp * LB * C2N;       // [2][LB][C2N]
+  T* sMu = sG + (size_t)nthr * 2 * C2N;        // [nthr][MS]; warp w's [LB][C2N] partials at row 32 w
+  T* sC = sMu + (size_t)nthr * MS;             // [2][LB][C2N]
   double* sCz = reinterpret_cast<double*>(sC + 2 * LB * C2N);  // [2][LB] c_l of this and the next block
 
   double z = 0.0, s0 = 0.0, s1 = 0.0;
@@ -362,7 +362,9 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
           for (int c = 0; c < CPL; ++c) acc[a][c] = fma(mv[a], odd ? gav[c] : gsv[c], acc[a][c]);
         }
       }
-      T* wp = sW + (size_t)warp * LB * C2N;
+      // this warp's partials over its own mu rows, which only it has read
+      T* wp = sMu + (size_t)(warp * 32) * MS;
+      __syncwarp();
 #pragma unroll
       for (int a = 0; a < LPL; ++a)
 #pragma unroll
@@ -370,7 +372,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
       __syncthreads();
       for (int o = t; o < LB * C2N; o += nthr) {
         T s = (T)0;
-        for (int w = 0; w < nwarp; ++w) s += sW[(size_t)w * LB * C2N + o];
+        for (int w = 0; w < nwarp; ++w) s += sMu[(size_t)(w * 32) * MS + o];
         cpart[o] = s;
       }
     } else {
