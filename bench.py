@@ -790,9 +790,15 @@ def run_mixed(args, dist, dev, world, gpu_index) -> dict:
            "modes": {}}
     ref = None
     maps = None
-    for mode in MIXED_MODES:
-        kw = dict(lambda_table=True, tensor_cores=True) if mode == "f32" else {}
-        plan = hpx.Plan(ns, lmax, lmax, nb, mode, device=dev, **kw)
+    # the FP32 plans: tensor cores with FP16 hi/lo split products (the
+    # reference of the speed-ups and deviations), with 3xTF32, and the
+    # CUDA-core contraction over the FP32 table (plain FP32 arithmetic)
+    fp32 = {"f32": dict(lambda_table=True, tensor_cores=True),
+            "f32-tf32x3": dict(lambda_table=True, tensor_cores=True, tf32x3=True),
+            "f32-cuda-cores": dict(lambda_table=True)}
+    for mode in ["f32", "f32-tf32x3", "f32-cuda-cores"] + [m for m in MIXED_MODES if m != "f32"]:
+        kw = fp32.get(mode, {})
+        plan = hpx.Plan(ns, lmax, lmax, nb, "f32" if mode in fp32 else mode, device=dev, **kw)
         if maps is None:
             maps = plan.alm2map(alm_in)
         a = plan.map2alm(maps)
@@ -815,8 +821,10 @@ def run_mixed(args, dist, dev, world, gpu_index) -> dict:
         plan.close()
         torch.cuda.empty_cache()
     f32 = out["modes"]["f32"]["ms_per_step"]
+    f32cc = out["modes"]["f32-cuda-cores"]["ms_per_step"]
     for mode, r in out["modes"].items():
         r["speedup_vs_f32"] = f32 / r["ms_per_step"]
+        r["speedup_vs_f32_cuda_cores"] = f32cc / r["ms_per_step"]
     return out
 
 
