@@ -37,7 +37,11 @@
  * may run at the same time on two streams (issued from one host thread);
  * two analyses, two syntheses, the host-buffer calls, hpx_map2alm_iter and
  * every call on an out-of-core plan must be ordered by the caller, or use
- * one plan per stream.
+ * one plan per stream.  The device-buffer transforms of a resident plan
+ * (hpx_map2alm, hpx_alm2map, their adjoints, gradients and _n forms)
+ * allocate nothing and never wait on the host, so a stream capture may
+ * record them into a CUDA graph after one call outside the capture; the
+ * replays give the same results.
  *
  * Errors: every call returns an hpx_status; on failure hpx_last_error()
  * returns a message for the calling thread.  No exception crosses the ABI.
