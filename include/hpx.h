@@ -32,9 +32,10 @@
  *
  * Calls are asynchronous and ordered on the stream passed in (NULL = the
  * legacy default stream).  A plan owns device workspace: one part for its
- * analyses (hpx_map2alm, hpx_alm2map_adjoint) and one for its syntheses
- * (hpx_alm2map, hpx_map2alm_adjoint).  So one analysis and one synthesis
- * may run at the same time on two streams (issued from one host thread);
+ * analyses (hpx_map2alm, hpx_alm2map_adjoint, hpx_map2alm_n) and one for
+ * its syntheses (hpx_alm2map, hpx_map2alm_adjoint, hpx_alm2map_n).  So one
+ * analysis and one synthesis may run at the same time on two streams
+ * (issued from one host thread);
  * two analyses, two syntheses, the host-buffer calls, hpx_map2alm_iter and
  * every call on an out-of-core plan must be ordered by the caller, or use
  * one plan per stream.  The device-buffer transforms of a resident plan

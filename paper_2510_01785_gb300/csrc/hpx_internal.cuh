@@ -95,9 +95,10 @@ struct hpx_plan_s {
   void* d_gt;          // analysis operand Gt[m][group][rows][row width] (per transform)
   void* d_at;          // synthesis operand At[chunk][rows][row width] (per transform)
   long long* d_achunk; // [mmax+2] first At chunk of each m
-  unsigned* d_bmax;    // [2][nbatch] 16-bit modes: largest operand component per channel, of the
-                       // analysis (spectra) and of the synthesis (alm), apart so that an analysis
-                       // and a synthesis may run on the plan at the same time
+  unsigned* d_bmax;    // [2][bmax_stride] 16-bit modes: largest operand component per channel, of
+                       // the analysis (spectra) and of the synthesis (alm), apart so that an
+                       // analysis and a synthesis may run on the plan at the same time
+  int bmax_stride;     // the plan's own nbatch (views for fewer channels keep it)
   void* d_stab;        // column lambda table: blocks of 128 pairs x (32 or 64) l
   void* d_stab_lo;     // 16-bit x3: its remainders
   long long* d_stab_off;  // [mmax+1][nptile] first element of each (m, pair tile)

@@ -1056,7 +1056,7 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.ngroup = syn ? p->nptile : p->ngroup;
   a.achunk = p->d_achunk;
   a.coef_pf = p->d_coef_pf;
-  a.bmax = p->tc_mode ? p->d_bmax + (syn ? p->nbatch : 0) : nullptr;
+  a.bmax = p->tc_mode ? p->d_bmax + (syn ? p->bmax_stride : 0) : nullptr;
   a.sfac = syn ? p->tc_sfac_s : p->tc_sfac_a;
   a.lscale = p->tc_mode ? (float)(1.0 / kLamScale) : 1.f;
   a.out = out;
@@ -1104,7 +1104,7 @@ cudaError_t pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, do
   const int nchunk0 = p->lmax / KW + 1;  // chunks of m = 0, the most
   k_pack_at<CP, E><<<dim3((nchunk0 + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
       (const float2*)alm, p->d_coef_pf, p->d_achunk, (E*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, (float)mfac,
-      p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax + p->nbatch : nullptr, p->tc_sfac_s);
+      p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax + p->bmax_stride : nullptr, p->tc_sfac_s);
   return cudaGetLastError();
 }
 
@@ -1220,7 +1220,7 @@ namespace {
 // (the synthesis half of the plan's maxima)
 cudaError_t absmax(hpx_plan_s const* p, const float2* x, long long n, long long stride, int b0, int nb,
                    cudaStream_t s) {
-  unsigned* bm = p->d_bmax + p->nbatch;
+  unsigned* bm = p->d_bmax + p->bmax_stride;
   cudaError_t e = cudaMemsetAsync(bm + b0, 0, sizeof(unsigned) * nb, s);
   if (e != cudaSuccess) return e;
   const long long blocks = (n + 1023) / 1024;  // about four values per thread
@@ -1383,6 +1383,7 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_achunk, ach.data(), sizeof(long long) * (p->mmax + 2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = dalloc(&p->d_at, (size_t)es * ach[p->mmax + 1] * rbs * kw);
+  p->bmax_stride = p->nbatch;
   if (e == cudaSuccess) e = dalloc((void**)&p->d_bmax, 2 * sizeof(unsigned) * p->nbatch);
   if (e != cudaSuccess) return e;
   // column table layout

@@ -203,3 +203,34 @@ def test_analysis_and_synthesis_on_two_streams(kw):
             torch.cuda.synchronize()
             assert torch.equal(oa, ra) and torch.equal(om, rm)
         p.device_status()
+
+
+@pytest.mark.parametrize("kw", [dict(lambda_table=True, tensor_cores=True), {}], ids=["fp16-split", "cuda-cores"])
+def test_n_forms_and_their_concurrency(kw):
+    """The _n forms (the first n channels of the plan's batch, as the server
+    packs them) equal the full calls' first n channels bit for bit (the
+    16-bit operand scales are per channel), and an _n analysis and an _n
+    synthesis with different n may run at once on two streams."""
+    nside, lmax, nb = 64, 191, 8
+    maps = torch.from_numpy(syn.white_maps(97, nside, nb).astype(np.float32)).cuda()
+    alm = torch.from_numpy(syn.gaussian_alm(98, lmax, lmax, nb).astype(np.complex64)).cuda()
+    with hpx().Plan(nside, lmax, lmax, nb, "f32", **kw) as p:
+        fa, fm = p.map2alm(maps).clone(), p.alm2map(alm).clone()
+        a5, m3 = p.empty_alm(), p.empty_map()
+        p.map2alm_n(5, maps, a5)
+        p.alm2map_n(3, alm, m3)
+        torch.cuda.synchronize()
+        assert torch.equal(a5[:5], fa[:5]) and torch.equal(m3[:3], fm[:3])
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        main = torch.cuda.current_stream()
+        a8, m4 = p.empty_alm(), p.empty_map()
+        for _ in range(3):
+            sa.wait_stream(main)
+            sb.wait_stream(main)
+            p.map2alm_n(8, maps, a8, stream=sa)
+            p.alm2map_n(4, alm, m4, stream=sb)
+            main.wait_stream(sa)
+            main.wait_stream(sb)
+            torch.cuda.synchronize()
+            assert torch.equal(a8, fa) and torch.equal(m4[:4], fm[:4])
+        p.device_status()
