@@ -202,10 +202,12 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
 // The radix-2, -4 or -8 pass comes last: there Ns R = 2^logm, so its writes
 // are contiguous.
 // `pre`, if given, multiplies the input pointwise as the first pass reads it.
+// `first` passes are done already (the caller's own first pass).
 template <bool INV, typename V>
-__device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, const V* __restrict__ pre = nullptr) {
-  int Ns = 1;
-  for (int rest = logm; rest >= 4; rest -= 4) {
+__device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, const V* __restrict__ pre = nullptr,
+                         int first = 0) {
+  int Ns = 1 << (4 * first);
+  for (int rest = logm - 4 * first; rest >= 4; rest -= 4) {
     stockham_pass<16, 1, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
     Ns <<= 4;
   }
@@ -264,10 +266,31 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   // zero-padded to 2^logm
   const V* x2 = reinterpret_cast<const V*>(map + (long long)b * npix + R.start);
   const int M = blue ? 1 << logm : H;
-  for (int n = threadIdx.x; n < M; n += blockDim.x)
-    buf[spos(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
-  __syncthreads();
-  ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
+  if (!blue && logm >= 4) {
+    // power-of-two rings: the first radix-16 pass (Ns = 1, no twiddles)
+    // reads the ring straight from HBM -- butterfly j takes elements
+    // j + r H/16, contiguous across the block's threads -- and writes
+    // elements 16 j + r: no separate load loop, one shared-memory round trip
+    // and one barrier fewer (r2c 0.67 -> 0.58 ms at Nside 1024, 8 channels;
+    // the same for the Bluestein rings, or the last pass of c2r written
+    // straight to the map, measured slower)
+    const int nb = H >> 4;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      V v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = x2[j + r * nb];
+      dft_small<16, false>(v);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) buf[spos(16 * j + r)] = v[r];
+    }
+    __syncthreads();
+    fft_pow2<false>(buf, logm, tw, logtw, static_cast<const V*>(nullptr), 1);
+  } else {
+    for (int n = threadIdx.x; n < M; n += blockDim.x)
+      buf[spos(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
+    __syncthreads();
+    ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
+  }
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
   V* out = spec + (long long)b * nspec + R.specoff;
   T amax = 0;  // largest |component| written by this thread
