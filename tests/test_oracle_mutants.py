@@ -1,0 +1,95 @@
+"""Planted mistakes in the oracle fail its pins.
+
+Each case copies oracle.c, plants one plausible mistake in the copy (a
+dropped sign, term, factor or offset), builds it into a temporary library
+beside the test, points the oracle's loader at it and runs the hand-derived
+Nside-1 worked examples of tests/golden/ (pixel centres, Eq. 1 analysis and
+Eq. 2 synthesis in both oracle tiers).  At least one check must fail for
+every mistake, and none for the unmodified copy built the same way.  The
+source snippet of each mistake must occur exactly once, so that a change to
+oracle.c shows up here instead of leaving a case that plants nothing.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import golden_cases as g
+import oracle
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "oracle.c")
+
+MUTANTS = {
+    "condon-shortley sign dropped (Eq. 15)": (
+        "v = snorm(-v.mant * sqrt(", "v = snorm(v.mant * sqrt("),
+    "1/alpha_{l-1} dropped from the recurrence (Eq. 16)": (
+        "(l - 1 > m) ? 1.0 / alpha_lm(l - 1, m) : 0.0", "(l - 1 > m) ? 1.0 : 0.0"),
+    "lambda_mm product (2k-1)/(2k) instead of (2k+1)/(2k) (Eq. 8)": (
+        "sqrt((2.0 * k + 1.0) / (2.0 * k))", "sqrt((2.0 * k - 1.0) / (2.0 * k))"),
+    "belt half-pixel shift parity flipped (Sec. III-A)": (
+        "*sigma = (int)((i - ns + 1) & 1);", "*sigma = (int)((i - ns) & 1);"),
+    "belt z without its factor 2 (Sec. III-A)": (
+        "*z = (double)(2 * (2 * ns - ii)) / (double)(3 * ns);", "*z = (double)(2 * ns - ii) / (double)(3 * ns);"),
+    "ring phase offset phi_0 dropped in the ring DFT (Eq. 13, 26)": (
+        "(m * (2 * (int64_t)x + sigma)) % (2 * (int64_t)n)", "(m * (2 * (int64_t)x)) % (2 * (int64_t)n)"),
+    "conjugation dropped in the ring DFT (Eq. 26)": (
+        "acc_add(&im, -p[x] * cs[2 * r + 1]);", "acc_add(&im, p[x] * cs[2 * r + 1]);"),
+    "factor 2 of the m >= 1 terms dropped in the ring synthesis (Eq. 24)": (
+        "acc_add(&s, 2.0 * (F[2 * m] * cs[2 * r] - F[2 * m + 1] * cs[2 * r + 1]));",
+        "acc_add(&s, (F[2 * m] * cs[2 * r] - F[2 * m + 1] * cs[2 * r + 1]));"),
+    "sign of Im a_lm flipped in the direct synthesis (Eq. 24)": (
+        "(a[0] * c - a[1] * sn)", "(a[0] * c + a[1] * sn)"),
+}
+
+
+def failures():
+    """Names of the worked-example checks the loaded oracle fails."""
+    bad = []
+    px = g.pixels()
+    th, ph = oracle.pixel_angles(g.NSIDE)
+    if np.max(np.abs(np.cos(th) - px[:, 0])) > 1e-15 or np.max(np.abs(ph - px[:, 2])) > 1e-15:
+        bad.append("pixels")
+    ana = g.analysis_cases()
+    maps = np.stack([c[1] for c in ana])
+    ref = np.stack([c[2] for c in ana])
+    syn = g.synthesis_cases()
+    alm = np.stack([c[2] for c in syn])
+    fref = np.stack([c[1] for c in syn])
+    for tier in ("direct", "sep"):
+        if np.max(np.abs(oracle.map2alm(maps, g.LMAX, g.MMAX, tier=tier) - ref)) > 1e-14:
+            bad.append(f"analysis-{tier}")
+        if np.max(np.abs(oracle.alm2map(alm, g.NSIDE, g.LMAX, g.MMAX, tier=tier) - fref)) > 1e-14:
+            bad.append(f"synthesis-{tier}")
+    return bad
+
+
+def _load(monkeypatch, tmp_path, text, tag):
+    src = tmp_path / f"oracle_{tag}.c"
+    src.write_text(text)
+    so = tmp_path / f"liboracle_{tag}.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(so), str(src), "-lm"])
+    monkeypatch.setattr(oracle, "_LIB", str(so))
+    monkeypatch.setattr(oracle, "build", lambda force=False: str(so))
+    monkeypatch.setattr(oracle, "_lib", None)
+
+
+needs_gcc = pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not found")
+
+
+@needs_gcc
+def test_unmodified_copy_passes(monkeypatch, tmp_path):
+    _load(monkeypatch, tmp_path, open(SRC).read(), "control")
+    assert failures() == []
+
+
+@needs_gcc
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, monkeypatch, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"snippet for {name!r} must occur exactly once in oracle.c"
+    _load(monkeypatch, tmp_path, text.replace(old, new), "mutant")
+    assert failures(), f"no worked example catches: {name}"
