@@ -1,15 +1,16 @@
-"""Reader of the hand-derived worked examples under tests/golden/ (Nside 1,
-lmax = mmax = 4): pixel centres, maps with their analysis coefficients
-(Eq. 1) and coefficients with their synthesised maps (Eq. 2).  Expressions
-are evaluated with math's functions only; everything else in a fixture is
-a comment."""
+"""Reader of the hand-derived worked examples under tests/golden/ (Nside 1
+and 2, lmax = mmax = 4): pixel centres, maps with their analysis
+coefficients (Eq. 1) and coefficients with their synthesised maps (Eq. 2).
+Expressions are evaluated with math's functions only; everything else in a
+fixture is a comment."""
 import math
 import os
 
 import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-NSIDE, LMAX, MMAX = 1, 4, 4
+NSIDES = (1, 2)
+NSIDE, LMAX, MMAX = 1, 4, 4  # NSIDE: the default of the functions below
 _NS = {"sqrt": math.sqrt, "pi": math.pi, "cos": math.cos, "sin": math.sin}
 
 
@@ -25,11 +26,19 @@ def _lines(name):
                 yield ln.split()
 
 
-def pixels():
-    """[12, 3]: z, sin(theta), phi of each pixel in RING order."""
-    rows = sorted((int(p), _ev(z), _ev(s), _ev(ph)) for p, z, s, ph in _lines("nside1_pixels.txt"))
-    assert [r[0] for r in rows] == list(range(12 * NSIDE * NSIDE))
-    return np.array([r[1:] for r in rows])
+def pixels(nside=NSIDE):
+    """[12 nside^2, 3]: z, sin(theta), phi of each pixel in RING order, from
+    a per-pixel fixture or from the rings (pixels evenly spaced in phi from
+    phi_0)."""
+    if os.path.exists(os.path.join(GOLDEN, f"nside{nside}_pixels.txt")):
+        rows = sorted((int(p), _ev(z), _ev(s), _ev(ph)) for p, z, s, ph in _lines(f"nside{nside}_pixels.txt"))
+        assert [r[0] for r in rows] == list(range(12 * nside * nside))
+        return np.array([r[1:] for r in rows])
+    rings = sorted((int(i), _ev(z), _ev(s), int(n), _ev(p0)) for i, z, s, n, p0 in _lines(f"nside{nside}_rings.txt"))
+    assert [r[0] for r in rings] == list(range(1, 4 * nside))
+    px = [(z, s, p0 + 2 * math.pi * x / n) for _, z, s, n, p0 in rings for x in range(n)]
+    assert len(px) == 12 * nside * nside
+    return np.array(px)
 
 
 def alm_index(l, m):
@@ -41,7 +50,7 @@ def nalm():
     return (MMAX + 1) * (LMAX + 1) - MMAX * (MMAX + 1) // 2
 
 
-def _cases(name):
+def _cases(name, nside):
     maps, alms, order = {}, {}, []
     for f in _lines(name):
         if f[0] == "map":
@@ -55,7 +64,7 @@ def _cases(name):
                 order.append(f[1])
         else:
             raise ValueError(f"unknown record {f[0]!r} in {name}")
-    px = pixels()
+    px = pixels(nside)
     out = []
     for k in order:
         m = np.array([_ev(maps[k], z=z, s=s, phi=ph) for z, s, ph in px])
@@ -63,11 +72,11 @@ def _cases(name):
     return out
 
 
-def analysis_cases():
-    """[(name, map [12], alm [nalm])]: map in, coefficients out."""
-    return _cases("nside1_analysis.txt")
+def analysis_cases(nside=NSIDE):
+    """[(name, map [12 nside^2], alm [nalm])]: map in, coefficients out."""
+    return _cases(f"nside{nside}_analysis.txt", nside)
 
 
-def synthesis_cases():
-    """[(name, map [12], alm [nalm])]: coefficients in, map out."""
-    return _cases("nside1_synthesis.txt")
+def synthesis_cases(nside=NSIDE):
+    """[(name, map [12 nside^2], alm [nalm])]: coefficients in, map out."""
+    return _cases(f"nside{nside}_synthesis.txt", nside)

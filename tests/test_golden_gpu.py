@@ -1,8 +1,9 @@
-"""The hand-derived Nside-1 worked examples of tests/golden/ through every
-plan kind of the CUDA library: analysis (Eq. 1), synthesis (Eq. 2) and both
-adjoints (Sec. III-F), against the closed forms themselves rather than the
-oracle.  Bars as in the parity tests: relative L2 per channel, FP64 1e-12,
-FP32 (CUDA cores or either tensor-core split scheme) 1e-5."""
+"""The hand-derived Nside-1 and Nside-2 worked examples of tests/golden/
+through every plan kind of the CUDA library: analysis (Eq. 1), synthesis
+(Eq. 2) and both adjoints (Sec. III-F), against the closed forms themselves
+rather than the oracle.  Bars as in the parity tests: relative L2 per
+channel, FP64 1e-12, FP32 (CUDA cores or either tensor-core split scheme)
+1e-5."""
 import numpy as np
 import pytest
 import torch
@@ -27,34 +28,39 @@ def rel_err(got, ref):
     return float(np.max(num / den))
 
 
-@pytest.mark.parametrize("kind", list(KINDS))
-def test_worked_examples_on_gpu(kind):
-    import paper_2510_01785_gb300 as h
-    kw, tol = KINDS[kind]
+def _run(h, nside, kw, ana, syn):
     f64 = kw["dtype"] == "f64"
     rt, ct = (torch.float64, torch.complex128) if f64 else (torch.float32, torch.complex64)
-    ana, syn = g.analysis_cases(), g.synthesis_cases()
     maps = np.stack([c[1] for c in ana])
-    aref = np.stack([c[2] for c in ana])
     alm = np.stack([c[2] for c in syn])
-    fref = np.stack([c[1] for c in syn])
-    nb = len(ana)
-    assert len(syn) == nb
-    with h.Plan(g.NSIDE, g.LMAX, g.MMAX, nb, **kw) as p:
+    out = {}
+    with h.Plan(nside, g.LMAX, g.MMAX, len(ana), **kw) as p:
         dm = torch.from_numpy(maps).to(rt).cuda()
+        out["map2alm"] = p.map2alm(dm)
+        out["alm2map_adjoint"] = p.alm2map_adjoint(dm)
+    with h.Plan(nside, g.LMAX, g.MMAX, len(syn), **kw) as p:
         da = torch.from_numpy(alm).to(ct).cuda()
-        got = {
-            "map2alm": p.map2alm(dm),
-            "alm2map": p.alm2map(da),
-            "alm2map_adjoint": p.alm2map_adjoint(dm),
-            "map2alm_adjoint": p.map2alm_adjoint(da),
-        }
-        torch.cuda.synchronize()
+        out["alm2map"] = p.alm2map(da)
+        out["map2alm_adjoint"] = p.map2alm_adjoint(da)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("nside", g.NSIDES)
+@pytest.mark.parametrize("kind", list(KINDS))
+def test_worked_examples_on_gpu(kind, nside):
+    import paper_2510_01785_gb300 as h
+    kw, tol = KINDS[kind]
+    ana, syn = g.analysis_cases(nside), g.synthesis_cases(nside)
+    aref = np.stack([c[2] for c in ana])
+    fref = np.stack([c[1] for c in syn])
+    w = 4 * np.pi / (12 * nside * nside)
+    got = _run(h, nside, kw, ana, syn)
     ref = {"map2alm": aref, "alm2map": fref,
-           "alm2map_adjoint": aref * 3 / np.pi,      # Y^dagger: unit weights
-           "map2alm_adjoint": fref * np.pi / 3}      # W Y: equal weights 4 pi / 12
+           "alm2map_adjoint": aref / w,     # Y^dagger: unit weights
+           "map2alm_adjoint": fref * w}     # W Y: equal weights 4 pi / Npix
     for op, r in ref.items():
         x = got[op].cpu().numpy().astype(np.complex128 if np.iscomplexobj(r) else np.float64)
         assert x.shape == r.shape, op
         e = rel_err(x, r)
-        assert e <= tol, (kind, op, e)
+        assert e <= tol, (kind, nside, op, e)

@@ -3,8 +3,8 @@
 Each case copies oracle.c, plants one plausible mistake in the copy (a
 dropped sign, term, factor or offset), builds it into a temporary library
 beside the test, points the oracle's loader at it and runs the hand-derived
-Nside-1 worked examples of tests/golden/ (pixel centres, Eq. 1 analysis and
-Eq. 2 synthesis in both oracle tiers).  At least one check must fail for
+Nside-1 and Nside-2 worked examples of tests/golden/ (pixel centres, Eq. 1
+analysis and Eq. 2 synthesis in both oracle tiers).  At least one check must fail for
 every mistake, and none for the unmodified copy built the same way.  The
 source snippet of each mistake must occur exactly once, so that a change to
 oracle.c shows up here instead of leaving a case that plants nothing.
@@ -22,6 +22,10 @@ import oracle
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "oracle.c")
 
 MUTANTS = {
+    "cap ring z with 2 Nside^2 instead of 3 Nside^2 (Sec. III-A)": (
+        "const double den = 3.0 * (double)(ns * ns);", "const double den = 2.0 * (double)(ns * ns);"),
+    "cap ring half-pixel shift dropped (Sec. III-A)": (
+        "    *sigma = 1;\n", "    *sigma = 0;\n"),
     "condon-shortley sign dropped (Eq. 15)": (
         "v = snorm(-v.mant * sqrt(", "v = snorm(v.mant * sqrt("),
     "1/alpha_{l-1} dropped from the recurrence (Eq. 16)": (
@@ -47,21 +51,22 @@ MUTANTS = {
 def failures():
     """Names of the worked-example checks the loaded oracle fails."""
     bad = []
-    px = g.pixels()
-    th, ph = oracle.pixel_angles(g.NSIDE)
-    if np.max(np.abs(np.cos(th) - px[:, 0])) > 1e-15 or np.max(np.abs(ph - px[:, 2])) > 1e-15:
-        bad.append("pixels")
-    ana = g.analysis_cases()
-    maps = np.stack([c[1] for c in ana])
-    ref = np.stack([c[2] for c in ana])
-    syn = g.synthesis_cases()
-    alm = np.stack([c[2] for c in syn])
-    fref = np.stack([c[1] for c in syn])
-    for tier in ("direct", "sep"):
-        if np.max(np.abs(oracle.map2alm(maps, g.LMAX, g.MMAX, tier=tier) - ref)) > 1e-14:
-            bad.append(f"analysis-{tier}")
-        if np.max(np.abs(oracle.alm2map(alm, g.NSIDE, g.LMAX, g.MMAX, tier=tier) - fref)) > 1e-14:
-            bad.append(f"synthesis-{tier}")
+    for nside in g.NSIDES:
+        px = g.pixels(nside)
+        th, ph = oracle.pixel_angles(nside)
+        if np.max(np.abs(np.cos(th) - px[:, 0])) > 1e-15 or np.max(np.abs(ph - px[:, 2])) > 1e-15:
+            bad.append(f"pixels-{nside}")
+        ana = g.analysis_cases(nside)
+        maps = np.stack([c[1] for c in ana])
+        ref = np.stack([c[2] for c in ana])
+        syn = g.synthesis_cases(nside)
+        alm = np.stack([c[2] for c in syn])
+        fref = np.stack([c[1] for c in syn])
+        for tier in ("direct", "sep"):
+            if np.max(np.abs(oracle.map2alm(maps, g.LMAX, g.MMAX, tier=tier) - ref)) > 1e-14:
+                bad.append(f"analysis-{tier}-{nside}")
+            if np.max(np.abs(oracle.alm2map(alm, nside, g.LMAX, g.MMAX, tier=tier) - fref)) > 1e-14:
+                bad.append(f"synthesis-{tier}-{nside}")
     return bad
 
 
