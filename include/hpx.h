@@ -313,8 +313,8 @@ hpx_status hpx_plan_ring_table(hpx_plan plan, int64_t* start, int32_t* nphi,
  * the operand packs of the tensor-core analysis and synthesis
  * (HPX_PLAN_TENSOR_CORES plans only).  hpx_plan_stage_times waits for the
  * recorded events, adds their elapsed times (ms) and kernel launch counts
- * into ms[6] and launches[6] (either may be NULL), and clears the record.  Measurement support, not part of the
- * transform. */
+ * into ms[6] and launches[6] (either may be NULL), and clears the record.
+ * Measurement support, not part of the transform. */
 hpx_status hpx_plan_set_timing(hpx_plan plan, int enable);
 hpx_status hpx_plan_stage_times(hpx_plan plan, double* ms, int64_t* launches);
 
