@@ -130,52 +130,88 @@ def throughput(world: int, steps: int, t_max_ms: float, nbatch: int = NBATCH) ->
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+    """nvidia-smi samples every 50 ms; only those taken between mark_start()
+    and mark_end() (host clock, the same machine as the GPU) count."""
+    FIELDS = ["timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
         self.out = os.path.join("/tmp", f"hpx_clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling and wait (at most 5 s) for the first sample, so the
+        sampler is running when the timed region opens."""
         try:
             self.f = open(self.out, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)], stdout=self.f,
+                stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        deadline = time.time() + 5.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.out) > 0:
+                break
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(2 * self.PERIOD_MS / 1000)  # the sample straddling the end has landed
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.out):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < len(self.FIELDS):
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+        with open(self.out) as f:
+            text = f.read()
         os.unlink(self.out)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return summarize_clocks(text, self.t0, self.t1)
+
+
+def summarize_clocks(text: str, t0=None, t1=None) -> dict:
+    """Median SM clock, max SM clock and the throttle reasons seen, from
+    nvidia-smi CSV lines (FIELDS order).  Samples stamped within [t0, t1]
+    (epoch seconds; 0.05 s slack for the timestamps' rounding) are used; if
+    none is, all samples are, and "in_region" says so."""
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in text.splitlines():
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < len(ClockSampler.FIELDS):
+            continue
+        try:
+            ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+            ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+        except (ValueError, IndexError):
+            ts = None
+        try:
+            sm, smax = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        active = [n for n, v in zip(names, parts[6:10]) if v.lower().startswith("active")]
+        rows.append((ts, sm, smax, active))
+    inside = [r for r in rows if t0 is not None and t1 is not None and r[0] is not None
+              and t0 - 0.05 <= r[0] <= t1 + 0.05]
+    use = inside if inside else rows
+    reasons = sorted({n for r in use for n in r[3]})
+    return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+            "sm_max_mhz": max(r[2] for r in use) if use else None,
+            "samples": len(use), "in_region": bool(inside), "reasons": reasons}
 
 
 # --------------------------------------------------------------------------
@@ -444,11 +480,13 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark_start()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    clocks.mark_end()
     clk = clocks.stop()
     barrier(dist, dev)
     t_ms = e0.elapsed_time(e1)

@@ -1,10 +1,12 @@
-"""Host-side bookkeeping of bench.py's roofline object: the DRAM-traffic
+"""Host-side bookkeeping of bench.py: the roofline object (the DRAM-traffic
 lookup keyed by the CUDA sources' hash, the choice of the dominant Legendre
-kernel, and achieved / peak.  No GPU: the plan is a stand-in that answers
-the few size queries the roofline needs."""
+kernel, achieved / peak) and the clock summary of the timed region.  No GPU:
+the plan is a stand-in that answers the few size queries the roofline needs,
+and the clock samples are written in nvidia-smi's CSV form."""
 import hashlib
 import os
 import sys
+import time
 
 import pytest
 
@@ -127,3 +129,32 @@ def test_cuda_core_table_and_recompute_rooflines(monkeypatch):
     assert r["achieved"] == pytest.approx(3.0 * active / 50e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS)
     assert "hbm_gbs_algorithmic" not in st["legendre_synthesis"]
+
+
+def _smi_line(t, sm, reasons=()):
+    """One nvidia-smi CSV line in the sampler's field order."""
+    stamp = time.strftime("%Y/%m/%d %H:%M:%S", time.localtime(t)) + ".%03d" % int(round((t % 1) * 1000) % 1000)
+    flags = ["Active" if n in reasons else "Not Active"
+             for n in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")]
+    return ", ".join([stamp, "0", str(sm), "2070", "900.00", "0x0"] + flags)
+
+
+def test_clock_summary_keeps_the_timed_region():
+    t0 = 1_900_000_000.0
+    lines = [_smi_line(t0 - 1.0, 1200, ["sw_thermal_slowdown"]),  # before the region
+             _smi_line(t0 + 0.10, 2070), _smi_line(t0 + 0.15, 2055, ["sw_power_cap"]),
+             _smi_line(t0 + 0.20, 2070),
+             _smi_line(t0 + 2.0, 600)]                               # after it (idle)
+    r = bench.summarize_clocks("\n".join(lines), t0, t0 + 0.25)
+    assert r["in_region"] and r["samples"] == 3
+    assert r["sm_mhz"] == 2070 and r["sm_max_mhz"] == 2070
+    assert r["reasons"] == ["sw_power_cap"]  # the thermal flag before the region does not count
+
+
+def test_clock_summary_falls_back_to_all_samples():
+    t0 = 1_900_000_000.0
+    lines = [_smi_line(t0 + 1.0, 2070), _smi_line(t0 + 1.05, 2060, ["hw_slowdown"]), "garbage", ""]
+    r = bench.summarize_clocks("\n".join(lines), t0, t0 + 0.01)
+    assert not r["in_region"] and r["samples"] == 2
+    assert r["sm_mhz"] == 2065 and r["reasons"] == ["hw_slowdown"]
+    assert bench.summarize_clocks("", t0, t0 + 1)["sm_mhz"] is None
