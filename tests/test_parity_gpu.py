@@ -205,6 +205,34 @@ def test_cfg2_adjoint_identity(big):
     assert rel < 1e-6
 
 
+def test_max_size_sampled():
+    """The largest plan: Nside 2048, lmax 6143, 4 FP32 channels, lambda
+    recomputed (its tables would not fit).  Sampled coefficients at the
+    extreme and aliased m (4096 = the belt ring length 8192 / 2) and sampled
+    rings at both poles, the last cap ring and the equator, against tier B."""
+    ns, lm, nb = 2048, 6143, 4
+    maps = syn.white_maps(syn.SEED_BASE + 4, ns, nb).astype(np.float32)
+    alm = syn.gaussian_alm(syn.SEED_BASE + 5, lm, lm, nb, power=2.0).astype(np.complex64)
+    with hpx().Plan(ns, lm, lm, nb, "f32") as p:
+        got_a = p.map2alm(to_dev(maps, "f32")).cpu().numpy()
+        got_s = p.alm2map(to_dev(alm, "f32")).cpu().numpy()
+    ls, mm = [], []
+    r = syn.rng(78)
+    for m in (0, 1, 2047, 4095, 4096, 6142, 6143):
+        cand = sorted(set([m, min(m + 1, lm), lm] + list(r.integers(m, lm + 1, 3))))
+        ls += cand
+        mm += [m] * len(cand)
+    ls, mm = np.array(ls, np.int32), np.array(mm, np.int32)
+    ref = oracle.analysis_sep(maps.astype(np.float64), lm, ls, mm, weights="equal")
+    assert rel_err(got_a[:, oracle.alm_index(lm, ls, mm)], ref) <= 1e-5
+    R = 4 * ns - 1
+    rings = np.array([0, 1, ns - 2, ns - 1, 2 * ns - 1, R - 2, R - 1], np.int32)
+    ref_s = oracle.synthesis_sep(alm.astype(np.complex128), ns, lm, lm, rings)
+    g = oracle.ring_geometry(ns)
+    got = np.concatenate([got_s[:, g["start"][y]: g["start"][y] + g["nphi"][y]] for y in rings], axis=1)
+    assert rel_err(got, ref_s) <= 1e-5
+
+
 def test_cfg2_deterministic_and_stream(big):
     p = big["plan"]
     s = torch.cuda.Stream()
