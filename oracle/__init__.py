@@ -35,12 +35,20 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# Test infrastructure: the planted-mistake tests run the pin suite in a
+# subprocess against a modified build of oracle.c named by this variable.
+_OVERRIDE = os.environ.get("HPX_ORACLE_LIB")
+if _OVERRIDE:
+    _LIB = _OVERRIDE
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` beside it (gcc, OpenMP)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` beside it (gcc, OpenMP);
+    with HPX_ORACLE_LIB set, use that library as it is."""
+    if _OVERRIDE:
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                "-o", _LIB + ".tmp", _SRC, "-lm"]
