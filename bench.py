@@ -217,6 +217,16 @@ def summarize_clocks(text: str, t0=None, t1=None) -> dict:
 # --------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm)
 # --------------------------------------------------------------------------
+def host_cores() -> int:
+    """Host cores this process may run on (the oracle's thread count: the
+    timing legs run alone, on rank 0, so OMP_NUM_THREADS=1 that torchrun sets
+    per rank does not apply to them)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_sample(step: int = 0, n_m: int = 2, n_r: int = 2):
     """Time the FP64 oracle on a bounded sample of one step and extrapolate:
     analysis of n_m whole m columns (all l, all 8 channels) and synthesis of
@@ -239,9 +249,10 @@ def oracle_sample(step: int = 0, n_m: int = 2, n_r: int = 2):
     ls_all = np.concatenate(ls_all).astype(np.int32)
     ms_all = np.concatenate(ms_all).astype(np.int32)
     t0 = time.perf_counter()
-    oracle.analysis_sep(maps, LMAX, ls_all, ms_all, weights="equal")
+    nthreads = host_cores()
+    oracle.analysis_sep(maps, LMAX, ls_all, ms_all, weights="equal", nthreads=nthreads)
     t1 = time.perf_counter()
-    oracle.synthesis_sep(alm, NSIDE, LMAX, MMAX, rings)
+    oracle.synthesis_sep(alm, NSIDE, LMAX, MMAX, rings, nthreads=nthreads)
     t2 = time.perf_counter()
     t_step = (t1 - t0) * (MMAX + 1) / n_m + (t2 - t1) * R / n_r
     return {"seconds_measured": t2 - t0, "seconds_per_step_extrapolated": t_step,

@@ -158,3 +158,11 @@ def test_clock_summary_falls_back_to_all_samples():
     assert not r["in_region"] and r["samples"] == 2
     assert r["sm_mhz"] == 2065 and r["reasons"] == ["hw_slowdown"]
     assert bench.summarize_clocks("", t0, t0 + 1)["sm_mhz"] is None
+
+
+def test_oracle_legs_use_the_host_cores(monkeypatch):
+    """The oracle timing runs alone on rank 0: it takes every core the
+    process may use, whatever OMP_NUM_THREADS torchrun set for the ranks."""
+    monkeypatch.setenv("OMP_NUM_THREADS", "1")
+    n = bench.host_cores()
+    assert 1 <= n <= (os.cpu_count() or 1)
