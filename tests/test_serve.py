@@ -1,6 +1,8 @@
 """Host-side logic of the continuously batching server, with a fake executor
 (no GPU): batching, admission under the HBM cap with eviction of idle
-slots, and requests that fail on the host without blocking the others."""
+slots, oldest-first service across geometries, one slot per geometry for
+both ops without mixing them in a batch, requests that fail on the host
+without blocking the others, and the latency report."""
 import itertools
 
 from paper_2510_01785_gb300.serve import Request, Server, latency_report, make_requests
@@ -122,3 +124,44 @@ def test_make_requests_is_seeded_and_follows_the_mix():
     assert 800 < len(a) < 1200
     assert all(1 <= r.nch <= 32 and r.lmax == 3 * r.nside - 1 for r in a)
     assert 0.4 < sum(r.op == "map2alm" for r in a) / len(a) < 0.6
+
+
+def test_oldest_waiting_request_goes_first_across_geometries():
+    """With memory for one slot, the geometry whose head request arrived
+    first is served first, and the idle slot of the other is evicted."""
+    ex = FakeExecutor(bytes_per_slot=10, work=2)
+    clk = Clock()
+    srv = Server(ex, hbm_cap_bytes=10, max_channels=32, max_slots_per_key=1, clock=clk)
+    srv.submit(Request(rid=0, op="map2alm", nside=32, nch=4, t_arrival=0.5))
+    srv.submit(Request(rid=1, op="map2alm", nside=16, nch=4, t_arrival=0.1))
+    srv.submit(Request(rid=2, op="map2alm", nside=32, nch=4, t_arrival=0.6))
+    drain(srv)
+    assert [b for _, _, b in ex.launches] == [[1], [0, 2]]
+    assert srv.peak_bytes <= 10
+
+
+def test_ops_share_a_geometry_slot_but_not_a_batch():
+    ex = FakeExecutor()
+    srv = Server(ex, hbm_cap_bytes=100, max_channels=32, max_slots_per_key=1, clock=Clock())
+    for i in range(6):
+        srv.submit(Request(rid=i, op="map2alm" if i % 2 else "alm2map", nside=64, nch=3))
+    drain(srv)
+    slots = {h for h, _, _ in ex.launches}
+    assert len(slots) == 1  # one slot for the geometry, both ops on it
+    for _, op, b in ex.launches:
+        assert all((rid % 2 == 1) == (op == "map2alm") for rid in b)
+    assert sorted(rid for _, _, b in ex.launches for rid in b) == list(range(6))
+
+
+def test_latency_report_percentiles():
+    reqs = []
+    for i in range(100):
+        r = Request(rid=i, op="map2alm", nside=16, nch=1, t_arrival=float(i))
+        r.t_done = r.t_arrival + (i + 1) * 1e-3  # latencies 1 .. 100 ms
+        reqs.append(r)
+    bad = Request(rid=100, op="map2alm", nside=16, nch=1)
+    bad.error, bad.t_done = "rejected", 0.0
+    rep = latency_report(reqs + [bad])
+    assert rep["requests"] == 101 and rep["served"] == 100 and rep["errors"] == 1
+    assert abs(rep["p50_ms"] - 50.5) < 1e-9 and abs(rep["p99_ms"] - 99.01) < 1e-9
+    assert abs(rep["mean_ms"] - 50.5) < 1e-9
