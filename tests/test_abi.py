@@ -83,3 +83,49 @@ def test_estimate_counts_the_tensor_core_operands(hpxlib):
     tc = L.hpx_plan_estimate_bytes(1024, 3071, 3071, 8, 1, 3)
     # Gt operand: (mmax+1) x 64 groups x 32 columns x 32 pairs x 4 bytes
     assert tc - table >= 3072 * 64 * 32 * 32 * 4
+
+
+def _header_declarations():
+    """{name: (return type, [argument types])} of every function declared in
+    include/hpx.h (comments and preprocessor lines stripped)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "hpx.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = "\n".join(ln for ln in src.splitlines() if not ln.lstrip().startswith("#"))
+    out = {}
+    for stmt in src.split(";"):
+        stmt = re.split(r"[{}]", stmt)[-1]
+        mt = re.fullmatch(r"\s*([A-Za-z_][\w\s\*]*?)\s*\b(hpx_\w+)\s*\(([^()]*)\)\s*", stmt, flags=re.S)
+        if not mt:
+            continue
+        ret, name, args = mt.groups()
+        parts = [a.strip() for a in args.split(",")] if args.strip() not in ("", "void") else []
+        types = [re.sub(r"\s*\b\w+$", "", a).replace(" *", "*").strip() for a in parts]
+        out[name] = (" ".join(ret.split()).replace(" *", "*"), types)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """The ctypes table of the Python binding mirrors include/hpx.h: the same
+    functions, argument counts and argument types, so no call passes a value
+    of the wrong width."""
+    import ctypes
+
+    from paper_2510_01785_gb300 import _lib
+    P = ctypes.c_void_p
+    arg = {"const double*": P, "const void*": P, "double*": P, "void*": P, "int32_t*": P, "int64_t*": P,
+           "hpx_plan": P, "hpx_stream_t": P, "hpx_plan*": ctypes.POINTER(P),
+           "int": ctypes.c_int, "hpx_dtype": ctypes.c_int, "hpx_layout": ctypes.c_int,
+           "unsigned": ctypes.c_uint, "size_t": ctypes.c_size_t}
+    res = {"hpx_status": ctypes.c_int, "size_t": ctypes.c_size_t, "int64_t": ctypes.c_int64,
+           "const char*": ctypes.c_char_p}
+    decl = _header_declarations()
+    assert len(decl) >= 30
+    assert set(decl) == set(_lib.SIGNATURES)
+    for name, (ret, types) in decl.items():
+        r, a = _lib.SIGNATURES[name]
+        assert r is res[ret], (name, ret)
+        assert len(a) == len(types), (name, types)
+        for got, t in zip(a, types):
+            assert got is arg[t], (name, t)
