@@ -88,7 +88,6 @@ def test_estimate_counts_the_tensor_core_operands(hpxlib):
 def _header_declarations():
     """{name: (return type, [argument types])} of every function declared in
     include/hpx.h (comments and preprocessor lines stripped)."""
-    import re
     src = open(os.path.join(ROOT, "include", "hpx.h")).read()
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
@@ -110,8 +109,6 @@ def test_binding_signatures_match_the_header():
     """The ctypes table of the Python binding mirrors include/hpx.h: the same
     functions, argument counts and argument types, so no call passes a value
     of the wrong width."""
-    import ctypes
-
     from paper_2510_01785_gb300 import _lib
     P = ctypes.c_void_p
     arg = {"const double*": P, "const void*": P, "double*": P, "void*": P, "int32_t*": P, "int64_t*": P,
