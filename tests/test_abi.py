@@ -126,3 +126,13 @@ def test_binding_signatures_match_the_header():
         assert len(a) == len(types), (name, types)
         for got, t in zip(a, types):
             assert got is arg[t], (name, t)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with libhpx.so missing, the first library call raises
+    and names the build step."""
+    from paper_2510_01785_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libhpx.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="libhpx.so not found"):
+        _lib.lib()
