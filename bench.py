@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-drain", type=float, default=15.0)
+    ap.add_argument("--record", default=os.path.join("gpurun_out", "bench_record.json"),
+                    help="file for the full record (every plan, stage, config); stdout gets the headline only")
     ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiling only")
     ap.add_argument("--lmax", type=int, default=None)
     ap.add_argument("--nbatch", type=int, default=NBATCH)
@@ -214,6 +216,68 @@ def summarize_clocks(text: str, t0=None, t1=None) -> dict:
             "samples": len(use), "in_region": bool(inside), "reasons": reasons}
 
 
+
+def workload_config(world: int) -> dict:
+    """The workload keys both arms print (the same dict)."""
+    return {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX, "nbatch": NBATCH,
+            "step": "map2alm + alm2map of the batch",
+            "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB at Nside 1024); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
+def _round(x, sig: int = 6):
+    """x with `sig` significant digits (floats only), for a short line."""
+    if isinstance(x, float):
+        return float(f"{x:.{sig}g}")
+    if isinstance(x, dict):
+        return {k: _round(v, sig) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_round(v, sig) for v in x]
+    return x
+
+
+HEADLINE_KEYS = ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                 "higher_is_better", "scaling", "vs_baseline", "dtype", "precision", "data", "config")
+
+
+def headline(line: dict, record_path=None) -> dict:
+    """The compact line printed last: the contract's keys, the roofline of
+    the dominant kernel, the oracle baseline, end to end and the clocks;
+    every other figure stays in the record file."""
+    h = {k: line[k] for k in HEADLINE_KEYS if k in line}
+    if "roofline" in line and line["roofline"]:
+        h["roofline"] = {k: line["roofline"].get(k)
+                         for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic")}
+    cpu = line.get("cpu_baseline")
+    h["cpu_baseline"] = {k: cpu.get(k) for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None
+    e2e = line.get("e2e")
+    h["e2e"] = {k: e2e.get(k) for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")} \
+        if e2e else None
+    if "gpu_launches" in line:
+        h["gpu_launches"] = line["gpu_launches"]
+    if line.get("clocks"):
+        h["clocks"] = {k: line["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if record_path:
+        h["record"] = record_path
+    return _round(h)
+
+
+def emit(line: dict, record_path) -> None:
+    """Write the full record to `record_path` (when given) and print the
+    headline as the one line on stdout."""
+    if record_path:
+        d = os.path.dirname(record_path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        with open(record_path, "w") as f:
+            json.dump(line, f, indent=1)
+    print(json.dumps(headline(line, record_path)), flush=True)
+
+
+def note(msg: str) -> None:
+    """Progress for a person watching the run (stderr; stdout is the line)."""
+    print(msg, file=sys.stderr, flush=True)
+
 # --------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm)
 # --------------------------------------------------------------------------
@@ -228,10 +292,11 @@ def host_cores() -> int:
 
 
 def oracle_sample(step: int = 0, n_m: int = 2, n_r: int = 2):
-    """Time the FP64 oracle on a bounded sample of one step and extrapolate:
-    analysis of n_m whole m columns (all l, all 8 channels) and synthesis of
-    n_r whole rings (all 8 channels), spread over the workload and shifted by
-    `step`; the full step costs (mmax+1)/n_m and nring/n_r times as much."""
+    """Time the FP64 oracle on a bounded sample of one step: analysis of n_m
+    whole m columns (all l, all channels) and synthesis of n_r whole rings
+    (all channels), spread over the workload and shifted by `step`.  A full
+    step costs about (mmax+1)/n_m times the analysis sample and R/n_r times
+    the synthesis sample; `fraction` is the measured share of a full step."""
     import numpy as np
 
     import oracle
@@ -254,15 +319,19 @@ def oracle_sample(step: int = 0, n_m: int = 2, n_r: int = 2):
     t1 = time.perf_counter()
     oracle.synthesis_sep(alm, NSIDE, LMAX, MMAX, rings, nthreads=nthreads)
     t2 = time.perf_counter()
-    t_step = (t1 - t0) * (MMAX + 1) / n_m + (t2 - t1) * R / n_r
+    xa, xs = (MMAX + 1) / n_m, R / n_r
+    t_step = (t1 - t0) * xa + (t2 - t1) * xs
     return {"seconds_measured": t2 - t0, "seconds_per_step_extrapolated": t_step,
-            "value": NBATCH / t_step, "cores": oracle.max_threads(),
-            "sample": f"oracle tier B: analysis of m in {list(map(int, ms))} (all l, 8 ch) and synthesis "
-                      f"of rings {list(map(int, rings))} (8 ch), extrapolated x{(MMAX + 1) / n_m:.0f} "
-                      f"(m) and x{R / n_r:.0f} (rings)"}
+            "fraction": (t2 - t0) / t_step, "value": NBATCH / t_step, "cores": oracle.max_threads(),
+            "sample": f"oracle tier B (FP64 C, OpenMP): {n_m} of {MMAX + 1} m columns analysed and "
+                      f"{n_r} of {R} rings synthesised, {NBATCH} ch; extrapolated x{xa:.0f} and x{xs:.0f}"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper ships no code), on the
+    host cores.  Each step times a bounded sample of one full step (8 m
+    columns + 8 rings); ms_per_step is that measured sample time, and value
+    is the work the samples did (in full-step pairs) over their time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -270,22 +339,26 @@ def run_reference(args):
     oracle.build()
     for w in range(args.warmup):
         oracle_sample(step=-1 - w, n_m=8, n_r=8)
-    vals, secs = [], []
+    secs, fracs, full = [], [], []
     for k in range(args.steps):
         r = oracle_sample(step=k, n_m=8, n_r=8)
-        vals.append(r["value"])
-        secs.append(r["seconds_per_step_extrapolated"])
+        secs.append(r["seconds_measured"])
+        fracs.append(r["fraction"])
+        full.append(r["seconds_per_step_extrapolated"])
         last = r
-    value = len(vals) / sum(1.0 / v for v in vals)  # pairs per second over all sampled steps
+    value = NBATCH * sum(fracs) / sum(secs)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX, "nbatch": NBATCH},
+            "precision": "FP64 oracle, each timed step a bounded sample of one full step",
+            "data": "synthetic", "config": workload_config(world),
+            "sample_fraction_of_step": statistics.mean(fracs),
+            "extrapolated_ms_per_full_step": 1e3 * statistics.mean(full),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": "per step: " + last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    rec = args.record.replace(".json", "_reference.json") if args.record else None
+    emit(line, rec)
     return 0
 
 
@@ -416,15 +489,12 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "mmax": MMAX,
-                           "nbatch": NBATCH, "step": "map2alm + alm2map of the batch",
-                           "lambda": "plan-resident table generated once by the FP64 recurrence",
-                           "analysis": "tensor cores (tcgen05 kind::f16): table and operands as FP16 hi/lo "
-                                       "pairs (operands scaled per channel by a power of two), "
-                                       "hi*hi + hi*lo + lo*hi per term, FP32 sums per 64-pair block",
-                           "l2": "inputs larger than L2 (maps 403 MB, alm 302 MB); no flush",
-                           "parallelism": f"replicas x{world}"},
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "precision": "FP32 I/O; lambda from the FP64 recurrence (plan-time table); contraction on "
+                             "tcgen05 as FP16 hi/lo split products (hi*hi + hi*lo + lo*hi, FP32 sums): "
+                             f"{acc['map2alm_max_rel_l2_vs_f64']:.1e} / {acc['alm2map_max_rel_l2_vs_f64']:.1e} "
+                             "rel. L2 vs FP64",
+                "data": "synthetic", "config": workload_config(world),
                 "roofline": roofline, "stages": stage_report, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "mixed_precision": mixed,
                 "next_rows": next_rows, "out_of_core": ooc, "other_configs": small,
@@ -437,7 +507,9 @@ def run_ours(args):
                 | {"ms_per_step": cc["t_max"] / args.steps},
                 "lambda_recompute": {k: rec[k] for k in ("value", "roofline", "stages", "accuracy", "clocks")}
                 | {"ms_per_step": rec["t_max"] / args.steps}}
-        print(json.dumps(line), flush=True)
+        for k in ("tensor_core_tf32x3", "cuda_core_table", "lambda_recompute"):
+            note(f"{k}: {line[k]['value']:.1f} pairs/s, roofline frac {line[k]['roofline']['frac']:.3f}")
+        emit(line, args.record)
     plan.close()
     if dist.is_available() and dist.is_initialized():
         dist.destroy_process_group()
@@ -512,59 +584,57 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
             "clocks": clk, "launches": sum(n for _, n in stages.values())}
 
 
-def legendre_roofline(plan, stages, table: bool):
+def legendre_roofline(plan, stages, table: bool, value_bytes: int = 4):
     """Roofline of the slower Legendre kernel, with per-stage figures added
-    to `stages` in place.  Recomputing: FP64 pipe (3 flop per significant
-    (l, m, ring-pair) triple).  Table: HBM (the table's bytes plus the
-    kernel's compulsory inputs and outputs)."""
+    to `stages` in place.
+
+    Recomputing plans: the FP64 pipe, 3 flop per significant (l, m,
+    ring-pair) triple (one DMUL + one DFMA per step of the recurrence).
+    Table plans: HBM, algorithmic bytes only: `value_bytes` per significant
+    triple (4 for FP32 and for FP16 hi/lo pairs, 2 for one 16-bit part) plus
+    the stage's own input and output (analysis: half spectra in, alm out;
+    synthesis: alm in, ring coefficients F out).  The table's alignment
+    padding and the zero parity halves of the packed tensor-core operands
+    are not counted: they are traffic of this design, not of the method."""
     active, total = plan.chain_stats()
     map_bytes = 4 * NBATCH * 12 * NSIDE * NSIDE
     alm_bytes = 8 * NBATCH * plan.nalm
     spec_bytes = 8 * NBATCH * (6 * NSIDE * NSIDE + 4 * NSIDE - 1)
     f_bytes = 8 * NBATCH * (4 * NSIDE - 1) * (MMAX + 1)
-    tab_bytes = plan.table_bytes if table else 0
-    tc = "analysis_operand_pack" in stages
-    # tensor-core analysis: the pack reads the spectra and writes the operand
-    # Gt[m][group][4 x channels][32] once; the tile kernel reads the table,
-    # Gt and writes alm
-    gt_bytes = 4 * (MMAX + 1) * ((2 * NSIDE + 31) // 32) * 32 * 4 * min(32, max(8, 1 << (NBATCH - 1).bit_length()))
+    # folded, phased S/A operand of the analysis contraction: both parities,
+    # complex, per (m, ring pair, channel)
+    g_bytes = 16 * NBATCH * (MMAX + 1) * 2 * NSIDE
     for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes),
-                  ("analysis_operand_pack", spec_bytes + gt_bytes)):
+                  ("analysis_operand_pack", spec_bytes + g_bytes), ("synthesis_operand_pack", 2 * alm_bytes)):
         if k in stages:
             s = stages[k]
             s["hbm_gbs_algorithmic"] = by / (s["ms_per_step"] / 1e3) / 1e9
-    fp64_flop = 3.0 * active  # mu_l = c_l z mu_{l-1} - mu_{l-2}: one DMUL + one DFMA per triple
-    # the tensor-core synthesis reads the column copy of the table and its packed operand
-    ctab_bytes = plan.column_table_bytes if (table and tc) else tab_bytes
-    at_bytes = 4 * sum((LMAX - m) // 32 + 1 for m in range(MMAX + 1)) * 32 * 4 * min(32, max(8, 1 << (NBATCH - 1).bit_length()))
-    leg_bytes = {"legendre_analysis": tab_bytes + (gt_bytes if tc else spec_bytes) + alm_bytes,
-                 "legendre_synthesis": (ctab_bytes + at_bytes + f_bytes) if tc else tab_bytes + alm_bytes + f_bytes}
+    lam_bytes = value_bytes * active if table else 0
+    leg_io = {"legendre_analysis": spec_bytes + alm_bytes, "legendre_synthesis": alm_bytes + f_bytes}
     for k in ("legendre_analysis", "legendre_synthesis"):
         s = stages[k]
-        sec = s["ms_per_launch"] / 1e3
+        sec = s["ms_per_step"] / 1e3
         s["fp32_contraction_tflops"] = 4.0 * NBATCH * active / sec / 1e12
         if table:
-            s["hbm_gbs_algorithmic"] = leg_bytes[k] / sec / 1e9
+            s["hbm_gbs_algorithmic"] = (lam_bytes + leg_io[k]) / sec / 1e9
         else:
-            s["fp64_tflops"] = fp64_flop / sec / 1e12
-    dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k]["ms_per_launch"])
-    kname = {"legendre_analysis": "k_legendre_analysis", "legendre_synthesis": "k_legendre_synthesis"}[dom]
+            s["fp64_tflops"] = 3.0 * active / sec / 1e12
+    dom = max(["legendre_analysis", "legendre_synthesis"], key=lambda k: stages[k]["ms_per_step"])
+    tc = "analysis_operand_pack" in stages
+    side = "analysis" if dom == "legendre_analysis" else "synthesis"
+    kname = f"k_legendre_{side}"
     if table:
-        kname = f"k_legendre_tc<{'analysis' if dom == 'legendre_analysis' else 'synthesis'}>" if tc \
-            else kname + "<table>"
+        kname = f"k_legendre_tc<{side}>" if tc else kname + "<table>"
         achieved = stages[dom]["hbm_gbs_algorithmic"]
         return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": HBM_PEAK_GBS,
                 "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": kernel_traffic(kname),
-                "peak_source": HBM_PEAK_SOURCE,
-                "work": f"lambda table {ctab_bytes if (tc and dom == 'legendre_synthesis') else tab_bytes} B "
-                        f"+ compulsory inputs/outputs "
-                        f"{leg_bytes[dom] - (ctab_bytes if (tc and dom == 'legendre_synthesis') else tab_bytes)} B "
-                        f"per launch"}
+                "peak_source": HBM_PEAK_SOURCE, "algorithmic_bytes": lam_bytes + leg_io[dom],
+                "work": f"{value_bytes} B x {active} significant lambda + {leg_io[dom]} B stage in/out per step"}
     achieved = stages[dom]["fp64_tflops"]
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(kname),
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-            "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per launch "
+            "work": f"3 FP64 flop x {active} significant (l,m,ring-pair) triples per step "
                     f"(of {total}; contributions below 2^-193 dropped)"}
 
 

@@ -281,13 +281,16 @@ hpx_status hpx_alm2map_host(hpx_plan plan, const void* host_alm,
  * synchronisation that cudaMalloc / cudaFree may cause).  The paper has no
  * counterpart: this is a deployment variant of the same kernels.
  *   The intermediate ring spectra live in one fixed 16 MiB device array
- *   compiled into the library (held on every GPU that loads it until the
- *   process exits) instead of the plan's workspace; the call allocates
- *   nothing.  Plans needing more than 16 MiB of spectra (nbatch *
- *   (6 nside^2 + 4 nside - 1) complex values) get HPX_ERR_INVALID.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   compiled into the library (held on every GPU where it was used, until
+ *   the process exits) instead of the plan's workspace.  Plans needing
+ *   more than 16 MiB of spectra (nbatch * (6 nside^2 + 4 nside - 1) complex
+ *   values) get HPX_ERR_INVALID.
+ *   The first call on a device (and the first after its context was reset)
+ *   looks up the array's device address (cudaGetSymbolAddress) with that
+ *   device current.  Under lazy module loading, the CUDA default, that
+ *   lookup also loads the array, which may allocate and synchronise once:
+ *   make the first call during set-up, outside the loop that must not
+ *   allocate, and before any stream capture.  Later calls allocate nothing.
  *   All calls share the array: calls whose work overlaps on the GPU race and
  *   must be ordered by the caller.  Nothing in it needs to start at zero.
  *   The Legendre stage runs on the CUDA cores: on the plan's table if it

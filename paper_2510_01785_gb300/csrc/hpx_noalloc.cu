@@ -13,8 +13,8 @@
 // Limit: nbatch * (6 nside^2 + 4 nside - 1) complex values of the plan's real
 // type must fit in kScratchBytes (16 MiB), e.g. nside 256 with up to 5 FP32
 // channels or nside 512 with one FP32 channel; larger requests are rejected
-// with HPX_ERR_INVALID.  The array exists once per GPU that loads the library
-// and stays allocated until the process exits.
+// with HPX_ERR_INVALID.  The array exists once per GPU on which its module has
+// been loaded (see set-up) and stays allocated until the process exits.
 //
 // Sharing: every call on a device uses the same array, and it keeps whatever
 // the last call wrote.  Nothing in it has to start at zero here: the ring
@@ -23,9 +23,15 @@
 // different host threads) race on the array; the caller must order them.
 //
 // Set-up: the device address of the array is looked up with
-// cudaGetSymbolAddress once per device, on the first call made on that
-// device, with that device current.  That first call should come before any
-// stream capture.
+// cudaGetSymbolAddress once per device and CUDA context, on the first call
+// made there, with that device current, and kept for later calls.  A device
+// whose context was reset (cudaDeviceReset) gets a new context and so a
+// fresh lookup.  Under lazy module loading (the CUDA default) that first
+// lookup also loads the module holding the array, which may allocate the
+// array's memory and synchronise once: make the first call during set-up,
+// outside any loop that must not allocate, and before any stream capture.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "hpx_internal.cuh"
@@ -39,22 +45,60 @@ constexpr int kMaxDevices = 64;
 // device address; kernels get the address looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchSlot {
+  void* ptr = nullptr;
+  unsigned long long ctx_id = 0;  // the context the address belongs to (0: unknown)
+};
 
+std::mutex g_setup_mutex;
+ScratchSlot g_scratch[kMaxDevices];
+
+// Unique id of the current CUDA context (cuCtxGetId), or 0 if the driver
+// cannot tell; with 0 the address is looked up on every call.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the array on `device`, which must be current.
 hpx_status scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) {
     hpx::set_error("hpx_map2alm_noalloc: device %d out of range", device);
     return HPX_ERR_INVALID;
   }
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[device]) {
+  ScratchSlot& slot = g_scratch[device];
+  if (!slot.ptr || ctx == 0 || slot.ctx_id != ctx) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return hpx::cuda_fail(e, "hpx_map2alm_noalloc: cudaGetSymbolAddress");
-    g_scratch_ptr[device] = ptr;
+    if (e != cudaSuccess) {
+      slot = ScratchSlot{};
+      return hpx::cuda_fail(e, "hpx_map2alm_noalloc: cudaGetSymbolAddress");
+    }
+    slot.ptr = ptr;
+    slot.ctx_id = ctx;
   }
-  *out = g_scratch_ptr[device];
+  *out = slot.ptr;
   return HPX_OK;
 }
 
@@ -83,8 +127,12 @@ extern "C" hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* 
     return HPX_ERR_INVALID;
   }
   int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != plan->device) cudaSetDevice(plan->device);
+  cudaError_t de = cudaGetDevice(&prev);
+  if (de != cudaSuccess) return hpx::cuda_fail(de, "hpx_map2alm_noalloc: cudaGetDevice");
+  if (prev != plan->device) {
+    de = cudaSetDevice(plan->device);
+    if (de != cudaSuccess) return hpx::cuda_fail(de, "hpx_map2alm_noalloc: cudaSetDevice");
+  }
   void* scratch = nullptr;
   hpx_status st = scratch_address(plan->device, &scratch);
   if (st == HPX_OK) {
@@ -106,6 +154,9 @@ extern "C" hpx_status hpx_map2alm_noalloc(hpx_plan plan, const void* map, void* 
     }
     if (e != cudaSuccess) st = hpx::cuda_fail(e, "hpx_map2alm_noalloc");
   }
-  if (prev >= 0 && prev != plan->device) cudaSetDevice(prev);
+  if (prev != plan->device) {
+    de = cudaSetDevice(prev);
+    if (de != cudaSuccess && st == HPX_OK) st = hpx::cuda_fail(de, "hpx_map2alm_noalloc: restoring the device");
+  }
   return st;
 }

@@ -619,18 +619,39 @@ static hpx_status host_call_async(hpx_plan p, const void* hin, void* hout, hpx_s
   const size_t alm_bytes = 2 * rs * (size_t)p->nbatch * p->nalm;
   cudaError_t e = cudaSuccess;
   if (!p->aio_streams) {
+    // Everything is made into locals first and handed to the plan only once
+    // all of it exists; on a failure what was made is released again, so a
+    // later call retries the whole set-up.
     cudaStream_t* st = new cudaStream_t[2]();
-    p->aio_streams = st;
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
     cudaEvent_t* ev = new cudaEvent_t[6]();
-    p->aio_events = ev;
+    void* dm[2] = {nullptr, nullptr};
+    void* da[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-      e = cudaMalloc(&p->d_aio_map[k], map_bytes);
-      if (e == cudaSuccess) e = cudaMalloc(&p->d_aio_alm[k], alm_bytes);
-      if (e == cudaSuccess) p->bytes += map_bytes + alm_bytes;
+      e = cudaMalloc(&dm[k], map_bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&da[k], alm_bytes);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "pipelined I/O set-up");
+    if (e != cudaSuccess) {
+      for (int k = 0; k < 2; ++k) {
+        if (dm[k]) cudaFree(dm[k]);
+        if (da[k]) cudaFree(da[k]);
+      }
+      for (int i = 0; i < 6; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+      for (int i = 0; i < 2; ++i)
+        if (st[i]) cudaStreamDestroy(st[i]);
+      delete[] ev;
+      delete[] st;
+      return cuda_fail(e, "pipelined I/O set-up");
+    }
+    for (int k = 0; k < 2; ++k) {
+      p->d_aio_map[k] = dm[k];
+      p->d_aio_alm[k] = da[k];
+    }
+    p->bytes += 2 * (map_bytes + alm_bytes);
+    p->aio_events = ev;
+    p->aio_streams = st;
   }
   cudaStream_t* st = static_cast<cudaStream_t*>(p->aio_streams);
   cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->aio_events);  // uploaded[2], computed[2], free[2]

@@ -89,30 +89,42 @@ def _stages(ana_ms, syn_ms, tc):
     return s
 
 
+def _bytes():
+    nalm = _Plan().nalm
+    return {"map": 4 * bench.NBATCH * 12 * bench.NSIDE ** 2, "alm": 8 * bench.NBATCH * nalm,
+            "spec": 8 * bench.NBATCH * (6 * bench.NSIDE ** 2 + 4 * bench.NSIDE - 1),
+            "F": 8 * bench.NBATCH * (4 * bench.NSIDE - 1) * (bench.MMAX + 1)}
+
+
 def test_table_roofline_takes_the_slower_kernel(monkeypatch):
+    """Algorithmic bytes: 4 B per significant lambda plus the stage's own
+    input and output; the table's padding (table_bytes) does not count."""
     monkeypatch.setattr(bench, "kernel_traffic", lambda k: None)
     plan = _Plan()
+    active, _ = plan.chain_stats()
+    b = _bytes()
     st = _stages(4.0, 5.0, tc=True)
     r = bench.legendre_roofline(plan, st, table=True)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["kernel"] == "k_legendre_tc<synthesis>"
     assert r["achieved"] == st["legendre_synthesis"]["hbm_gbs_algorithmic"]
     assert r["frac"] == pytest.approx(r["achieved"] / bench.HBM_PEAK_GBS)
-    # the tensor-core synthesis streams the column copy of the table
-    assert r["achieved"] > plan.column_table_bytes / 5e-3 / 1e9
-    assert r["achieved"] < 1.1 * plan.column_table_bytes / 5e-3 / 1e9
-    # the analysis streams the row table: slower stage flips the choice
+    assert r["achieved"] == pytest.approx((4 * active + b["alm"] + b["F"]) / 5e-3 / 1e9)
+    assert r["algorithmic_bytes"] == 4 * active + b["alm"] + b["F"]
+    # the slower stage flips the choice; the analysis reads spectra, writes alm
     st = _stages(6.0, 5.0, tc=True)
     r = bench.legendre_roofline(plan, st, table=True)
     assert r["kernel"] == "k_legendre_tc<analysis>"
-    assert plan.table_bytes / 6e-3 / 1e9 < r["achieved"] < 1.1 * plan.table_bytes / 6e-3 / 1e9
+    assert r["achieved"] == pytest.approx((4 * active + b["spec"] + b["alm"]) / 6e-3 / 1e9)
+    # 16-bit single-part tables: 2 B per value
+    r2 = bench.legendre_roofline(plan, _stages(6.0, 5.0, tc=True), table=True, value_bytes=2)
+    assert r2["achieved"] == pytest.approx((2 * active + b["spec"] + b["alm"]) / 6e-3 / 1e9)
     # every FFT stage and the pack get an algorithmic bandwidth
     for k in ("ring_fft_analysis", "ring_fft_synthesis", "analysis_operand_pack"):
         assert st[k]["hbm_gbs_algorithmic"] > 0
     # the analysis ring FFT moves the maps and the spectra once each
-    map_b = 4 * bench.NBATCH * 12 * bench.NSIDE ** 2
-    spec_b = 8 * bench.NBATCH * (6 * bench.NSIDE ** 2 + 4 * bench.NSIDE - 1)
-    assert st["ring_fft_analysis"]["hbm_gbs_algorithmic"] == pytest.approx((map_b + spec_b) / 0.5e-3 / 1e9)
+    assert st["ring_fft_analysis"]["hbm_gbs_algorithmic"] == pytest.approx((b["map"] + b["spec"]) / 0.5e-3 / 1e9)
+    assert st["ring_fft_synthesis"]["hbm_gbs_algorithmic"] == pytest.approx((b["F"] + b["map"]) / 1.0e-3 / 1e9)
 
 
 def test_cuda_core_table_and_recompute_rooflines(monkeypatch):
@@ -129,6 +141,90 @@ def test_cuda_core_table_and_recompute_rooflines(monkeypatch):
     assert r["achieved"] == pytest.approx(3.0 * active / 50e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS)
     assert "hbm_gbs_algorithmic" not in st["legendre_synthesis"]
+
+
+def _full_line():
+    """A record shaped like the benchmark's, with its bulky sub-records."""
+    big = {"stages": {f"s{i}": {"ms_per_step": 1.234567, "launches": 3} for i in range(20)},
+           "sample": list(range(64))}
+    return {"metric": bench.METRIC, "value": 712.123456789, "unit": bench.UNIT, "n_gpus": 1, "steps": 20,
+            "warmup": 5, "ms_per_step": 11.2345678, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "precision": "FP32 I/O; FP64 lambda; FP16 hi/lo products",
+            "data": "synthetic", "config": bench.workload_config(1),
+            "roofline": {"bound": "hbm", "kernel": "k_legendre_tc<synthesis>", "achieved": 6345.6789,
+                         "peak": 6791.0, "unit": "GB/s", "frac": 0.9344, "traffic": 2.9e10,
+                         "peak_source": "measured", "work": "x" * 300, "algorithmic_bytes": 29890000000},
+            "cpu_baseline": {"value": 0.021, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
+                             "sample": "oracle tier B (FP64 C, OpenMP): 64 of 3072 m columns analysed and 64 "
+                                       "of 4095 rings synthesised, 8 ch; extrapolated x48 and x64",
+                             "seconds": 7.1},
+            "e2e": {"value": 678.9, "unit": bench.UNIT, "h2d_bytes_per_step": 704_643_072,
+                    "d2h_bytes_per_step": 704_643_072, "calls": "y" * 200, "blocking_calls_value": 400.0},
+            "gpu_launches": 180, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 7,
+                                            "in_region": True, "reasons": []},
+            "serving": big, "mixed_precision": big, "next_rows": big, "out_of_core": big, "other_configs": big,
+            "cuda_core_table": big, "lambda_recompute": big, "tensor_core_tf32x3": big}
+
+
+def test_headline_is_short_and_complete():
+    """The line printed last fits in the 1.5 KB a driver keeps of stdout and
+    carries the contract's keys; the bulky sub-records stay in the file."""
+    import json
+    line = _full_line()
+    assert len(json.dumps(line)) > 4000
+    h = bench.headline(line, "gpurun_out/bench_record.json")
+    text = json.dumps(h)
+    assert len(text) < 1500, len(text)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+              "gpu_launches", "clocks"):
+        assert k in h, k
+    assert set(h["roofline"]) == {"bound", "kernel", "achieved", "peak", "unit", "frac", "traffic"}
+    assert set(h["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert h["value"] == pytest.approx(line["value"], rel=1e-4)
+    assert h["config"]["workload"] == bench.WORKLOAD
+    for k in ("serving", "mixed_precision", "stages", "next_rows"):
+        assert k not in h
+
+
+def test_emit_writes_the_record_and_prints_one_line(tmp_path, capsys):
+    import json
+    line = _full_line()
+    path = str(tmp_path / "out" / "rec.json")
+    bench.emit(line, path)
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    h = json.loads(out[0])
+    assert h["record"] == path and h["value"] == pytest.approx(712.123, rel=1e-6)
+    assert json.load(open(path)) == json.loads(json.dumps(line))
+
+
+def test_reference_arm_times_what_it_measured(tmp_path, monkeypatch, capsys):
+    """The oracle arm: ms_per_step is the measured time of each sampled step
+    (so ms_per_step x steps is the timed region), and value is the sampled
+    work in full-step pairs over that time; the two arms share config."""
+    import json
+    pytest.importorskip("oracle")
+    monkeypatch.setattr(bench, "NSIDE", 8)
+    monkeypatch.setattr(bench, "LMAX", 23)
+    monkeypatch.setattr(bench, "MMAX", 23)
+    monkeypatch.setattr(bench, "NBATCH", 2)
+    monkeypatch.setattr(bench, "WORKLOAD", "healpix-sht-nside8-lmax23-b2-f32")
+    args = type("A", (), {"steps": 2, "warmup": 1, "record": str(tmp_path / "rec.json")})()
+    t0 = time.perf_counter()
+    assert bench.run_reference(args) == 0
+    wall = time.perf_counter() - t0
+    h = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert h["impl"] == "reference" and h["steps"] == 2 and h["warmup"] == 1
+    assert h["ms_per_step"] * h["steps"] / 1e3 <= wall
+    rec = json.load(open(str(tmp_path / "rec_reference.json")))
+    assert 0 < rec["sample_fraction_of_step"] <= 1
+    assert rec["extrapolated_ms_per_full_step"] >= rec["ms_per_step"]
+    # value = sampled share of a step x channels / measured seconds
+    assert h["value"] == pytest.approx(2 * rec["sample_fraction_of_step"] / (rec["ms_per_step"] / 1e3),
+                                       rel=1e-3)
+    assert h["config"] == bench.workload_config(1)
+    assert h["e2e"]["h2d_bytes_per_step"] == 0
 
 
 def _smi_line(t, sm, reasons=()):
