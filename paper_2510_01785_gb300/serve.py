@@ -4,7 +4,10 @@ Requests (map2alm or alm2map of 1..max_channels channels at some Nside) are
 queued per (nside, lmax, op).  Whenever a slot -- a plan with its own CUDA
 stream and I/O buffers, resident on the device -- is free, the oldest queue
 with a slot of its geometry packs as many of its waiting requests as fit
-into one batched call (hpx_map2alm_n / hpx_alm2map_n): requests that arrive
+into one batched call (hpx_map2alm_n / hpx_alm2map_n) of up to the slot's
+batch capacity, which the executor sets per geometry and which may exceed
+one request's channel limit, so that one pass over the Legendre functions
+serves several requests: requests that arrive
 while others run join the next batch, and slots of different geometries run
 concurrently on their own streams.  New slots are admitted only while the
 device bytes of all resident slots stay under the HBM cap; idle slots of
@@ -71,7 +74,14 @@ class Server:
         self.bytes = 0
         self.peak_bytes = 0
         self.batches = 0
+        self.evictions = 0
         self.finished: list = []
+
+    def capacity(self, nside: int, lmax: int) -> int:
+        """Channels one batch of this geometry may hold (the executor's
+        choice, else the per-request limit)."""
+        f = getattr(self.ex, "batch_capacity", None)
+        return max(self.max_ch, int(f(nside, lmax))) if f else self.max_ch
 
     # -- admission ------------------------------------------------------------
     def submit(self, req: Request) -> None:
@@ -84,7 +94,7 @@ class Server:
             err = f"{req.nch} channels outside [1, {self.max_ch}]"
         elif req.lmax < 0:
             err = f"lmax {req.lmax} < 0"
-        elif self.ex.slot_bytes(req.nside, req.lmax, self.max_ch) > self.cap:
+        elif self.ex.slot_bytes(req.nside, req.lmax, self.capacity(req.nside, req.lmax)) > self.cap:
             err = "one slot for this request exceeds the HBM cap"
         if err is not None:
             req.error = err
@@ -106,7 +116,8 @@ class Server:
                 return s
         if len(self.slots[key]) >= self.max_slots:
             return None
-        need = self.ex.slot_bytes(key[0], key[1], self.max_ch)
+        cap_ch = self.capacity(key[0], key[1])
+        need = self.ex.slot_bytes(key[0], key[1], cap_ch)
         while self.bytes + need > self.cap:  # evict idle slots of other geometries, least recently used first
             idle = [s for k, ss in self.slots.items() if k != key for s in ss if not s.busy]
             if not idle:
@@ -115,7 +126,8 @@ class Server:
             self.slots[victim.key].remove(victim)
             self.ex.free_slot(victim.handle)
             self.bytes -= victim.nbytes
-        handle = self.ex.new_slot(key[0], key[1], self.max_ch)
+            self.evictions += 1
+        handle = self.ex.new_slot(key[0], key[1], cap_ch)
         s = Slot(key=key, nbytes=self.ex.handle_bytes(handle), handle=handle, last_used=now)
         self.slots[key].append(s)
         self.bytes += s.nbytes
@@ -144,7 +156,8 @@ class Server:
                 if s is None:
                     break
                 batch, nch = [], 0
-                while q and nch + q[0].nch <= self.max_ch:
+                cap_ch = self.capacity(k[0], k[1])
+                while q and nch + q[0].nch <= cap_ch:
                     r = q.popleft()
                     r.t_start = now
                     batch.append(r)
@@ -196,26 +209,45 @@ def latency_report(requests) -> dict:
 # ----------------------------------------------------------------------------
 class GpuExecutor:
     """Slots are libhpx plans (FP32) with a CUDA stream and one map and one
-    coefficient buffer of max_channels rows each."""
+    coefficient buffer of the slot's batch capacity.
 
-    def __init__(self, device=None, keep_outputs: bool = True, lambda_table_nsides=()):
+    table_nsides: geometries whose slots hold a plan-time lambda table on the
+    tensor cores (FP16 hi/lo split products, FP32 accuracy); the others
+    recompute lambda with the FP64 recurrence on every call.
+    batch_channels: channels per batch by Nside (default 32); one batch runs
+    the recurrence, or streams the table, once for all its requests."""
+
+    def __init__(self, device=None, keep_outputs: bool = True, lambda_table_nsides=(), batch_channels=None,
+                 tensor_cores: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.keep = keep_outputs
         self.table_nsides = set(lambda_table_nsides)
+        self.batch_channels = dict(batch_channels or {})
+        self.tc = tensor_cores
+
+    def batch_capacity(self, nside, lmax) -> int:
+        return int(self.batch_channels.get(nside, 32))
+
+    def _flags(self, nside) -> int:
+        from . import _lib
+        if nside not in self.table_nsides:
+            return _lib.HPX_PLAN_LAMBDA_RECOMPUTE
+        return _lib.HPX_PLAN_LAMBDA_TABLE | (_lib.HPX_PLAN_TENSOR_CORES if self.tc else 0)
 
     def slot_bytes(self, nside, lmax, max_ch) -> int:
         from . import _lib
-        flags = _lib.HPX_PLAN_LAMBDA_TABLE if nside in self.table_nsides else 0
-        plan = _lib.lib().hpx_plan_estimate_bytes(nside, lmax, lmax, max_ch, _lib.HPX_F32, flags)
+        plan = _lib.lib().hpx_plan_estimate_bytes(nside, lmax, lmax, max_ch, _lib.HPX_F32, self._flags(nside))
         io = max_ch * (4 * 12 * nside * nside + 8 * ((lmax + 1) * (lmax + 2) // 2))
         return int(plan + io)
 
     def new_slot(self, nside, lmax, max_ch):
         from . import Plan
         torch = self.torch
-        plan = Plan(nside, lmax, lmax, max_ch, "f32", lambda_table=nside in self.table_nsides, device=self.device)
+        tab = nside in self.table_nsides
+        plan = Plan(nside, lmax, lmax, max_ch, "f32", lambda_table=tab, tensor_cores=tab and self.tc,
+                    device=self.device)
         h = {"plan": plan, "stream": torch.cuda.Stream(self.device), "map": plan.empty_map(),
              "alm": plan.empty_alm(), "event": torch.cuda.Event(), "ys": []}
         h["nbytes"] = plan.device_bytes + h["map"].nbytes + h["alm"].nbytes

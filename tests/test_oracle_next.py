@@ -133,7 +133,7 @@ def test_ring_weights_properties(nside, lmax):
     assert np.allclose(w, w[::-1], rtol=0, atol=1e-18)                  # north/south symmetric
     assert abs(np.sum(N * w) - 4 * np.pi) < 1e-12                        # total area
     assert hw.quadrature_residual(w, nside, lmax) <= hw.quadrature_residual(weq, nside, lmax)
-    assert np.all(np.abs(w / weq - 1) < 0.25)  # the Tikhonov term keeps them near equal (15% at 16, 47)
+    assert np.all(np.abs(w / weq - 1) < hw.MAX_DEVIATION)  # the Tikhonov term keeps them near equal
 
 
 @pytest.mark.parametrize("nside,lmax", [(16, 32), (64, 128)])
@@ -143,3 +143,19 @@ def test_ring_weights_improve_band_limited_analysis(nside, lmax):
     e_eq = np.linalg.norm(oracle.map2alm(f, lmax, lmax) - a)
     e_w = np.linalg.norm(oracle.analysis(f, lmax, lmax, weights=hw.ring_weights(nside, lmax)) - a)
     assert e_w < e_eq
+
+
+@pytest.mark.parametrize("nside,lmax,gain", [(16, 16, 5.0), (32, 32, 10.0), (32, 48, 4.0), (64, 96, 8.0)])
+def test_ring_weights_gain_an_order_of_magnitude_at_low_band_limits(nside, lmax, gain):
+    """Where the latitude conditions can be met (lmax up to about 1.5 nside)
+    the ring weights cut the analysis error of band-limited maps by about an
+    order of magnitude or more (Sec. IV-A reports ~10x for its ring
+    weights); the small Tikhonov weight chosen there is what allows it (the
+    fixed alpha = 1e-2 gained only 1.5-4x)."""
+    a = syn.gaussian_alm(720 + nside, lmax, lmax, 1, power=2.0)
+    f = oracle.alm2map(a, nside, lmax, lmax)
+    e_eq = np.linalg.norm(oracle.map2alm(f, lmax, lmax) - a)
+    e_w = np.linalg.norm(oracle.analysis(f, lmax, lmax, weights=hw.ring_weights(nside, lmax)) - a)
+    e_w2 = np.linalg.norm(oracle.analysis(f, lmax, lmax, weights=hw.ring_weights(nside, lmax, alpha=1e-2)) - a)
+    assert e_eq / e_w >= gain, e_eq / e_w
+    assert e_w < e_w2

@@ -165,3 +165,41 @@ def test_latency_report_percentiles():
     assert rep["requests"] == 101 and rep["served"] == 100 and rep["errors"] == 1
     assert abs(rep["p50_ms"] - 50.5) < 1e-9 and abs(rep["p99_ms"] - 99.01) < 1e-9
     assert abs(rep["mean_ms"] - 50.5) < 1e-9
+
+
+class WideExecutor(FakeExecutor):
+    """Batches of up to 96 channels at Nside 2048, the default elsewhere."""
+
+    def batch_capacity(self, nside, lmax):
+        return 96 if nside == 2048 else 32
+
+    def launch(self, h, op, batch):
+        cap = self.batch_capacity(batch[0].nside, batch[0].lmax)
+        assert sum(r.nch for r in batch) <= cap and len({(r.nside, r.op) for r in batch}) == 1
+        h["left"], h["batch"] = self.work, batch
+        self.launches.append((h["id"], op, [r.rid for r in batch]))
+
+
+def test_batch_capacity_may_exceed_one_requests_limit():
+    """A geometry whose slots take 96 channels packs several 32-channel
+    requests into one call; requests are still limited to 32 channels."""
+    ex = WideExecutor()
+    srv = Server(ex, hbm_cap_bytes=100, max_channels=32, max_slots_per_key=1, clock=Clock())
+    reqs = [Request(rid=i, op="alm2map", nside=2048, nch=30) for i in range(9)]
+    reqs.append(Request(rid=9, op="alm2map", nside=2048, nch=33))
+    for r in reqs:
+        srv.submit(r)
+    drain(srv)
+    assert reqs[9].error is not None and "channels" in reqs[9].error
+    assert all(r.y == f"out{r.rid}" for r in reqs[:9])
+    assert [len(b) for _, _, b in ex.launches] == [3, 3, 3]
+
+
+def test_evictions_are_counted():
+    ex = FakeExecutor(bytes_per_slot=10)
+    srv = Server(ex, hbm_cap_bytes=20, max_channels=32, max_slots_per_key=1, clock=Clock())
+    for i, ns in enumerate([64, 128, 256, 64, 512]):
+        srv.submit(Request(rid=i, op="map2alm", nside=ns, nch=4))
+        drain(srv)
+    # two slots fit: 256 evicts 64's (LRU), 64 evicts 128's, 512 evicts 256's
+    assert srv.evictions == 3 and srv.bytes <= 20

@@ -35,3 +35,63 @@ def test_results_alone_equal_results_in_the_mix():
             torch.cuda.synchronize()
         err = (r.y - alone).abs().max().item() / max(alone.abs().max().item(), 1e-30)
         assert err <= 1e-6, (r.rid, r.op, r.nside, r.nch, err)
+
+
+def _rel(got, ref):
+    got, ref = np.atleast_2d(got), np.atleast_2d(ref)
+    num = np.linalg.norm((got - ref).reshape(ref.shape[0], -1), axis=1)
+    return float(np.max(num / np.maximum(np.linalg.norm(ref.reshape(ref.shape[0], -1), axis=1), 1e-300)))
+
+
+def test_served_results_match_the_oracle_with_tables_and_eviction():
+    """Every served result against the FP64 oracle (relative L2 per channel
+    <= 1e-5, the FP32 bar): geometries up to Nside 256, tensor-core table
+    slots (Nside 32 and 128) beside recomputing ones, batches wider than one
+    request, and an HBM cap small enough that idle slots are evicted."""
+    import oracle
+    from paper_2510_01785_gb300.serve import GpuExecutor, Server, latency_report, make_requests
+
+    weights = {16: 1, 32: 1, 64: 1, 128: 1, 256: 1}
+    reqs = make_requests(23, rate=3000.0, duration=0.012, nside_weights=weights, max_channels=6)
+    assert len(reqs) >= 20
+    for r in reqs:
+        if r.op == "map2alm":
+            alm = syn.gaussian_alm(3000 + r.rid, r.lmax, r.lmax, r.nch, power=2.0)
+            r.x_np = oracle.alm2map(alm, r.nside, r.lmax, r.lmax) if r.nside <= 64 else \
+                syn.white_maps(3000 + r.rid, r.nside, r.nch)
+            r.x = torch.from_numpy(r.x_np.astype(np.float32)).cuda()
+        else:
+            r.x_np = syn.gaussian_alm(4000 + r.rid, r.lmax, r.lmax, r.nch).astype(np.complex64)
+            r.x = torch.from_numpy(r.x_np).cuda()
+    ex = GpuExecutor(lambda_table_nsides=(32, 128), batch_channels={ns: 12 for ns in weights})
+    sizes = sorted(ex.slot_bytes(ns, 3 * ns - 1, 12) for ns in weights)
+    cap = sizes[-1] + sizes[-2] + 1  # the two largest slots fit, not all five geometries
+    srv = Server(ex, hbm_cap_bytes=cap, max_channels=6, max_slots_per_key=1)
+    srv.run(reqs, drain_s=120.0)
+    torch.cuda.synchronize()
+    rep = latency_report(reqs)
+    assert rep["served"] == len(reqs) and rep["errors"] == 0
+    assert srv.batches < len(reqs) and srv.evictions > 0 and srv.peak_bytes <= cap
+    for r in reqs:
+        y = r.y.cpu().numpy()
+        x = r.x_np.astype(np.float64) if r.op == "map2alm" else r.x_np.astype(np.complex128)
+        if r.nside <= 128:
+            ref = oracle.map2alm(x, r.lmax, r.lmax) if r.op == "map2alm" else \
+                oracle.alm2map(x, r.nside, r.lmax, r.lmax)
+            got = y
+        elif r.op == "map2alm":  # sampled coefficients, including l = m, lmax and m = lmax
+            g = syn.rng(r.rid)
+            ms = np.array([0, 1, r.lmax // 2, r.lmax - 1, r.lmax], np.int32)
+            ls = np.array([min(m + int(k), r.lmax) for m in ms for k in (0, 1, g.integers(0, r.lmax + 1))], np.int32)
+            ms = np.repeat(ms, 3)
+            ls = np.maximum(ls, ms)
+            ref = oracle.analysis_sep(x, r.lmax, ls, ms, weights="equal")
+            got = y[:, oracle.alm_index(r.lmax, ls, ms)]
+        else:  # sampled rings: both poles, a cap ring, the equator
+            R = 4 * r.nside - 1
+            rings = np.array([0, 1, r.nside - 1, 2 * r.nside - 1, R - 1], np.int32)
+            ref = oracle.synthesis_sep(x, r.nside, r.lmax, r.lmax, rings)
+            geo = oracle.ring_geometry(r.nside)
+            got = np.concatenate([y[:, geo["start"][k]: geo["start"][k] + geo["nphi"][k]] for k in rings], axis=1)
+        e = _rel(got, ref)
+        assert e <= 1e-5, (r.rid, r.op, r.nside, r.nch, e)

@@ -178,6 +178,53 @@ def test_cfg2_tensor_core_sampled():
     assert rel_err(a[:, oracle.alm_index(L2, ls, mm)], ref) <= 1e-5
 
 
+def test_cfg2_tensor_core_adjoints_and_gradients_sampled():
+    """Nside 1024, lmax 3071, 8 channels on the benchmark's tensor-core plan
+    (FP16 hi/lo): both adjoints (Sec. III-F) and both gradient forms against
+    the oracle on sampled coefficients and rings.  Y^dagger p is the analysis
+    sum with unit weights; W Y a the synthesis times the ring weight; the
+    gradients are D Y^dagger g (Im of m = 0 dropped) and W Y D^-1 g, with
+    D = 1 at m = 0 and 2 above (the complex-gradient convention)."""
+    maps = syn.white_maps(syn.SEED_BASE + 12, NS2, B2).astype(np.float32)
+    alm_in = syn.gaussian_alm(syn.SEED_BASE + 13, L2, L2, B2, power=2.0).astype(np.complex64)
+    h = hpx()
+    dm, da = torch.from_numpy(maps).cuda(), torch.from_numpy(alm_in).cuda()
+    with h.Plan(NS2, L2, L2, B2, "f32", lambda_table=True, tensor_cores=True) as pc:
+        adj_a = pc.alm2map_adjoint(dm).cpu().numpy()
+        grad_a = pc.alm2map_grad(dm).cpu().numpy()
+        adj_m = pc.map2alm_adjoint(da).cpu().numpy()
+        grad_m = pc.map2alm_grad(da).cpu().numpy()
+        pc.device_status()
+    ms = [0, 1, 2, 127, 128, 1024, 2047, 3000, 3071]
+    ls, mm = [], []
+    r = syn.rng(79)
+    for m in ms:
+        cand = sorted(set([m, min(m + 1, L2), min(m + 127, L2), min(m + 128, L2), L2]
+                          + list(r.integers(m, L2 + 1, 3))))
+        ls += cand
+        mm += [m] * len(cand)
+    ls, mm = np.array(ls, np.int32), np.array(mm, np.int32)
+    idx = oracle.alm_index(L2, ls, mm)
+    ref = oracle.analysis_sep(maps.astype(np.float64), L2, ls, mm, weights=None)
+    assert rel_err(adj_a[:, idx], ref) <= 1e-5
+    Dm = np.where(mm == 0, 1.0, 2.0)
+    gref = Dm * ref
+    gref[:, mm == 0] = gref[:, mm == 0].real
+    assert rel_err(grad_a[:, idx], gref) <= 1e-5
+    R = 4 * NS2 - 1
+    rings = np.array([0, 1, 2, 127, 128, 511, 1023, 1500, 2047, 3070, R - 2, R - 1], np.int32)
+    g = oracle.ring_geometry(NS2)
+
+    def pick(x):
+        return np.concatenate([x[:, g["start"][y]: g["start"][y] + g["nphi"][y]] for y in rings], axis=1)
+    a64 = alm_in.astype(np.complex128)
+    ref = oracle.synthesis_sep(a64, NS2, L2, L2, rings, scale="equal")
+    assert rel_err(pick(adj_m), ref) <= 1e-5
+    _, mall = oracle.lm_arrays(L2, L2)
+    ref = oracle.synthesis_sep(a64 / np.where(mall == 0, 1.0, 2.0), NS2, L2, L2, rings, scale="equal")
+    assert rel_err(pick(grad_m), ref) <= 1e-5
+
+
 @pytest.mark.parametrize("kw", [dict(lambda_table=True, tensor_cores=True), dict(lambda_table=True, tensor_cores=True,
                                                                               tf32x3=True), {}],
                          ids=["fp16-split", "tf32x3", "cuda-cores"])
