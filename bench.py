@@ -467,6 +467,7 @@ def run_ours(args):
         plan.close()
         torch.cuda.empty_cache()
         small = run_small_configs(dev)
+        small["round_trip_vs_nside"] = run_round_trip(dev)
 
     mixed = None
     if not args.no_mixed:
@@ -578,7 +579,7 @@ def timed_steps(plan, maps, alm_in, args, dist, dev, world, gpu_index):
     t_max = reduce_max(dist, t_ms, dev)
     report = {}
     for k, (ms, n) in stages.items():
-        if n > 0 or k != "analysis_operand_pack":
+        if n > 0 or k not in ("analysis_operand_pack", "synthesis_operand_pack"):
             report[k] = {"ms_per_step": ms / args.steps, "ms_per_launch": ms / max(n, 1), "launches": n}
     return {"t_max": t_max, "value": throughput(world, args.steps, t_max, plan.nbatch), "stages": report,
             "clocks": clk, "launches": sum(n for _, n in stages.values())}
@@ -606,7 +607,7 @@ def legendre_roofline(plan, stages, table: bool, value_bytes: int = 4):
     g_bytes = 16 * NBATCH * (MMAX + 1) * 2 * NSIDE
     for k, by in (("ring_fft_analysis", map_bytes + spec_bytes), ("ring_fft_synthesis", f_bytes + map_bytes),
                   ("analysis_operand_pack", spec_bytes + g_bytes), ("synthesis_operand_pack", 2 * alm_bytes)):
-        if k in stages:
+        if k in stages and stages[k]["ms_per_step"] > 0:
             s = stages[k]
             s["hbm_gbs_algorithmic"] = by / (s["ms_per_step"] / 1e3) / 1e9
     lam_bytes = value_bytes * active if table else 0
@@ -885,6 +886,44 @@ def run_small_configs(dev) -> dict:
         hpx.clear_plans()
         torch.cuda.empty_cache()
     out["config4_differentiation"] = diff
+    return out
+
+
+def run_round_trip(dev, nsides=(16, 32, 64, 128, 256, 512, 1024)) -> dict:
+    """Round-trip error against Nside (Sec. IV-A, Fig. 7A), on FP64 plans:
+    f = alm2map(a) with a_lm ~ N(0, (l+1)^-2), then f' = alm2map(map2alm(f)).
+    Relative L2 and L-infinity of f' - f and relative L2 of map2alm(f) - a,
+    at the band limit lmax = 3 Nside - 1 of the paper and at lmax = Nside,
+    each with equal weights and with the ring weights of that band limit
+    (ring weights up to Nside 512).  The quadrature error of the grid, not a
+    parity figure."""
+    import numpy as np
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300 import synthetic as syn
+    from paper_2510_01785_gb300 import weights as hw
+
+    out = {}
+    for ns in nsides:
+        for lmax in (3 * ns - 1, ns):
+            a = torch.from_numpy(syn.gaussian_alm(SEED + 50 + ns, lmax, lmax, 1, power=2.0)).to(dev)
+            with hpx.Plan(ns, lmax, lmax, 1, "f64", device=dev) as p:
+                f = p.alm2map(a)
+                r = {}
+                for wname in ("equal", "ring"):
+                    if wname == "ring":
+                        if ns > 512:
+                            continue
+                        p.set_ring_weights(hw.ring_weights(ns, lmax))
+                    a1 = p.map2alm(f)
+                    d = p.alm2map(a1) - f
+                    r[wname] = {"map_rel_l2": float(d.norm() / f.norm()),
+                                "map_rel_linf": float(d.abs().max() / f.abs().max()),
+                                "alm_rel_l2": float((a1 - a).abs().norm() / a.abs().norm())}
+                out[f"nside{ns}_lmax{lmax}"] = r
+            del a, f
+    torch.cuda.empty_cache()
     return out
 
 

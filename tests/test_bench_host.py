@@ -130,6 +130,11 @@ def test_table_roofline_takes_the_slower_kernel(monkeypatch):
 def test_cuda_core_table_and_recompute_rooflines(monkeypatch):
     monkeypatch.setattr(bench, "kernel_traffic", lambda k: None)
     plan = _Plan()
+    # a stage that ran no launch in the timed region gets no bandwidth
+    st = _stages(6.0, 5.0, tc=False)
+    st["synthesis_operand_pack"] = {"ms_per_step": 0.0, "ms_per_launch": 0.0, "launches": 0}
+    bench.legendre_roofline(plan, st, table=False)
+    assert "hbm_gbs_algorithmic" not in st["synthesis_operand_pack"]
     r = bench.legendre_roofline(plan, _stages(6.0, 5.0, tc=False), table=True)
     assert r["kernel"] == "k_legendre_analysis<table>" and r["bound"] == "hbm"
     st = _stages(40.0, 50.0, tc=False)
