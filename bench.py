@@ -640,6 +640,11 @@ def legendre_roofline(plan, stages, table: bool, value_bytes: int = 4):
 
 
 SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
+# slots with a plan-time lambda table on the tensor cores (the Nside-2048
+# tables would not fit the cap: those slots recompute lambda) and channels
+# per batch: one table stream or one recurrence serves every request of a batch
+SERVE_TABLE_NSIDES = (64, 128, 256, 512, 1024)
+SERVE_BATCH = {64: 64, 128: 64, 256: 64, 512: 64, 1024: 64, 2048: 32}
 
 
 def _serve_stream(dev, pools, rate, duration, drain_s, seed):
@@ -650,8 +655,8 @@ def _serve_stream(dev, pools, rate, duration, drain_s, seed):
     for r in reqs:
         m, a = pools[r.nside]
         r.x = m[: r.nch] if r.op == "map2alm" else a[: r.nch]
-    ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=(64, 128, 256, 512))
-    srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=2)
+    ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=SERVE_TABLE_NSIDES, batch_channels=SERVE_BATCH)
+    srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=1)
     wall = srv.run(reqs, drain_s=drain_s)
     torch.cuda.synchronize(dev)
     for ss in srv.slots.values():
@@ -691,13 +696,18 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
     out = {"offered_rps": len(reqs) / duration, "duration_s": duration, "drain_limit_s": drain_s,
            "wall_s": wall, "served_rps": rep["served"] / wall, "transforms_per_s": served_ch / wall,
            "unserved": len(reqs) - rep["served"] - rep["errors"], "batches": srv.batches,
+           "requests_per_batch": rep["served"] / max(srv.batches, 1), "evictions": srv.evictions,
            "peak_slot_bytes": srv.peak_bytes, **rep,
-           "lambda": "tables for Nside <= 512, recomputed above"}
-    # the same served requests, one at a time
+           "lambda": f"tensor-core tables for Nside in {list(SERVE_TABLE_NSIDES)}, recomputed above",
+           "batch_channels": SERVE_BATCH}
+    # the same served requests, one at a time (one launch per request, the
+    # same kinds of plan)
     plans, outs = {}, {}
     for r in served:
         if r.nside not in plans:
-            plans[r.nside] = hpx.Plan(r.nside, r.lmax, r.lmax, 32, "f32", lambda_table=r.nside <= 512, device=dev)
+            tab = r.nside in SERVE_TABLE_NSIDES
+            plans[r.nside] = hpx.Plan(r.nside, r.lmax, r.lmax, 32, "f32", lambda_table=tab, tensor_cores=tab,
+                                      device=dev)
             outs[r.nside] = (plans[r.nside].empty_alm(), plans[r.nside].empty_map())
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -714,6 +724,7 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
     torch.cuda.empty_cache()
     out["one_at_a_time_same_requests"] = {"requests": len(served), "seconds": t1,
                                           "transforms_per_s": served_ch / t1 if t1 > 0 else None}
+    out["batched_gain_same_requests"] = (served_ch / wall) / (served_ch / t1) if t1 > 0 and wall > 0 else None
     sreqs, ssrv, swall = _serve_stream(dev, pools, sustainable_rate, duration, drain_s, SEED + 6)
     srep = latency_report(sreqs)
     out["sustainable_point"] = {"offered_rps": len(sreqs) / duration, "wall_s": swall, "batches": ssrv.batches,

@@ -92,8 +92,14 @@ struct hpx_plan_s {
   int tc_fmt;          // 16-bit operand format: 0 FP16, 1 BF16
   float tc_sfac_a, tc_sfac_s;  // channel-scale bound factors of the current transform
   void* d_tab_lo;      // 16-bit x3: remainders of the row table
-  void* d_gt;          // analysis operand Gt[m][group][rows][row width] (per transform)
-  void* d_at;          // synthesis operand At[chunk][rows][row width] (per transform)
+  void* d_gt;          // analysis operand Gt[cgroup][m][group][rows][row width] (per transform), one
+                       // region per channel group of an analysis launch
+  long long gt_group_elems;  // elements of one channel group's Gt region
+  int gt_groups;       // channel groups Gt holds
+  void* d_at;          // synthesis operand At[group][chunk][rows][row width] (per transform), one
+                       // region per channel group of a synthesis launch
+  long long at_group_elems;  // elements of one channel group's At region
+  int at_groups;       // channel groups At holds (the plan's nbatch over channels per group)
   long long* d_achunk; // [mmax+2] first At chunk of each m
   unsigned* d_bmax;    // [2][bmax_stride] 16-bit modes: largest operand component per channel, of
                        // the analysis (spectra) and of the synthesis (alm), apart so that an
@@ -209,7 +215,11 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s);
 // buffers and TMA descriptors; per launch of up to tc_channels_per_launch
 // channels from b0, an operand pack and then the tile kernel.  The analysis
 // pack reads the ring spectra and the tile kernel writes alm; the synthesis
-// pack reads alm and the tile kernel writes the ring workspace d_F.
+// pack reads alm and the tile kernel writes the ring workspace d_F.  Both
+// stages pack every channel group of the transform (launch_pack_tc /
+// launch_pack_at_tc per group, into the group's Gt / At region) and then run
+// one tile launch over all of them (launch_tile_tc / launch_synthesis_tc with
+// nb up to the plan's nbatch).
 // The 16-bit dtypes (HPX_F32_BF16 ...) have only this path; their tables
 // (row and column, hi and for x3 lo parts) are built here too.
 int tc_columns(int nbatch, int cap);  // N of a tile for nbatch channels, at most cap per launch

@@ -199,7 +199,9 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e != cudaSuccess) return e;
-  if (p->tc_nn_a) {  // tensor cores: operand pack (stage 4), then the tile kernel (stage 1), per channel chunk
+  if (p->tc_nn_a) {
+    // tensor cores: the operand pack of every channel group (stage 4), then
+    // one tile launch over all groups (stage 1)
     const int cp = tc_channels_per_launch(p, false);
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
@@ -207,12 +209,12 @@ static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool 
         *n = 1;
         return launch_pack_tc(p, b0, nb, weighted, s);
       });
-      if (e == cudaSuccess)
-        e = staged(p, 1, s, [&](int* n) {
-          *n = 1;
-          return launch_tile_tc(p, static_cast<float*>(alm), b0, nb, mfac, s);
-        });
     }
+    if (e == cudaSuccess)
+      e = staged(p, 1, s, [&](int* n) {
+        *n = 1;
+        return launch_tile_tc(p, static_cast<float*>(alm), 0, p->nbatch, mfac, s);
+      });
     return e;
   }
   return staged(p, 1, s,
@@ -223,7 +225,10 @@ template <typename T>
 static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool weighted, double mfac,
                                  cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (p->tc_nn_s) {  // tensor cores: operand pack (stage 5), then the tile kernel (stage 2), per channel chunk
+  if (p->tc_nn_s) {
+    // tensor cores: the operand pack of every channel group (stage 5), then
+    // one tile launch over all groups (stage 2), whose groups share each
+    // lambda block through L2
     const int cp = tc_channels_per_launch(p, true);
     for (int b0 = 0; b0 < p->nbatch && e == cudaSuccess; b0 += cp) {
       const int nb = p->nbatch - b0 < cp ? p->nbatch - b0 : cp;
@@ -231,12 +236,12 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
         *n = p->tc_mode ? 2 : 1;  // 16-bit operands: channel maxima, then the pack
         return launch_pack_at_tc(p, static_cast<const float*>(alm), b0, nb, mfac, s);
       });
-      if (e == cudaSuccess)
-        e = staged(p, 2, s, [&](int* n) {
-          *n = 1;
-          return launch_synthesis_tc(p, b0, nb, s);
-        });
     }
+    if (e == cudaSuccess)
+      e = staged(p, 2, s, [&](int* n) {
+        *n = 1;
+        return launch_synthesis_tc(p, 0, p->nbatch, s);
+      });
   } else {
     e = staged(p, 2, s, [&](int* n) { return launch_synthesis<T>(p, static_cast<const T*>(alm), mfac, s, n); });
   }

@@ -577,6 +577,8 @@ struct TcArgs {
   int* status;
   int m0, nm;               // the launch's m range (analysis: blockIdx.y = m - m0)
   long long tbase;          // table element at row 0 of the lambda descriptor (streamed blocks)
+  int ncg;                  // synthesis: channel groups of the launch (CTAs per pair tile)
+  long long cg_rows;        // synthesis: operand rows between consecutive groups' At regions
 };
 
 // One CTA: a 128-row tile of one m, all channels of the launch.
@@ -623,8 +625,15 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   // analysis: m; synthesis: the first of the CTA's nq consecutive m
   const int m = a.m0 + blockIdx.y * MQ;
+  // the ncg channel groups of one tile (pairs: synthesis; l: analysis) are
+  // consecutive CTAs, so they stream the same lambda blocks at about the same
+  // time and all but the first read them from L2
+  const int ptile = (int)blockIdx.x / a.ncg;
+  const int cgi = (int)blockIdx.x % a.ncg;
+  const int b0 = a.b0 + cgi * (C2N / 2);           // first channel of the CTA
+  const int nbl = min(C2N / 2, a.nb - cgi * (C2N / 2));  // its channels
   const int nq = SYN ? min(MQ, a.m0 + a.nm - m) : 1;
-  const int l0 = m + kTcTile * blockIdx.x;  // analysis tile
+  const int l0 = m + kTcTile * ptile;  // analysis tile
   if (!SYN && l0 > a.lmax) return;          // whole CTA, before any shared state
 
   extern __shared__ unsigned char smem_raw[];
@@ -669,7 +678,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const int ls = a.lstart[mg];
       act = ls <= l0;
       ra = (int)((a.off[mg] - a.tbase) / KW) + (l0 - ls);
-      rb = (int)(mg * RB);
+      rb = (int)(mg * RB + cgi * a.cg_rows);
     }
     bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) wcount[warp] = __popc(bal);
@@ -679,12 +688,12 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     int n = 0, ra = 0, rb = 0;
     if (lane < nq) {
       const int mj = m + lane;
-      const long long mT = (long long)mj * a.ngroup + blockIdx.x;
+      const long long mT = (long long)mj * a.ngroup + ptile;
       const int ls = a.lstart[mT];
       if (ls <= a.lmax) {
         n = (a.lmax - ls) / KW + 1;
         ra = (int)((a.off[mT] - a.tbase) / KW);
-        rb = (int)((a.achunk[mj] + (ls - mj) / KW) * RB);
+        rb = (int)((a.achunk[mj] + (ls - mj) / KW) * RB + cgi * a.cg_rows);
       }
     }
     qna[lane] = n;
@@ -808,12 +817,36 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     };
     auto drain = [&](int buf) {  // warp-collective
       const uint32_t c0 = trow + (uint32_t)(buf * S::kBuf);
-      if constexpr (SYN) {
+      if constexpr (MODE != 0) {
+        // 16-bit modes: QB loads of 16 columns in flight per wait (the
+        // accumulator read back in few round trips)
+        constexpr int NQ = SYN ? NN / 16 : C2N / 16;
+        constexpr int QB = SYN ? (NQ < 4 ? NQ : 4) : (NQ < 2 ? NQ : 2);
+#pragma unroll
+        for (int q0 = 0; q0 < NQ; q0 += QB) {
+          uint32_t v1[QB][16], v2[SYN ? 1 : QB][16];
+#pragma unroll
+          for (int u = 0; u < QB; ++u) {
+            tmem_ld16(c0 + (uint32_t)((q0 + u) * 16), v1[u]);
+            if constexpr (!SYN) tmem_ld16(c0 + (uint32_t)(C2N + (q0 + u) * 16), v2[u]);
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < QB; ++u)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if constexpr (SYN)
+                sum[(q0 + u) * 16 + j] += __uint_as_float(v1[u][j]);
+              else
+                sum[(q0 + u) * 16 + j] += __uint_as_float(odd ? v2[u][j] : v1[u][j]);
+            }
+        }
+      } else if constexpr (SYN) {
 #pragma unroll
         for (int q = 0; q < NN / 16; ++q) {
           uint32_t v1[16], v2[16];
           tmem_ld16(c0 + (uint32_t)(q * 16), v1);
-          if (MODE == 0) tmem_ld16(c0 + (uint32_t)(NN + q * 16), v2);
+          tmem_ld16(c0 + (uint32_t)(NN + q * 16), v2);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j) sum[q * 16 + j] += col(v1, v2, j);
@@ -824,10 +857,8 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
           uint32_t s1[16], s2[16], a1[16], a2[16];
           tmem_ld16(c0 + (uint32_t)(q * 16), s1);
           tmem_ld16(c0 + (uint32_t)(C2N + q * 16), a1);
-          if (MODE == 0) {
-            tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
-            tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
-          }
+          tmem_ld16(c0 + (uint32_t)(NN + q * 16), s2);
+          tmem_ld16(c0 + (uint32_t)(NN + C2N + q * 16), a2);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j) sum[q * 16 + j] += odd ? col(a1, a2, j) : col(s1, s2, j);
@@ -845,7 +876,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
           for (int cc = 0; cc < 8; ++cc) {
             const int c = 8 * g + cc;
-            const float inv = a.lscale / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
+            const float inv = a.lscale / chan_scale(a.bmax, b0 + c, a.sfac);  // a power of two
             const float er = sum[2 * c] * inv, ei = sum[2 * c + 1] * inv;
             const float orr = sum[C2N + 2 * c] * inv, oi = sum[C2N + 2 * c + 1] * inv;
             v[4 * cc] = __float_as_uint(er + orr);
@@ -941,7 +972,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       if constexpr (SYN && MQ > 1) {
         // the staged outputs of the CTA's nq m, 4 channels (16 columns) at a
         // time; per ring and channel the nq values are adjacent in F
-        const int p = blockIdx.x * 128 + t;
+        const int p = ptile * 128 + t;
         const int ys = p == a.npair - 1 ? -1 : a.nring - 1 - p;
         float2* F = reinterpret_cast<float2*>(a.out);
         const long long mstride = a.mmax + 1;
@@ -954,12 +985,12 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int c = 4 * cg + cc;
-            if (p < a.npair && c < a.nb) {
+            if (p < a.npair && c < nbl) {
 #pragma unroll
               for (int side = 0; side < 2; ++side) {
                 const int y = side ? ys : p;
                 if (y < 0) continue;
-                const long long at = ((long long)(a.b0 + c) * a.nring + y) * mstride + m;
+                const long long at = ((long long)(b0 + c) * a.nring + y) * mstride + m;
                 float2 w[MQ];
 #pragma unroll
                 for (int j = 0; j < MQ; ++j)
@@ -977,18 +1008,18 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       } else if constexpr (SYN) {
         // north ring p: E + O; its mirror (none for the equator): E - O
-        const int p = blockIdx.x * 128 + t;
+        const int p = ptile * 128 + t;
         if (p < a.npair) {
           const int ys = p == a.npair - 1 ? -1 : a.nring - 1 - p;
           float2* F = reinterpret_cast<float2*>(a.out);
           const long long mstride = a.mmax + 1;
 #pragma unroll
           for (int c = 0; c < C2N / 2; ++c) {
-            if (c < a.nb) {
-              const float inv = a.lscale / chan_scale(a.bmax, a.b0 + c, a.sfac);  // a power of two
+            if (c < nbl) {
+              const float inv = a.lscale / chan_scale(a.bmax, b0 + c, a.sfac);  // a power of two
               const float er = sum[2 * c] * inv, ei = sum[2 * c + 1] * inv;
               const float orr = sum[C2N + 2 * c] * inv, oi = sum[C2N + 2 * c + 1] * inv;
-              const long long fb = (long long)(a.b0 + c) * a.nring;
+              const long long fb = (long long)(b0 + c) * a.nring;
               F[(fb + p) * mstride + m] = make_float2(er + orr, ei + oi);
               if (ys >= 0) F[(fb + ys) * mstride + m] = make_float2(er - orr, ei - oi);
             }
@@ -998,11 +1029,11 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const long long base = alm_base(a.lmax, m);
         // P_l (FP32) times powers of two (mfac, the table and channel scales)
         const float scale = a.coef_pf[base + l] * (m > 0 ? (float)a.mfac : 1.f) * a.lscale;
-        float2* out = reinterpret_cast<float2*>(a.out) + (long long)a.b0 * a.nalm + base + l;
+        float2* out = reinterpret_cast<float2*>(a.out) + (long long)b0 * a.nalm + base + l;
 #pragma unroll
         for (int c = 0; c < C2N / 2; ++c)
-          if (c < a.nb) {  // the channel scale last: exact unless the result itself is subnormal
-            const float inv = 1.f / chan_scale(a.bmax, a.b0 + c, a.sfac);
+          if (c < nbl) {  // the channel scale last: exact unless the result itself is subnormal
+            const float inv = 1.f / chan_scale(a.bmax, b0 + c, a.sfac);
             out[(long long)c * a.nalm] = make_float2(scale * sum[2 * c] * inv, scale * sum[2 * c + 1] * inv);
           }
       }
@@ -1073,6 +1104,8 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.m0 = 0;
   a.nm = p->mmax + 1;
   a.tbase = 0;
+  a.ncg = 1;
+  a.cg_rows = 0;
   return a;
 }
 
@@ -1092,8 +1125,9 @@ cudaError_t pack_gt_cp(const hpx_plan_s* p, int b0, int nb, bool use_w, cudaStre
   const size_t smem = (size_t)kPackM * pack_slab(pack_rows(x3)) + kPackC * sizeof(float);
   cudaError_t e = allow_max_smem(k_pack_gt<E>);
   if (e != cudaSuccess) return e;
+  E* gt = (E*)p->d_gt + (long long)(b0 / CP) * p->gt_group_elems;  // the group's region
   k_pack_gt<E><<<dim3(p->ngroup, (p->mmax + kPackM) / kPackM, CP / kPackC), 256, smem, s>>>(
-      (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, (E*)p->d_gt, p->npair, p->nring, p->ngroup,
+      (const float2*)p->d_spec, (const float2*)p->d_etab, p->d_ring, gt, p->npair, p->nring, p->ngroup,
       p->nspec, p->mmax, 4 * CP, b0, nb, use_w ? 1 : 0, x3 ? 1 : 0, p->tc_mode ? p->d_bmax : nullptr, p->tc_sfac_a);
   return cudaGetLastError();
 }
@@ -1102,8 +1136,9 @@ template <int CP, typename E>
 cudaError_t pack_at_cp(const hpx_plan_s* p, const float* alm, int b0, int nb, double mfac, cudaStream_t s) {
   constexpr int KW = Elt<E>::kw;
   const int nchunk0 = p->lmax / KW + 1;  // chunks of m = 0, the most
+  E* at = (E*)p->d_at + (long long)(b0 / CP) * p->at_group_elems;  // the group's region
   k_pack_at<CP, E><<<dim3((nchunk0 + 128 / KW - 1) / (128 / KW), p->mmax + 1), 128, 0, s>>>(
-      (const float2*)alm, p->d_coef_pf, p->d_achunk, (E*)p->d_at, p->lmax, p->mmax, p->nalm, b0, nb, (float)mfac,
+      (const float2*)alm, p->d_coef_pf, p->d_achunk, at, p->lmax, p->mmax, p->nalm, b0, nb, (float)mfac,
       p->tc_mode == 2 ? 1 : 0, p->tc_mode ? p->d_bmax + p->bmax_stride : nullptr, p->tc_sfac_s);
   return cudaGetLastError();
 }
@@ -1116,11 +1151,16 @@ cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac
   if (e != cudaSuccess) return e;
   const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(SYN ? p->tm_at : p->tm_gt);
   constexpr int MQ = tc_mq<NN, SYN, MODE>();
-  const dim3 grid(SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile, (r.nm + MQ - 1) / MQ);
+  // all channel groups of [b0, b0 + nb) in one launch, the groups' operand
+  // regions (At or Gt) at_group_elems / gt_group_elems apart
+  const int ncg = (nb + CP - 1) / CP;
+  const dim3 grid((SYN ? p->nptile : (p->lmax + kTcTile) / kTcTile) * ncg, (r.nm + MQ - 1) / MQ);
   TcArgs a = tc_args(p, SYN, out, b0, nb, mfac);
   a.m0 = r.m0;
   a.nm = r.nm;
   a.tbase = r.tbase;
+  a.ncg = ncg;
+  a.cg_rows = (SYN ? p->at_group_elems : p->gt_group_elems) / (MODE == 0 ? 32 : 64);
   k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, MODE>::kSmem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(r.tmA), *reinterpret_cast<const CUtensorMap*>(r.tmAlo), *tmB, a);
   return cudaGetLastError();
@@ -1230,6 +1270,20 @@ cudaError_t absmax(hpx_plan_s const* p, const float2* x, long long n, long long 
 
 }  // namespace
 
+// Channels per synthesis CTA (the tile's N is 4 per channel); a synthesis of
+// more channels runs their groups side by side in one launch.
+#ifndef HPX_TC_SYN_CHANNELS
+#define HPX_TC_SYN_CHANNELS 16
+#endif
+constexpr int kSynChannels = HPX_TC_SYN_CHANNELS;
+// Channels per analysis CTA: 32 for FP32 operands (3xTF32), else this.
+#ifndef HPX_TC_ANA_CHANNELS
+#define HPX_TC_ANA_CHANNELS 64
+#endif
+constexpr int kAnaChannels = HPX_TC_ANA_CHANNELS;
+static_assert(kAnaChannels == 8 || kAnaChannels == 16 || kAnaChannels == 32 || kAnaChannels == 64, "analysis group");
+static_assert(kSynChannels == 8 || kSynChannels == 16 || kSynChannels == 32, "synthesis channel group");
+
 int tc_columns(int nbatch, int cap) {
   int cp = 8;
   while (cp < nbatch && cp < cap) cp *= 2;
@@ -1242,14 +1296,16 @@ size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mo
   if (mode < 0) return 0;
   const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
   const size_t npair = 2 * (size_t)nside, ngroup = (npair + kw - 1) / kw, nptile = (npair + 127) / 128;
-  const size_t nna = (size_t)tc_columns(nbatch, mode ? 64 : 32), nns = (size_t)tc_columns(nbatch, 32);
+  const size_t nna = (size_t)tc_columns(nbatch, mode ? kAnaChannels : 32), nns = (size_t)tc_columns(nbatch, kSynChannels);
   size_t chunks = 0, rows = 0;
   for (int m = 0; m <= mmax; ++m) {
     chunks += (size_t)((lmax - m) / kw + 1);
     rows += (size_t)(lmax + 1 - m) + kTcTile;
   }
-  size_t b = es * (size_t)(mmax + 1) * ngroup * nna * kw * parts  // Gt
-             + es * chunks * nns * kw * parts                     // At
+  const size_t cps = nns / 4, groups = ((size_t)nbatch + cps - 1) / cps;
+  const size_t cpa = nna / 4, groups_a = ((size_t)nbatch + cpa - 1) / cpa;
+  size_t b = es * (size_t)(mmax + 1) * ngroup * nna * kw * parts * groups_a  // Gt, one region per channel group
+             + es * chunks * nns * kw * parts * groups                       // At, likewise
              + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * (nptile + ngroup) +
              sizeof(long long) * (mmax + 2) + 2 * sizeof(unsigned) * nbatch;
   if (host_tables) return b + 2 * parts * (size_t(1) << 30);      // staging buffers at the default size
@@ -1343,7 +1399,7 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;  // FP32 plans: FP16
   const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
   const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
-  const int nna = tc_columns(p->nbatch, mode ? 64 : 32), nns = tc_columns(p->nbatch, 32);
+  const int nna = tc_columns(p->nbatch, mode ? kAnaChannels : 32), nns = tc_columns(p->nbatch, kSynChannels);
   const int rba = mode == 2 ? 2 * nna : nna, rbs = mode == 2 ? 2 * nns : nns;
   auto dalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
@@ -1372,8 +1428,10 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
     e = cudaMemcpy(p->d_tab_off, roff.data(), sizeof(long long) * nent, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
   }
-  // analysis operand
-  e = dalloc(&p->d_gt, (size_t)es * (p->mmax + 1) * p->ngroup * rba * kw);
+  // analysis operand, one region per channel group
+  p->gt_group_elems = (long long)(p->mmax + 1) * p->ngroup * rba * kw;
+  p->gt_groups = (p->nbatch + nna / 4 - 1) / (nna / 4);
+  e = dalloc(&p->d_gt, (size_t)es * p->gt_group_elems * p->gt_groups);
   if (e != cudaSuccess) return e;
   // synthesis operand: chunk offsets of each m, then At
   std::vector<long long> ach(p->mmax + 2);
@@ -1382,7 +1440,9 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   e = dalloc((void**)&p->d_achunk, sizeof(long long) * (p->mmax + 2));
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_achunk, ach.data(), sizeof(long long) * (p->mmax + 2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = dalloc(&p->d_at, (size_t)es * ach[p->mmax + 1] * rbs * kw);
+  p->at_group_elems = (long long)ach[p->mmax + 1] * rbs * kw;
+  p->at_groups = (p->nbatch + nns / 4 - 1) / (nns / 4);
+  if (e == cudaSuccess) e = dalloc(&p->d_at, (size_t)es * p->at_group_elems * p->at_groups);
   p->bmax_stride = p->nbatch;
   if (e == cudaSuccess) e = dalloc((void**)&p->d_bmax, 2 * sizeof(unsigned) * p->nbatch);
   if (e != cudaSuccess) return e;
@@ -1496,8 +1556,9 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
   }
-  if (!encode_rows128(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * rba, nna, es) ||
-      !encode_rows128(p->tm_at, p->d_at, (unsigned long long)ach[p->mmax + 1] * rbs, nns, es)) {
+  if (!encode_rows128(p->tm_gt, p->d_gt, (unsigned long long)(p->mmax + 1) * p->ngroup * rba * p->gt_groups, nna,
+                      es) ||
+      !encode_rows128(p->tm_at, p->d_at, (unsigned long long)ach[p->mmax + 1] * rbs * p->at_groups, nns, es)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return cudaErrorInvalidValue;
   }
