@@ -520,7 +520,9 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
 // ---------------------------------------------------------------------------
 // MODE 0: FP32 operands, 3xTF32 with the remainders made in shared memory;
 // MODE 1: one 16-bit product; MODE 2: 16-bit x3 (stored hi and lo parts).
-template <int NN, int MODE>
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : 2 * pow2_at_least((x + 1) / 2); }
+
+template <int NN, bool SYN, int MODE>
 struct TcShape {
   static constexpr int kA = kTcTile * 128;  // lambda tile bytes: 128 rows x 128 bytes
   static constexpr int kG = NN * 128;       // B tile bytes (Gt or At)
@@ -532,12 +534,20 @@ struct TcShape {
   static constexpr int kLo = MODE == 0 && !kLoTmem ? kA : 0;
   static constexpr int kBuf = MODE == 0 ? 2 * NN : NN;  // TMEM columns of one block accumulator
   static constexpr int kLoCol = 2 * kBuf;                // first TMEM column of the remainder buffers
-  static constexpr int kTmemCols = kLoTmem ? 256 : 2 * kBuf;
+  // MODE 1 (one 16-bit product, error bounds of 1e-2 / 2e-3): each m
+  // accumulates over its whole K range in its own TMEM region, drained once
+  // (the accumulator's truncation, ~1e-6, is far inside those bounds); the
+  // other modes accumulate each K block alone and add it into FP32 registers
+  static constexpr bool kFullK = MODE == 1;
+  // synthesis m per CTA (see tc_mq)
+  static constexpr int kMq = (SYN && MODE != 0) ? (kFullK ? (NN <= 64 ? 4 : 2) : (NN == 32 ? 4 : 2)) : 1;
+  static constexpr int kTmemCols = kFullK ? pow2_at_least(kMq * NN) : kLoTmem ? 256 : 2 * kBuf;
+  static constexpr int kAlloc = (!kFullK && kMq > 1) ? pow2_at_least(kTmemCols + kMq * NN) : kTmemCols;
   // two CTAs per SM where half the tensor memory and half the shared memory
   // (with at least two stages) suffice: the second CTA's prologue, tail and
   // epilogue then overlap the first's streaming
   static constexpr int kStages2 = (110 * 1024 - 2 * kLo) / kStage;
-  static constexpr int kCtas = (kTmemCols <= 256 && kStages2 >= 2 && NN <= 64) ? 2 : 1;
+  static constexpr int kCtas = (kAlloc <= 256 && kStages2 >= 2 && (NN <= 64 || kFullK)) ? 2 : 1;
   static constexpr int kBudget = kCtas == 2 ? 110 * 1024 : 200 * 1024;
   static constexpr int kNStage = (kBudget - 2 * kLo) / kStage < 8 ? (kBudget - 2 * kLo) / kStage : 8;
   static constexpr size_t kSmem =
@@ -555,9 +565,8 @@ constexpr int kTcThreads = 192;  // warps 0-3 split and drain, warp 4 copies, wa
 // kMq NN staging columns fit beside the accumulators within the allocation.
 template <int NN, bool SYN, int MODE>
 __host__ __device__ constexpr int tc_mq() {
-  return (SYN && MODE != 0) ? (NN == 32 ? 4 : 2) : 1;
+  return TcShape<NN, SYN, MODE>::kMq;
 }
-__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : 2 * pow2_at_least((x + 1) / 2); }
 
 struct TcArgs {
   const long long* off;     // analysis: row table offsets [m][group]; synthesis: column table [m][p tile]
@@ -610,18 +619,20 @@ struct TcArgs {
 // warp-collective tcgen05.ld stays convergent), waits for what it started,
 // and the CTA records the timeout.
 template <int NN, bool SYN, int MODE>
-__global__ void __launch_bounds__(kTcThreads, TcShape<NN, MODE>::kCtas)
+__global__ void __launch_bounds__(kTcThreads, TcShape<NN, SYN, MODE>::kCtas)
 k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  using S = TcShape<NN, MODE>;
+  using S = TcShape<NN, SYN, MODE>;
+  constexpr bool FK = S::kFullK;
   constexpr int NS = S::kNStage, C2N = NN / 2, KW = MODE == 0 ? 32 : 64;
   constexpr int RB = MODE == 2 ? 2 * NN : NN;  // operand rows per K block in memory
   constexpr int NSUM = SYN ? NN : C2N;
   constexpr int MQ = tc_mq<NN, SYN, MODE>();
-  constexpr int kStageCol = S::kTmemCols;  // first staging column (MQ > 1)
-  constexpr int kAlloc = MQ > 1 ? pow2_at_least(S::kTmemCols + MQ * NN) : S::kTmemCols;
+  constexpr int kStageCol = S::kTmemCols;  // first staging column (MQ > 1, not FK)
+  constexpr int kAlloc = S::kAlloc;
   static_assert(kAlloc <= (S::kCtas == 2 ? 256 : 512), "tensor memory");
-  static_assert(NN % 32 == 0 && NN <= (MODE == 0 || SYN ? 128 : 256), "N tile");
+  static_assert(NN % 32 == 0 && NN <= (MODE == 0 || (SYN && !FK) ? 128 : 256), "N tile");
+  static_assert(MQ <= 4, "per-m lists hold 4 entries");
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   // analysis: m; synthesis: the first of the CTA's nq consecutive m
   const int m = a.m0 + blockIdx.y * MQ;
@@ -706,9 +717,9 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 2; ++b) {  // FK: accf[0..3] (acce follows accf), one arrival each
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
+      mbar_init(&acce[b], FK ? 1 : 128);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -770,6 +781,32 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const uint32_t id2 = (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(2 * NN >> 3) << 17) | ((128u >> 4) << 24);
       const uint32_t id1 = (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(NN >> 3) << 17) | ((128u >> 4) << 24);
       bool issued_any = false;
+      if constexpr (FK) {
+        // every block of the CTA's j-th m accumulates into TMEM region j;
+        // accf[j] completes once the products of its last block have
+        int j = 0, kj = 0;
+        for (int k = 0; k < na; ++k) {
+          const int s = k % NS;
+          if constexpr (SYN)
+            while (kj >= qna[j]) {
+              kj = 0;
+              ++j;
+            }
+          if (!wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(j * NN);
+          const uint32_t aL = smem_u32(sL(s)), aB = smem_u32(sB(s));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t off = 32u * q;
+            umma_f16(d, sdesc_sw128(aL + off), sdesc_sw128(aB + off), id1, (kj > 0 || q > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
+          ++kj;
+          if (kj == (SYN ? qna[j] : na)) umma_commit(&accf[j]);
+          issued_any = true;
+        }
+      } else
       for (int k = 0; k < na; ++k) {
         const int s = k % NS, b = k & 1;
         if (!wait_phase(MODE == 0 ? &conv[s] : &full[s], (uint32_t)(k / NS) & 1u, abort_flag, true)) break;
@@ -899,77 +936,166 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
       }
     };
-    advance(0);  // leading m without blocks
-    bool alive = true;
-    for (int k = 0; k < na; ++k) {
-      const int s = k % NS, b = k & 1;
-      if (MODE == 0) {
-        if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
-        if constexpr (S::kLoTmem) alive = __all_sync(0xffffffffu, alive);  // the TMEM store is warp-collective
-        if (alive) {
-          // elementwise, so the swizzle does not matter; consecutive threads
-          // take consecutive 16-byte words.  Remainder buffer b was last read
-          // by block k-2's products, complete since this thread drained that
-          // block in the previous iteration.
-          if constexpr (S::kLoTmem) {
-            // this thread's row t of the tile (128 bytes, 16-byte chunks
-            // permuted by the swizzle: chunk c at c ^ (t mod 8)) to TMEM lane t
-            const unsigned char* row = sL(s) + t * 128;
-            uint32_t v[32];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const float4 q = tf32_rem4(*reinterpret_cast<const float4*>(row + ((c ^ (t & 7)) << 4)));
-              v[4 * c] = __float_as_uint(q.x);
-              v[4 * c + 1] = __float_as_uint(q.y);
-              v[4 * c + 2] = __float_as_uint(q.z);
-              v[4 * c + 3] = __float_as_uint(q.w);
+    if constexpr (FK) {
+      // one wait for the CTA's products: accf of its last m with blocks (a
+      // commit tracks every product the issuing thread started before it)
+      int last = -1;
+      if constexpr (SYN) {
+        for (int j = 0; j < MQ; ++j)
+          if (qna[j] > 0) last = j;
+      } else {
+        last = na > 0 ? 0 : -1;
+      }
+      if (last >= 0) {
+        bool ok = wait_phase(&accf[last], 0u, abort_flag, true);
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+    } else {
+      advance(0);  // leading m without blocks
+      bool alive = true;
+      for (int k = 0; k < na; ++k) {
+        const int s = k % NS, b = k & 1;
+        if (MODE == 0) {
+          if (alive) alive = wait_phase(&full[s], (uint32_t)(k / NS) & 1u, abort_flag, true);
+          if constexpr (S::kLoTmem) alive = __all_sync(0xffffffffu, alive);  // the TMEM store is warp-collective
+          if (alive) {
+            // elementwise, so the swizzle does not matter; consecutive threads
+            // take consecutive 16-byte words.  Remainder buffer b was last read
+            // by block k-2's products, complete since this thread drained that
+            // block in the previous iteration.
+            if constexpr (S::kLoTmem) {
+              // this thread's row t of the tile (128 bytes, 16-byte chunks
+              // permuted by the swizzle: chunk c at c ^ (t mod 8)) to TMEM lane t
+              const unsigned char* row = sL(s) + t * 128;
+              uint32_t v[32];
+  #pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                const float4 q = tf32_rem4(*reinterpret_cast<const float4*>(row + ((c ^ (t & 7)) << 4)));
+                v[4 * c] = __float_as_uint(q.x);
+                v[4 * c + 1] = __float_as_uint(q.y);
+                v[4 * c + 2] = __float_as_uint(q.z);
+                v[4 * c + 3] = __float_as_uint(q.w);
+              }
+              tmem_st32(trow + (uint32_t)(S::kLoCol + b * 32), v);
+            } else {
+              const float4* x = reinterpret_cast<const float4*>(sL(s));
+              float4* xlo = reinterpret_cast<float4*>(sLlo(s, b));
+  #pragma unroll
+              for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
             }
-            tmem_st32(trow + (uint32_t)(S::kLoCol + b * 32), v);
-          } else {
-            const float4* x = reinterpret_cast<const float4*>(sL(s));
-            float4* xlo = reinterpret_cast<float4*>(sLlo(s, b));
-#pragma unroll
-            for (int j = 0; j < S::kA / 2048; ++j) xlo[j * 128 + t] = tf32_rem4(x[j * 128 + t]);
+            const float4* y = reinterpret_cast<const float4*>(sB(s));
+            float4* ylo = reinterpret_cast<float4*>(sBlo(s));
+  #pragma unroll
+            for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if constexpr (S::kLoTmem) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&conv[s]);
           }
-          const float4* y = reinterpret_cast<const float4*>(sB(s));
-          float4* ylo = reinterpret_cast<float4*>(sBlo(s));
-#pragma unroll
-          for (int j = 0; j < S::kG / 2048; ++j) ylo[j * 128 + t] = tf32_rem4(y[j * 128 + t]);
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if constexpr (S::kLoTmem) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          mbar_arrive(&conv[s]);
+        }
+        if (k >= 1) {  // drain block k-1 while block k's products run
+          bool ok = alive && wait_phase(&accf[b ^ 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
+          ok = __all_sync(0xffffffffu, ok);
+          if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain(b ^ 1);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acce[b ^ 1]);
+          } else {
+            alive = false;
+          }
+          advance(k);
         }
       }
-      if (k >= 1) {  // drain block k-1 while block k's products run
-        bool ok = alive && wait_phase(&accf[b ^ 1], (uint32_t)((k - 1) >> 1) & 1u, abort_flag, true);
+      if (na > 0) {  // the last block
+        bool ok = alive && wait_phase(&accf[(na - 1) & 1], (uint32_t)((na - 1) >> 1) & 1u, abort_flag, true);
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          drain(b ^ 1);
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          mbar_arrive(&acce[b ^ 1]);
-        } else {
-          alive = false;
+          drain((na - 1) & 1);
         }
-        advance(k);
       }
+      advance(na);
     }
-    if (na > 0) {  // the last block
-      bool ok = alive && wait_phase(&accf[(na - 1) & 1], (uint32_t)((na - 1) >> 1) & 1u, abort_flag, true);
-      ok = __all_sync(0xffffffffu, ok);
-      if (ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        drain((na - 1) & 1);
-      }
-    }
-    advance(na);
     __syncwarp();
     // the CTA-wide sync below orders these writes after every role finished;
     // results are written only if no wait expired anywhere in the CTA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (*abort_flag == 0) {
-      if constexpr (SYN && MQ > 1) {
+      if constexpr (FK && SYN) {
+        // region j: E (columns 0 .. C2N-1) and O (C2N .. NN-1) of the CTA's
+        // j-th m (zero if it had no blocks); north ring p gets E + O, its
+        // mirror E - O, a ring's nq values adjacent in F
+        const int p = ptile * 128 + t;
+        const int ys = p == a.npair - 1 ? -1 : a.nring - 1 - p;
+        float2* F = reinterpret_cast<float2*>(a.out);
+        const long long mstride = a.mmax + 1;
+#pragma unroll 1
+        for (int cg = 0; cg < C2N / 16; ++cg) {  // 8 channels: 16 E and 16 O columns
+          uint32_t e[MQ][16], o[MQ][16];
+#pragma unroll
+          for (int j = 0; j < MQ; ++j) {
+            tmem_ld16(trow + (uint32_t)(j * NN + 16 * cg), e[j]);
+            tmem_ld16(trow + (uint32_t)(j * NN + C2N + 16 * cg), o[j]);
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const int c = 8 * cg + cc;
+            if (p < a.npair && c < nbl) {
+              const float inv = a.lscale / chan_scale(a.bmax, b0 + c, a.sfac);  // a power of two
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const int y = side ? ys : p;
+                if (y < 0) continue;
+                const long long at = ((long long)(b0 + c) * a.nring + y) * mstride + m;
+                float2 w[MQ];
+#pragma unroll
+                for (int j = 0; j < MQ; ++j) {
+                  const bool has = qna[j] > 0;
+                  const float er = has ? __uint_as_float(e[j][2 * cc]) * inv : 0.f;
+                  const float ei = has ? __uint_as_float(e[j][2 * cc + 1]) * inv : 0.f;
+                  const float orr = has ? __uint_as_float(o[j][2 * cc]) * inv : 0.f;
+                  const float oi = has ? __uint_as_float(o[j][2 * cc + 1]) * inv : 0.f;
+                  w[j] = side ? make_float2(er - orr, ei - oi) : make_float2(er + orr, ei + oi);
+                }
+                if (nq == MQ && (at % MQ) == 0) {  // whole pieces: 16 or 32 bytes
+                  float4* dd = reinterpret_cast<float4*>(F + at);
+#pragma unroll
+                  for (int h = 0; h < MQ / 2; ++h)
+                    dd[h] = make_float4(w[2 * h].x, w[2 * h].y, w[2 * h + 1].x, w[2 * h + 1].y);
+                } else {
+                  for (int j = 0; j < nq; ++j) F[at + j] = w[j];
+                }
+              }
+            }
+          }
+        }
+      } else if constexpr (FK) {
+        // the row's own parity: A columns for odd l - m, S columns for even
+        const long long base = alm_base(a.lmax, m);
+        const bool row = l <= a.lmax && na > 0;
+        const float scale = l <= a.lmax ? a.coef_pf[base + l] * (m > 0 ? (float)a.mfac : 1.f) * a.lscale : 0.f;
+        float2* out = reinterpret_cast<float2*>(a.out) + (long long)b0 * a.nalm + base + l;
+#pragma unroll 1
+        for (int cg = 0; cg < C2N / 16; ++cg) {
+          uint32_t sv[16], av[16];
+          tmem_ld16(trow + (uint32_t)(16 * cg), sv);
+          tmem_ld16(trow + (uint32_t)(C2N + 16 * cg), av);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const int c = 8 * cg + cc;
+            if (l <= a.lmax && c < nbl) {
+              const float inv = 1.f / chan_scale(a.bmax, b0 + c, a.sfac);
+              const float re = row ? __uint_as_float(odd ? av[2 * cc] : sv[2 * cc]) : 0.f;
+              const float im = row ? __uint_as_float(odd ? av[2 * cc + 1] : sv[2 * cc + 1]) : 0.f;
+              out[(long long)c * a.nalm] = make_float2(scale * re * inv, scale * im * inv);
+            }
+          }
+        }
+      } else if constexpr (SYN && MQ > 1) {
         // the staged outputs of the CTA's nq m, 4 channels (16 columns) at a
         // time; per ring and channel the nq values are adjacent in F
         const int p = ptile * 128 + t;
@@ -1161,7 +1287,7 @@ cudaError_t tile_cp(const hpx_plan_s* p, float* out, int b0, int nb, double mfac
   a.tbase = r.tbase;
   a.ncg = ncg;
   a.cg_rows = (SYN ? p->at_group_elems : p->gt_group_elems) / (MODE == 0 ? 32 : 64);
-  k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, MODE>::kSmem, s>>>(
+  k_legendre_tc<NN, SYN, MODE><<<grid, kTcThreads, TcShape<NN, SYN, MODE>::kSmem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(r.tmA), *reinterpret_cast<const CUtensorMap*>(r.tmAlo), *tmB, a);
   return cudaGetLastError();
 }
@@ -1184,7 +1310,7 @@ cudaError_t tile_t(const hpx_plan_s* p, float* out, int b0, int nb, double mfac,
                    cudaStream_t s) {
   switch (p->tc_mode) {
     case 0: if constexpr (CP <= 32) return tile_cp<CP, SYN, 0>(p, out, b0, nb, mfac, r, s); break;
-    case 1: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 1>(p, out, b0, nb, mfac, r, s); break;
+    case 1: return tile_cp<CP, SYN, 1>(p, out, b0, nb, mfac, r, s);  // up to 64 channels either way
     case 2: if constexpr (CP <= 32 || !SYN) return tile_cp<CP, SYN, 2>(p, out, b0, nb, mfac, r, s); break;
   }
   return cudaErrorInvalidValue;
@@ -1197,7 +1323,7 @@ cudaError_t tile_nn(const hpx_plan_s* p, float* out, int b0, int nb, double mfac
     case 32: return tile_t<8, SYN>(p, out, b0, nb, mfac, r, s);
     case 64: return tile_t<16, SYN>(p, out, b0, nb, mfac, r, s);
     case 128: return tile_t<32, SYN>(p, out, b0, nb, mfac, r, s);
-    case 256: if constexpr (!SYN) return tile_t<64, SYN>(p, out, b0, nb, mfac, r, s); break;
+    case 256: return tile_t<64, SYN>(p, out, b0, nb, mfac, r, s);  // (a 64-channel synthesis: mode 1 only)
   }
   return cudaErrorInvalidValue;
 }
@@ -1296,7 +1422,8 @@ size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mo
   if (mode < 0) return 0;
   const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
   const size_t npair = 2 * (size_t)nside, ngroup = (npair + kw - 1) / kw, nptile = (npair + 127) / 128;
-  const size_t nna = (size_t)tc_columns(nbatch, mode ? kAnaChannels : 32), nns = (size_t)tc_columns(nbatch, kSynChannels);
+  const size_t nna = (size_t)tc_columns(nbatch, mode ? kAnaChannels : 32),
+               nns = (size_t)tc_columns(nbatch, mode == 1 ? 64 : kSynChannels);
   size_t chunks = 0, rows = 0;
   for (int m = 0; m <= mmax; ++m) {
     chunks += (size_t)((lmax - m) / kw + 1);
@@ -1399,7 +1526,10 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;  // FP32 plans: FP16
   const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
   const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
-  const int nna = tc_columns(p->nbatch, mode ? kAnaChannels : 32), nns = tc_columns(p->nbatch, kSynChannels);
+  // synthesis channels per CTA: 64 for one 16-bit product (accumulated over
+  // all K in tensor memory), else kSynChannels
+  const int nna = tc_columns(p->nbatch, mode ? kAnaChannels : 32),
+            nns = tc_columns(p->nbatch, mode == 1 ? 64 : kSynChannels);
   const int rba = mode == 2 ? 2 * nna : nna, rbs = mode == 2 ? 2 * nns : nns;
   auto dalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
@@ -1594,6 +1724,7 @@ cudaError_t launch_pack_at_tc(hpx_plan_s* p, const float* alm, int b0, int nb, d
     case 32: return pack_at_t<8>(p, alm, b0, nb, mfac, s);
     case 64: return pack_at_t<16>(p, alm, b0, nb, mfac, s);
     case 128: return pack_at_t<32>(p, alm, b0, nb, mfac, s);
+    case 256: return pack_at_t<64>(p, alm, b0, nb, mfac, s);
     default: return cudaErrorInvalidValue;
   }
 }

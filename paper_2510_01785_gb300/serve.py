@@ -75,6 +75,7 @@ class Server:
         self.peak_bytes = 0
         self.batches = 0
         self.evictions = 0
+        self.known_bytes: dict = {}  # measured device bytes of a built slot, by geometry
         self.finished: list = []
 
     def capacity(self, nside: int, lmax: int) -> int:
@@ -117,7 +118,10 @@ class Server:
         if len(self.slots[key]) >= self.max_slots:
             return None
         cap_ch = self.capacity(key[0], key[1])
-        need = self.ex.slot_bytes(key[0], key[1], cap_ch)
+        # the executor's estimate is an upper bound (it cannot know which
+        # Legendre values are significant); once a slot of this geometry has
+        # been built, its measured size is used instead
+        need = self.known_bytes.get(key) or self.ex.slot_bytes(key[0], key[1], cap_ch)
         while self.bytes + need > self.cap:  # evict idle slots of other geometries, least recently used first
             idle = [s for k, ss in self.slots.items() if k != key for s in ss if not s.busy]
             if not idle:
@@ -129,6 +133,7 @@ class Server:
             self.evictions += 1
         handle = self.ex.new_slot(key[0], key[1], cap_ch)
         s = Slot(key=key, nbytes=self.ex.handle_bytes(handle), handle=handle, last_used=now)
+        self.known_bytes[key] = s.nbytes
         self.slots[key].append(s)
         self.bytes += s.nbytes
         self.peak_bytes = max(self.peak_bytes, self.bytes)

@@ -203,3 +203,30 @@ def test_evictions_are_counted():
         drain(srv)
     # two slots fit: 256 evicts 64's (LRU), 64 evicts 128's, 512 evicts 256's
     assert srv.evictions == 3 and srv.bytes <= 20
+
+
+class OverEstimating(FakeExecutor):
+    """Estimates 3x the bytes a slot turns out to hold."""
+
+    def slot_bytes(self, nside, lmax, max_ch):
+        return 3 * super().slot_bytes(nside, lmax, max_ch)
+
+    def handle_bytes(self, h):
+        return h["bytes"] // 3  # what the built slot holds
+
+
+def test_admission_uses_measured_slot_sizes_once_known():
+    """The first slot of a geometry is admitted on the estimate; later ones
+    on the size the first one measured, so an over-estimate does not keep
+    evicting slots that in fact fit."""
+    ex = OverEstimating(bytes_per_slot=10)
+    srv = Server(ex, hbm_cap_bytes=35, max_channels=32, max_slots_per_key=1, clock=Clock())
+    for i, ns in enumerate([64, 128, 256]):  # estimates 30 each: every new geometry evicts the other slot
+        srv.submit(Request(rid=i, op="map2alm", nside=ns, nch=4))
+        drain(srv)
+    assert srv.evictions == 2 and srv.known_bytes[(64, 191)] == 10
+    for i, ns in enumerate([64, 128, 256, 64, 128]):  # now known: 10 each, all three fit 35
+        srv.submit(Request(rid=10 + i, op="map2alm", nside=ns, nch=4))
+        drain(srv)
+    assert srv.evictions == 2  # no more: re-admitting 64 and 128 fits beside 256
+    assert len([s for ss in srv.slots.values() for s in ss]) == 3
