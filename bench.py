@@ -697,6 +697,8 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
            "wall_s": wall, "served_rps": rep["served"] / wall, "transforms_per_s": served_ch / wall,
            "unserved": len(reqs) - rep["served"] - rep["errors"], "batches": srv.batches,
            "requests_per_batch": rep["served"] / max(srv.batches, 1), "evictions": srv.evictions,
+           "slot_builds_by_nside": {k[0]: n for k, n in srv.builds.items()},
+           "slot_bytes_by_nside": {k[0]: b for k, b in srv.known_bytes.items()},
            "peak_slot_bytes": srv.peak_bytes, **rep,
            "lambda": f"tensor-core tables for Nside in {list(SERVE_TABLE_NSIDES)}, recomputed above",
            "batch_channels": SERVE_BATCH}

@@ -76,6 +76,7 @@ class Server:
         self.batches = 0
         self.evictions = 0
         self.known_bytes: dict = {}  # measured device bytes of a built slot, by geometry
+        self.builds: collections.Counter = collections.Counter()  # slots built, by geometry
         self.finished: list = []
 
     def capacity(self, nside: int, lmax: int) -> int:
@@ -134,6 +135,7 @@ class Server:
         handle = self.ex.new_slot(key[0], key[1], cap_ch)
         s = Slot(key=key, nbytes=self.ex.handle_bytes(handle), handle=handle, last_used=now)
         self.known_bytes[key] = s.nbytes
+        self.builds[key] += 1
         self.slots[key].append(s)
         self.bytes += s.nbytes
         self.peak_bytes = max(self.peak_bytes, self.bytes)
