@@ -644,7 +644,10 @@ SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
 # tables would not fit the cap: those slots recompute lambda) and channels
 # per batch: one table stream or one recurrence serves every request of a batch
 SERVE_TABLE_NSIDES = (64, 128, 256, 512, 1024)
-SERVE_BATCH = {64: 64, 128: 64, 256: 64, 512: 32, 1024: 32, 2048: 16}  # all six slots fit 120 GB together
+# (a slot holds at least one request of up to 32 channels: 32 everywhere keeps
+# all six slots, 119.7 GB, resident under the cap; wider small-Nside slots
+# pushed the total over it and made slots evict and rebuild one another)
+SERVE_BATCH = {64: 32, 128: 32, 256: 32, 512: 32, 1024: 32, 2048: 32}
 
 
 def _serve_stream(dev, pools, rate, duration, drain_s, seed):
