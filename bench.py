@@ -643,7 +643,7 @@ SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
 # slots with a plan-time lambda table on the tensor cores (the Nside-2048
 # tables would not fit the cap: those slots recompute lambda) and channels
 # per batch: one table stream or one recurrence serves every request of a batch
-SERVE_TABLE_NSIDES = (64, 128, 256, 512, 1024)
+SERVE_TABLE_NSIDES = (64, 128, 256, 1024)  # (all six slots, tabled 512 included, came to 120.1 GB)
 # (a slot holds at least one request of up to 32 channels: 32 everywhere keeps
 # all six slots, 119.7 GB, resident under the cap; wider small-Nside slots
 # pushed the total over it and made slots evict and rebuild one another)

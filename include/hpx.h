@@ -358,6 +358,15 @@ hpx_status hpx_plan_set_ring_weights(hpx_plan plan, const double* w, int n);
  * it themselves. */
 hpx_status hpx_plan_device_status(hpx_plan plan);
 
+/* Test support for the bounded waits (no counterpart in the paper).  While
+ * withhold is nonzero, the tensor-core tile kernels of the plan's transforms
+ * issue none of their copies, so the first wait of each CTA for a copy runs
+ * out after its limit (1 s), with no copy or product in flight; the CTA
+ * frees its tensor memory, writes no output and records HPX_ERR_TIMEOUT,
+ * which the next hpx_plan_device_status returns.  Transforms that have no
+ * tile kernel (CUDA-core plans) are unaffected.  0 restores normal work. */
+hpx_status hpx_plan_test_withhold_copies(hpx_plan plan, int withhold);
+
 /* Pixel layouts (Sec. III-B).
  *   HPX_RING   : rings north to south, pixels by increasing longitude.
  *   HPX_NESTED : face f (0..11) times nside^2 plus the Morton (Z-order)

@@ -27,6 +27,7 @@ SIGNATURES = {
     "hpx_plan_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_P)]),
     "hpx_plan_create_ex": (_I, [_I, _I, _I, _I, _I, _U, ctypes.POINTER(_P)]),
     "hpx_plan_create_ooc": (_I, [_I, _I, _I, _I, _I, _SZ, ctypes.POINTER(_P)]),
+    "hpx_plan_test_withhold_copies": (_I, [_P, _I]),
     "hpx_plan_host_bytes": (_SZ, [_P]),
     "hpx_plan_destroy": (_I, [_P]),
     "hpx_map2alm": (_I, [_P, _P, _P, _P]),

@@ -137,6 +137,7 @@ struct hpx_plan_s {
   void* copy_stream;   // cudaStream_t
   void* stage_events;  // cudaEvent_t[4]: copied[2], free[2]
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
+  int test_withhold;   // test support: tile kernels issue no copies (hpx_plan_test_withhold_copies)
   double w_max;        // largest ring weight (4 pi / Npix unless set)
   size_t bytes;
 };

@@ -759,6 +759,15 @@ hpx_status hpx_plan_device_status(hpx_plan plan) {
   return read_status(plan);
 }
 
+hpx_status hpx_plan_test_withhold_copies(hpx_plan plan, int withhold) {
+  if (!plan) {
+    set_error("null plan");
+    return HPX_ERR_INVALID;
+  }
+  plan->test_withhold = withhold ? 1 : 0;
+  return HPX_OK;
+}
+
 hpx_status hpx_map2alm_host_async(hpx_plan plan, const void* host_map, void* host_alm, hpx_stream_t stream) {
   return host_call_async(plan, host_map, host_alm, stream, true);
 }

@@ -586,6 +586,7 @@ struct TcArgs {
   int* status;
   int m0, nm;               // the launch's m range (analysis: blockIdx.y = m - m0)
   long long tbase;          // table element at row 0 of the lambda descriptor (streamed blocks)
+  int withhold;             // test support: issue no copies, so the first wait for one runs out
   int ncg;                  // synthesis: channel groups of the launch (CTAs per pair tile)
   long long cg_rows;        // synthesis: operand rows between consecutive groups' At regions
 };
@@ -746,7 +747,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   if (warp == 4) {
     // ---- copies: block k into stage k % NS once block k - NS's products are done
     int issued = 0;
-    if (lane == 0) {
+    if (lane == 0 && !a.withhold) {
       constexpr uint32_t kBytes = MODE == 2 ? 2 * (S::kA + S::kG) : S::kA + S::kG;
       int j = 0, kj = 0;  // synthesis: m of the CTA and block within it
       for (int k = 0; k < na; ++k) {
@@ -1232,6 +1233,7 @@ TcArgs tc_args(const hpx_plan_s* p, bool syn, float* out, int b0, int nb, double
   a.tbase = 0;
   a.ncg = 1;
   a.cg_rows = 0;
+  a.withhold = p->test_withhold;
   return a;
 }
 
