@@ -735,6 +735,53 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
     out["sustainable_point"] = {"offered_rps": len(sreqs) / duration, "wall_s": swall, "batches": ssrv.batches,
                                 "transforms_per_s": sum(r.nch for r in sreqs if r.t_done is not None) / swall,
                                 **srep}
+    out["batching_by_nside"] = _batching_gain(dev, pools)
+    return out
+
+
+def _batching_gain(dev, pools) -> dict:
+    """Per geometry: a burst of requests (1-32 channels, both ops) arriving
+    together, served by the batching server and then one launch per request
+    on the same kind of plan; transforms/s of each and their ratio."""
+    import torch
+
+    import paper_2510_01785_gb300 as hpx
+    from paper_2510_01785_gb300.serve import GpuExecutor, Server, make_requests
+    out = {}
+    for ns in SERVE_MIX:
+        nreq = 48 if ns <= 512 else 12
+        reqs = make_requests(SEED + 70 + ns, 1e6, nreq / 1e6, {ns: 1.0}, max_channels=32)
+        for r in reqs:
+            m, a = pools[r.nside]
+            r.x = m[: r.nch] if r.op == "map2alm" else a[: r.nch]
+        ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=SERVE_TABLE_NSIDES, batch_channels=SERVE_BATCH)
+        srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=1)
+        srv.run(reqs[:2], drain_s=60.0)  # builds the slot (and warms it) outside the timing
+        for r in reqs:
+            r.t_arrival, r.t_done, r.y = 0.0, None, None
+        torch.cuda.synchronize(dev)
+        b0 = srv.batches
+        wall = srv.run(reqs, drain_s=120.0)
+        torch.cuda.synchronize(dev)
+        nbat = srv.batches - b0
+        for ss in srv.slots.values():
+            for sl in ss:
+                ex.free_slot(sl.handle)
+        tab = ns in SERVE_TABLE_NSIDES
+        with hpx.Plan(ns, 3 * ns - 1, 3 * ns - 1, 32, "f32", lambda_table=tab, tensor_cores=tab, device=dev) as p:
+            oa, om = p.empty_alm(), p.empty_map()
+            for r in reqs[:2]:
+                (p.map2alm_n(r.nch, r.x, oa) if r.op == "map2alm" else p.alm2map_n(r.nch, r.x, om))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for r in reqs:
+                (p.map2alm_n(r.nch, r.x, oa) if r.op == "map2alm" else p.alm2map_n(r.nch, r.x, om))
+                torch.cuda.synchronize(dev)
+            t1 = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        ch = sum(r.nch for r in reqs)
+        out[ns] = {"requests": len(reqs), "batches": nbat, "batched_transforms_per_s": ch / wall,
+                   "one_at_a_time_transforms_per_s": ch / t1, "gain": t1 / wall}
     return out
 
 

@@ -406,6 +406,234 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
 }
 
 // ---------------------------------------------------------------------------
+// analysis with the roles split (FP32 plans recomputing lambda)
+// ---------------------------------------------------------------------------
+// The same sums as k_legendre_analysis, but the first half of the CTA's
+// threads (producers, one chain each) only run the FP64 recurrence, writing
+// each block of LB values of mu into one of two shared-memory slots, and the
+// second half (consumers, consumer i serving producer i's chain) contract the
+// blocks, add the warps' and the cluster's partial sums and write alm.  The
+// producers do not wait for the sums, so the FP64 pipe is not left idle
+// while a CTA contracts and reduces.
+//   producer -> consumer: mbarrier full[slot], one arrival per producer,
+//     waited with a time limit;
+//   among the consumers: named barrier 1;
+//   slot reuse and the cluster sums: every thread takes one cluster-barrier
+//     phase per block -- consumers once their block's partials are written,
+//     producers for block b just before they write block b + 2 into b's
+//     slot (the phase that frees it) -- and one more at the end.
+// Deterministic order, as the one-role kernel.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once the phase of `bar` with this parity has completed; false after 1 s
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned i = 1; i < (1u << 31); ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if ((i & 63u) == 0 && global_ns() - t0 > 1000000000ull) break;
+  }
+  return false;
+}
+
+template <int CP>
+size_t analysis_ws_smem(int nch) {
+  constexpr int C2N = 2 * CP;
+  return 32 + sizeof(float) * ((size_t)nch * 2 * C2N + 2 * (size_t)nch * MuStride<float>::v + 2 * LB * C2N);
+}
+
+template <int CP>
+__global__ void __launch_bounds__(1024)
+k_legendre_analysis_ws(const float2* __restrict__ spec, float* __restrict__ alm, const RingInfo* __restrict__ rings,
+                       const float2* __restrict__ etab, const double* __restrict__ coef_c,
+                       const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
+                       const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
+                       int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w,
+                       double mfac, int* __restrict__ status) {
+  using T = float;
+  using V = float2;
+  constexpr int C2N = 2 * CP;
+  constexpr int CPL = LaneTile<C2N>::CPL, LPL = LaneTile<C2N>::LPL, NCQ = C2N / CPL;
+  constexpr int MS = MuStride<T>::v;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank(), csize = (int)cluster.num_blocks();
+  const int nch = blockDim.x >> 1;  // chains of the CTA = producer threads = consumer threads
+  const int t = threadIdx.x, lane = t & 31;
+  const bool producer = t < nch;
+  const int ct = producer ? t : t - nch;  // the chain this thread serves
+  const int cw = ct >> 5, nw = nch >> 5;  // its warp among its role's warps
+  const int m = blockIdx.y;
+  const int p = (cw * csize + crank) * 32 + lane;
+  const bool active = p < npair;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);  // [2]
+  T* sG = reinterpret_cast<T*>(smem_raw + 32);              // [nch][2][C2N]  S, A
+  T* sMu = sG + (size_t)nch * 2 * C2N;                      // [2][nch][MS]; a consumer warp's partials in its rows
+  T* sC = sMu + (size_t)2 * nch * MS;                       // [2][LB][C2N]
+
+  double z = 0.0, s0 = 0.0, s1 = 0.0;
+  int lc = INT_MAX;
+  if (active) {
+    const long long ci = (long long)m * npair + p;
+    z = rings[p].z;
+    lc = lc_tab[ci];
+    s0 = mu0_tab[ci];
+    s1 = mu1_tab[ci];
+    if (lc > lmax) lc = INT_MAX;
+  }
+  if (producer) {  // the chain's S and A coefficients, as in the one-role kernel
+    T* g = sG + (size_t)ct * 2 * C2N;
+    if (active) {
+      const int ys = (p == npair - 1) ? -1 : nring - 1 - p;
+      const RingInfo Rn = rings[p];
+      for (int c = 0; c < CP; ++c) {
+        V gn = cmk<V>(0, 0), gs = cmk<V>(0, 0);
+        if (c < nb && lc != INT_MAX) {
+          gn = ring_coef<T>(spec, etab, Rn, m, b0 + c, nspec, use_w);
+          if (ys >= 0) gs = ring_coef<T>(spec, etab, rings[ys], m, b0 + c, nspec, use_w);
+        }
+        const V S = cadd(gn, gs), A = csub(gn, gs);
+        g[2 * c] = S.x;
+        g[2 * c + 1] = S.y;
+        g[C2N + 2 * c] = A.x;
+        g[C2N + 2 * c + 1] = A.y;
+      }
+    } else {
+      for (int c = 0; c < 2 * C2N; ++c) g[c] = (T)0;
+    }
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[0])), "r"(nch));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[1])), "r"(nch));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the last barrier of all the CTA's threads before the roles part
+
+  const long long base = alm_base(lmax, m);
+  const int nblk = (lmax - m) / LB + 1;
+  if (producer) {
+    // ---- the recurrence, block by block into slot b mod 2
+    const double* cl = coef_c + base;
+    double mu1 = 0.0, mu2 = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      const int lb0 = m + b * LB, slot = b & 1;
+      if (b >= 2) cluster.sync();  // phase b - 2: every consumer is done with block b - 2, which used this slot
+      T* myMu = sMu + ((size_t)slot * nch + ct) * MS;
+      if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
+#pragma unroll
+        for (int i4 = 0; i4 < LB; i4 += 4) {
+          double c4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) c4[u] = (lb0 + i4 + u <= lmax) ? cl[lb0 + i4 + u] : 0.0;
+          T v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int l = lb0 + i4 + u;
+            double mu = fma(c4[u] * z, mu1, -mu2);
+            if (l == lc) {
+              mu = s1;
+              mu1 = s0;
+            }
+            mu2 = mu1;
+            mu1 = mu;
+            v[u] = to_real<T>(mu);
+          }
+          *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < LB; i += 4) *reinterpret_cast<float4*>(myMu + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[slot])) : "memory");
+    }
+    for (int b = nblk > 2 ? nblk - 2 : 0; b < nblk; ++b) cluster.sync();  // the phases of the last blocks
+  } else {
+    // ---- contraction and sums
+    const int lq = lane / NCQ, cq = lane % NCQ;
+    const int l0 = lq * LPL, c0 = cq * CPL;
+    bool timed_out = false;
+    for (int b = 0; b < nblk; ++b) {
+      const int lb0 = m + b * LB, slot = b & 1;
+      const bool ok = mbar_wait_bounded(&full[slot], (uint32_t)(b >> 1) & 1u);
+      if (!ok) timed_out = true;
+      T* muS = sMu + (size_t)slot * nch * MS;
+      T acc[LPL][CPL];
+#pragma unroll
+      for (int a = 0; a < LPL; ++a)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[a][c] = (T)0;
+      if (__all_sync(0xffffffffu, ok) && __any_sync(0xffffffffu, lc < lb0 + LB)) {
+        const T* muw = muS + (size_t)(cw * 32) * MS + l0;
+        const T* gw = sG + (size_t)(cw * 32) * 2 * C2N + c0;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          T mv[LPL], gsv[CPL], gav[CPL];
+#pragma unroll
+          for (int a = 0; a < LPL; ++a) mv[a] = muw[(size_t)j * MS + a];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            gsv[c] = gw[(size_t)j * 2 * C2N + c];
+            gav[c] = gw[(size_t)j * 2 * C2N + C2N + c];
+          }
+#pragma unroll
+          for (int a = 0; a < LPL; ++a) {
+            const bool odd = ((l0 + a) & 1) != 0;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) acc[a][c] = fma(mv[a], odd ? gav[c] : gsv[c], acc[a][c]);
+          }
+        }
+      }
+      // this warp's partials over its own 32 mu rows of the slot, which only it has read
+      T* wp = muS + (size_t)(cw * 32) * MS;
+      __syncwarp();
+#pragma unroll
+      for (int a = 0; a < LPL; ++a)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) wp[(l0 + a) * C2N + c0 + c] = acc[a][c];
+      asm volatile("bar.sync 1, %0;" ::"r"(nch) : "memory");  // the consumers' partials are in
+      T* cpart = sC + slot * LB * C2N;
+      for (int o = ct; o < LB * C2N; o += nch) {
+        T s = (T)0;
+        for (int w = 0; w < nw; ++w) s += muS[(size_t)(w * 32) * MS + o];
+        cpart[o] = s;
+      }
+      cluster.sync();  // phase b
+      {
+        const int nout = LB * C2N;
+        const int per = (nout + csize - 1) / csize;
+        const int q_end = min(nout, (crank + 1) * per);
+        for (int q = crank * per + ct; q < q_end; q += nch) {
+          const int part = q & 1, li = (q >> 1) % LB, bb = (q >> 1) / LB;
+          const int l = lb0 + li;
+          if (l > lmax || bb >= nb) continue;
+          const int o = li * C2N + 2 * bb + part;
+          T s = (T)0;
+          for (int r = 0; r < csize; ++r) s += cluster.map_shared_rank(cpart, r)[o];
+          alm[((long long)(b0 + bb) * nalm + base + l) * 2 + part] =
+              (T)(coef_p[base + l] * (m > 0 ? mfac : 1.0) * (double)s);
+        }
+      }
+    }
+    if (timed_out) atomicExch(status, (int)HPX_ERR_TIMEOUT);
+  }
+  cluster.sync();  // peers may still read this CTA's partials
+}
+
+// ---------------------------------------------------------------------------
 // synthesis
 // ---------------------------------------------------------------------------
 // One thread per chain (m, pair): E_m = sum over even l - m of a_lm lambda_lm,
@@ -618,8 +846,83 @@ static int pick_cp(const hpx_plan_s* p) {
   return cp;
 }
 
+// The split-role analysis (FP32, lambda recomputed): clusters as for the
+// one-role kernel, twice the threads (producers and consumers).
+template <int CP>
+static cudaError_t launch_analysis_ws_cp(const hpx_plan_s* p, float* alm, bool use_w, double mfac, cudaStream_t s,
+                                         int* nlaunch) {
+  int nthr, csize;
+  analysis_shape(p->npair, &nthr, &csize);
+  const size_t smem = analysis_ws_smem<CP>(nthr);
+  cudaError_t e = allow_max_smem(k_legendre_analysis_ws<CP>);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize, p->mmax + 1, 1);
+  cfg.blockDim = dim3(2 * nthr, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
+    const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
+    e = cudaLaunchKernelEx(&cfg, k_legendre_analysis_ws<CP>, (const float2*)p->d_spec, alm,
+                           (const RingInfo*)p->d_ring, (const float2*)p->d_etab, (const double*)p->d_coef_c,
+                           (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
+                           (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
+                           use_w ? 1 : 0, mfac, p->d_status);
+    if (e != cudaSuccess) return e;
+    ++*nlaunch;
+  }
+  return cudaGetLastError();
+}
+
+// Channels per launch of the split-role analysis: the largest power of two
+// up to cap with which two CTAs fit an SM (0 if none).  With one CTA per SM
+// (512 chains per CTA at Nside 2048, or wide channel groups) every cluster
+// barrier idles the SM's FP64 pipe, and the one-role kernel, whose CTAs
+// share SMs with other clusters', is faster (252 against 295 ms at Nside
+// 2048 / lmax 6143 / 4 channels).
+static int pick_cp_ws(int npair, int cap) {
+  int nthr, csize;
+  analysis_shape(npair, &nthr, &csize);
+  if (nthr > 256) return 0;
+  for (int cp = cap; cp >= 1; cp /= 2) {
+    size_t sm = 0;
+    switch (cp) {
+      case 1: sm = analysis_ws_smem<1>(nthr); break;
+      case 2: sm = analysis_ws_smem<2>(nthr); break;
+      case 4: sm = analysis_ws_smem<4>(nthr); break;
+      case 8: sm = analysis_ws_smem<8>(nthr); break;
+      default: sm = analysis_ws_smem<16>(nthr); break;
+    }
+    if (sm <= 112 * 1024) return cp;
+  }
+  return 0;
+}
+
 template <typename T>
 cudaError_t launch_analysis(const hpx_plan_s* p, T* alm, bool use_w, double mfac, cudaStream_t s, int* nlaunch) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32 recomputing lambda: the split-role kernel, unless its channel
+    // groups would need more launches (each reruns the recurrence)
+    if (!p->d_tab) {
+      const int cp_one = pick_cp<T>(p), cp_ws = pick_cp_ws(p->npair, cp_one);
+      if (cp_ws > 0 && (p->nbatch + cp_ws - 1) / cp_ws == (p->nbatch + cp_one - 1) / cp_one) {
+        switch (cp_ws) {
+          case 1: return launch_analysis_ws_cp<1>(p, alm, use_w, mfac, s, nlaunch);
+          case 2: return launch_analysis_ws_cp<2>(p, alm, use_w, mfac, s, nlaunch);
+          case 4: return launch_analysis_ws_cp<4>(p, alm, use_w, mfac, s, nlaunch);
+          case 8: return launch_analysis_ws_cp<8>(p, alm, use_w, mfac, s, nlaunch);
+          default: return launch_analysis_ws_cp<16>(p, alm, use_w, mfac, s, nlaunch);
+        }
+      }
+    }
+  }
   switch (pick_cp<T>(p)) {
     case 1: return launch_analysis_sel<T, 1>(p, alm, use_w, mfac, s, nlaunch);
     case 2: return launch_analysis_sel<T, 2>(p, alm, use_w, mfac, s, nlaunch);
