@@ -640,25 +640,41 @@ def legendre_roofline(plan, stages, table: bool, value_bytes: int = 4):
 
 
 SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
-# slots with a plan-time lambda table on the tensor cores (the Nside-2048
-# tables would not fit the cap: those slots recompute lambda) and channels
-# per batch: one table stream or one recurrence serves every request of a batch
-SERVE_TABLE_NSIDES = (64, 128, 256, 1024)  # (all six slots, tabled 512 included, came to 120.1 GB)
-# (a slot holds at least one request of up to 32 channels: 32 everywhere keeps
-# all six slots, 119.7 GB, resident under the cap; wider small-Nside slots
-# pushed the total over it and made slots evict and rebuild one another)
-SERVE_BATCH = {64: 32, 128: 32, 256: 32, 512: 32, 1024: 32, 2048: 32}
+# slots with a plan-time lambda table on the tensor cores, and slots that
+# recompute lambda per batch into streamed blocks contracted on the tensor
+# cores (one FP64 recurrence per batch, whatever its channels); channels per
+# batch: one table stream or one recurrence serves every request of a batch
+SERVE_TABLE_NSIDES = (64, 128, 256)
+SERVE_STREAMED_NSIDES = (512, 1024, 2048)
+# (all six slots resident under the cap: the Nside-1024 table slot alone
+# held 74 GB, and a streamed Nside-2048 slot of 32 channels about 59 GB)
+SERVE_BATCH = {64: 64, 128: 64, 256: 64, 512: 64, 1024: 64, 2048: 32}
+
+
+def _serve_plan(hpx, ns, nch, dev):
+    """A plan of the serving slot's kind for Nside ns (lmax = 3 ns - 1)."""
+    lmax = 3 * ns - 1
+    if ns in SERVE_STREAMED_NSIDES:
+        return hpx.Plan(ns, lmax, lmax, nch, "f32", streamed=True, device=dev)
+    tab = ns in SERVE_TABLE_NSIDES
+    return hpx.Plan(ns, lmax, lmax, nch, "f32", lambda_table=tab, tensor_cores=tab, device=dev)
+
+
+def _serve_executor(dev):
+    from paper_2510_01785_gb300.serve import GpuExecutor
+    return GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=SERVE_TABLE_NSIDES, batch_channels=SERVE_BATCH,
+                       streamed_nsides=SERVE_STREAMED_NSIDES)
 
 
 def _serve_stream(dev, pools, rate, duration, drain_s, seed):
     import torch
 
-    from paper_2510_01785_gb300.serve import GpuExecutor, Server, make_requests
+    from paper_2510_01785_gb300.serve import Server, make_requests
     reqs = make_requests(seed, rate, duration, SERVE_MIX, max_channels=32)
     for r in reqs:
         m, a = pools[r.nside]
         r.x = m[: r.nch] if r.op == "map2alm" else a[: r.nch]
-    ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=SERVE_TABLE_NSIDES, batch_channels=SERVE_BATCH)
+    ex = _serve_executor(dev)
     srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=1)
     wall = srv.run(reqs, drain_s=drain_s)
     torch.cuda.synchronize(dev)
@@ -703,16 +719,15 @@ def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_r
            "slot_builds_by_nside": {k[0]: n for k, n in srv.builds.items()},
            "slot_bytes_by_nside": {k[0]: b for k, b in srv.known_bytes.items()},
            "peak_slot_bytes": srv.peak_bytes, **rep,
-           "lambda": f"tensor-core tables for Nside in {list(SERVE_TABLE_NSIDES)}, recomputed above",
+           "lambda": f"tensor-core tables for Nside in {list(SERVE_TABLE_NSIDES)}, recomputed into streamed "
+                     f"tensor-core blocks for {list(SERVE_STREAMED_NSIDES)}",
            "batch_channels": SERVE_BATCH}
     # the same served requests, one at a time (one launch per request, the
     # same kinds of plan)
     plans, outs = {}, {}
     for r in served:
         if r.nside not in plans:
-            tab = r.nside in SERVE_TABLE_NSIDES
-            plans[r.nside] = hpx.Plan(r.nside, r.lmax, r.lmax, 32, "f32", lambda_table=tab, tensor_cores=tab,
-                                      device=dev)
+            plans[r.nside] = _serve_plan(hpx, r.nside, 32, dev)
             outs[r.nside] = (plans[r.nside].empty_alm(), plans[r.nside].empty_map())
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -746,7 +761,7 @@ def _batching_gain(dev, pools) -> dict:
     import torch
 
     import paper_2510_01785_gb300 as hpx
-    from paper_2510_01785_gb300.serve import GpuExecutor, Server, make_requests
+    from paper_2510_01785_gb300.serve import Server, make_requests
     out = {}
     for ns in SERVE_MIX:
         nreq = 48 if ns <= 512 else 12
@@ -754,7 +769,7 @@ def _batching_gain(dev, pools) -> dict:
         for r in reqs:
             m, a = pools[r.nside]
             r.x = m[: r.nch] if r.op == "map2alm" else a[: r.nch]
-        ex = GpuExecutor(dev, keep_outputs=False, lambda_table_nsides=SERVE_TABLE_NSIDES, batch_channels=SERVE_BATCH)
+        ex = _serve_executor(dev)
         srv = Server(ex, hbm_cap_bytes=120e9, max_channels=32, max_slots_per_key=1)
         srv.run(reqs[:2], drain_s=60.0)  # builds the slot (and warms it) outside the timing
         for r in reqs:
@@ -767,8 +782,7 @@ def _batching_gain(dev, pools) -> dict:
         for ss in srv.slots.values():
             for sl in ss:
                 ex.free_slot(sl.handle)
-        tab = ns in SERVE_TABLE_NSIDES
-        with hpx.Plan(ns, 3 * ns - 1, 3 * ns - 1, 32, "f32", lambda_table=tab, tensor_cores=tab, device=dev) as p:
+        with _serve_plan(hpx, ns, 32, dev) as p:
             oa, om = p.empty_alm(), p.empty_map()
             for r in reqs[:2]:
                 (p.map2alm_n(r.nch, r.x, oa) if r.op == "map2alm" else p.alm2map_n(r.nch, r.x, om))

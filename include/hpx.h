@@ -145,6 +145,20 @@ typedef enum {
                                         with the tile kernels.  For tables
                                         larger than HBM.  Same results as
                                         the resident plan. */
+#define HPX_PLAN_LAMBDA_STREAM 16u   /* with the tensor-core path: no table
+                                        is kept; every transform recomputes
+                                        lambda by the FP64 recurrence (Eq.
+                                        15-16), block of m by block, into two
+                                        device staging buffers on a second
+                                        stream, and each block is contracted
+                                        on the tensor cores once it is
+                                        filled, while the recurrence fills
+                                        the other buffer.  One recurrence
+                                        serves all channels of the transform,
+                                        so the cost hardly grows with nbatch.
+                                        Same results as the resident plan
+                                        (the same fill kernels).  Not with
+                                        HPX_PLAN_LAMBDA_HOST. */
 
 /* Number of packed coefficients for (lmax, mmax). */
 int64_t hpx_nalm(int lmax, int mmax);
@@ -169,13 +183,24 @@ hpx_status hpx_plan_create_ex(int nside, int lmax, int mmax, int nbatch,
 /* An out-of-core tensor-core plan (HPX_PLAN_LAMBDA_TABLE |
  * HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST) whose two device staging
  * buffers hold stage_bytes per table part (hi, and lo for the x3 dtypes);
- * 0 selects 1 GiB.  dtype: HPX_F32 or a 16-bit dtype.  The tables are built
+ * 0 selects 1 GiB, or the larger table part where that is smaller.  dtype: HPX_F32 or a 16-bit dtype.  The tables are built
  * on the device block by block and copied to pinned host memory
  * (hpx_plan_host_bytes).  HPX_ERR_INVALID if one m's table slice does not
  * fit a staging buffer. */
 hpx_status hpx_plan_create_ooc(int nside, int lmax, int mmax, int nbatch,
                                hpx_dtype dtype, size_t stage_bytes,
                                hpx_plan* out);
+
+/* A streamed tensor-core plan (HPX_PLAN_LAMBDA_TABLE |
+ * HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_STREAM, plus `flags`: 0 or
+ * HPX_PLAN_TC_TF32X3 for an HPX_F32 plan) whose two device staging buffers
+ * hold stage_bytes per table part (hi, and lo for the x3 dtypes); 0 selects
+ * 1 GiB, or the larger table part where that is smaller.  dtype: HPX_F32 or a 16-bit dtype.  No table is built at plan
+ * time.  HPX_ERR_INVALID for other flags or if one m's table slice does not
+ * fit a staging buffer. */
+hpx_status hpx_plan_create_stream(int nside, int lmax, int mmax, int nbatch,
+                                  hpx_dtype dtype, unsigned flags,
+                                  size_t stage_bytes, hpx_plan* out);
 
 /* Pinned host bytes of an out-of-core plan's tables (0 otherwise). */
 size_t hpx_plan_host_bytes(hpx_plan plan);

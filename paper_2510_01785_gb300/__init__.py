@@ -58,7 +58,7 @@ class Plan:
     def __init__(self, nside: int, lmax: int, mmax: int | None = None, nbatch: int = 1,
                  dtype: str = "f32", lambda_table: bool = False, device=None,
                  tensor_cores: bool = False, out_of_core: bool = False, stage_bytes: int = 0,
-                 tf32x3: bool = False):
+                 tf32x3: bool = False, streamed: bool = False):
         mmax = lmax if mmax is None else mmax
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
@@ -79,10 +79,16 @@ class Plan:
         if tf32x3:  # 3xTF32 split products instead of FP16 hi/lo
             flags |= _lib.HPX_PLAN_TC_TF32X3
         self.tf32x3 = tf32x3
-        self.out_of_core = out_of_core
+        self.out_of_core, self.streamed = out_of_core, streamed
+        if out_of_core and streamed:
+            raise ValueError("out_of_core and streamed exclude each other")
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            if out_of_core:
+            if streamed:  # lambda recomputed per transform into staging slabs, tensor-core products
+                check(lib().hpx_plan_create_stream(nside, lmax, mmax, nbatch, DTYPES[dtype],
+                                                   _lib.HPX_PLAN_TC_TF32X3 if tf32x3 else 0, int(stage_bytes),
+                                                   ctypes.byref(h)), "hpx_plan_create_stream")
+            elif out_of_core:
                 check(lib().hpx_plan_create_ooc(nside, lmax, mmax, nbatch, DTYPES[dtype], int(stage_bytes),
                                                 ctypes.byref(h)), "hpx_plan_create_ooc")
             else:

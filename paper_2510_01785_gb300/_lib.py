@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libhpx.so")
 
 HPX_F64, HPX_F32, HPX_F32_BF16, HPX_F32_BF16X3, HPX_F32_FP16, HPX_F32_FP16X3 = range(6)
 HPX_PLAN_LAMBDA_RECOMPUTE, HPX_PLAN_LAMBDA_TABLE, HPX_PLAN_TENSOR_CORES, HPX_PLAN_LAMBDA_HOST = 0, 1, 2, 4
-HPX_PLAN_TC_TF32X3 = 8
+HPX_PLAN_TC_TF32X3, HPX_PLAN_LAMBDA_STREAM = 8, 16
 HPX_RING, HPX_NESTED, HPX_FLAT = 0, 1, 2
 STATUS = {0: "HPX_OK", 1: "HPX_ERR_INVALID", 2: "HPX_ERR_NOMEM", 3: "HPX_ERR_CUDA",
           4: "HPX_ERR_TIMEOUT", 5: "HPX_ERR_UNSUPPORTED"}
@@ -27,6 +27,7 @@ SIGNATURES = {
     "hpx_plan_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_P)]),
     "hpx_plan_create_ex": (_I, [_I, _I, _I, _I, _I, _U, ctypes.POINTER(_P)]),
     "hpx_plan_create_ooc": (_I, [_I, _I, _I, _I, _I, _SZ, ctypes.POINTER(_P)]),
+    "hpx_plan_create_stream": (_I, [_I, _I, _I, _I, _I, _U, _SZ, ctypes.POINTER(_P)]),
     "hpx_plan_test_withhold_copies": (_I, [_P, _I]),
     "hpx_plan_host_bytes": (_SZ, [_P]),
     "hpx_plan_destroy": (_I, [_P]),

@@ -316,6 +316,17 @@ hpx_status hpx_plan_create_ooc(int nside, int lmax, int mmax, int nbatch, hpx_dt
                      HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST, stage_bytes, out);
 }
 
+hpx_status hpx_plan_create_stream(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
+                                  size_t stage_bytes, hpx_plan* out) {
+  if (flags & ~HPX_PLAN_TC_TF32X3) {
+    if (out) *out = nullptr;
+    set_error("hpx_plan_create_stream: flags 0x%x (only HPX_PLAN_TC_TF32X3 may be added)", flags);
+    return HPX_ERR_INVALID;
+  }
+  return create_plan(nside, lmax, mmax, nbatch, dtype,
+                     flags | HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_STREAM, stage_bytes, out);
+}
+
 static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dtype dtype, unsigned flags,
                               size_t stage_bytes, hpx_plan* out) {
   if (!out) {
@@ -339,7 +350,8 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
     set_error("unknown dtype %d", (int)dtype);
     return HPX_ERR_INVALID;
   }
-  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST | HPX_PLAN_TC_TF32X3)) {
+  if (flags & ~(HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | HPX_PLAN_LAMBDA_HOST | HPX_PLAN_TC_TF32X3 |
+                HPX_PLAN_LAMBDA_STREAM)) {
     set_error("unknown plan flags 0x%x", flags);
     return HPX_ERR_INVALID;
   }
@@ -349,13 +361,22 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
     return HPX_ERR_INVALID;
   }
   if (mixed) {
-    flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES | (flags & HPX_PLAN_LAMBDA_HOST);  // their only path
+    flags = HPX_PLAN_LAMBDA_TABLE | HPX_PLAN_TENSOR_CORES |
+            (flags & (HPX_PLAN_LAMBDA_HOST | HPX_PLAN_LAMBDA_STREAM));  // their only path
   } else if ((flags & HPX_PLAN_TENSOR_CORES) && (dtype != HPX_F32 || !(flags & HPX_PLAN_LAMBDA_TABLE))) {
     set_error("HPX_PLAN_TENSOR_CORES needs an HPX_F32 plan with HPX_PLAN_LAMBDA_TABLE");
     return HPX_ERR_INVALID;
   }
   if ((flags & HPX_PLAN_LAMBDA_HOST) && !(flags & HPX_PLAN_TENSOR_CORES)) {
     set_error("HPX_PLAN_LAMBDA_HOST needs the tensor-core path (HPX_PLAN_TENSOR_CORES or a 16-bit dtype)");
+    return HPX_ERR_INVALID;
+  }
+  if ((flags & HPX_PLAN_LAMBDA_STREAM) && !(flags & HPX_PLAN_TENSOR_CORES)) {
+    set_error("HPX_PLAN_LAMBDA_STREAM needs the tensor-core path (HPX_PLAN_TENSOR_CORES or a 16-bit dtype)");
+    return HPX_ERR_INVALID;
+  }
+  if ((flags & HPX_PLAN_LAMBDA_STREAM) && (flags & HPX_PLAN_LAMBDA_HOST)) {
+    set_error("HPX_PLAN_LAMBDA_STREAM and HPX_PLAN_LAMBDA_HOST exclude each other");
     return HPX_ERR_INVALID;
   }
   hpx_plan_s* p = new hpx_plan_s();
@@ -431,7 +452,7 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
   // the CUDA-core table, also the 3xTF32 path's row table; the 16-bit
   // tensor-core paths build their own
   if (e == cudaSuccess && (flags & HPX_PLAN_LAMBDA_TABLE) && tc_mode_of(dtype, flags) <= 0 &&
-      !(flags & HPX_PLAN_LAMBDA_HOST))
+      !(flags & (HPX_PLAN_LAMBDA_HOST | HPX_PLAN_LAMBDA_STREAM)))
     e = dtype == HPX_F64 ? build_lambda_table<double>(p, s) : build_lambda_table<float>(p, s);
   if (e == cudaSuccess && (flags & HPX_PLAN_TENSOR_CORES)) e = build_tc(p, s);
   if (e == cudaSuccess) e = dtype == HPX_F64 ? build_fft_tables<double>(p, s) : build_fft_tables<float>(p, s);
@@ -484,7 +505,7 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
              cs * (size_t)nbatch * nring * (mmax + 1);
   const size_t ngroup = (npair + 31) / 32;
   const int mode = tc_mode_of(dtype, flags);
-  if (flags & HPX_PLAN_LAMBDA_HOST)  // tables on the host; two staging buffers (1 GiB parts) on the device
+  if (flags & (HPX_PLAN_LAMBDA_HOST | HPX_PLAN_LAMBDA_STREAM))  // no resident table; two staging buffers
     return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, mode, true);
   if (mode > 0) return b + sizeof(int) + tc_extra_bytes_estimate(nside, lmax, mmax, nbatch, mode, false);
   if (flags & HPX_PLAN_LAMBDA_TABLE)  // upper bound: every (l, m, ring pair) stored

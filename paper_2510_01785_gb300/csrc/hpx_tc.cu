@@ -406,6 +406,25 @@ struct Chain {
     return mu;
   }
 };
+// 16-bit tables hold kLamScale mu: the chain's restart values scaled by
+// that power of two scale every later value exactly.
+template <typename E>
+__device__ __forceinline__ void scale_start(Chain& ch) {
+  if constexpr (sizeof(E) == 2) {
+    ch.s0 *= kLamScale;
+    ch.s1 *= kLamScale;
+  }
+}
+// A table value as a stored element and its remainder: the FP64 value
+// rounded to FP32, then to E, the remainder of the FP32 value (exact in
+// FP32) rounded to E.  hi + lo is within 2^-22 |mu| for 16-bit E; FP32
+// tables store the rounded value alone.
+template <typename E>
+__device__ __forceinline__ void split_value(double mu, E& hi, E& lo) {
+  const float f = to_real<float>(mu);
+  hi = Elt<E>::from_float(f);
+  lo = Elt<E>::from_float(f - Elt<E>::to_float(hi));
+}
 __device__ __forceinline__ Chain chain_at(const RingInfo* rings, const double* coef_c, const int* lc_tab,
                                           const double* mu0_tab, const double* mu1_tab, int lmax, int npair, int m,
                                           int p) {
@@ -454,12 +473,20 @@ __global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __
   const int ls = lstart[mg];
   const long long o = off[mg] - base + (p % KW);
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
-  constexpr double kS = sizeof(E) == 2 ? kLamScale : 1.0;
-  for (int l = ls; l <= lmax; ++l) {
-    const double mu = p < npair ? kS * ch.step(l) : 0.0;
-    const E h = Elt<E>::from_double(mu);
+  scale_start<E>(ch);
+  // rows before the warp's first chain start are zero: no recurrence there
+  // (a group's warps are whole, so the early return above left all lanes)
+  const int lw = min(__reduce_min_sync(0xffffffffu, ch.lc), lmax + 1);
+  int l = ls;
+  for (; l < lw; ++l) {
+    hi[o + (long long)(l - ls) * KW] = Elt<E>::from_float(0.f);
+    if (lo) lo[o + (long long)(l - ls) * KW] = Elt<E>::from_float(0.f);
+  }
+  for (; l <= lmax; ++l) {
+    E h, r;
+    split_value<E>(p < npair ? ch.step(l) : 0.0, h, r);
     hi[o + (long long)(l - ls) * KW] = h;
-    if (lo) lo[o + (long long)(l - ls) * KW] = Elt<E>::from_double(mu - Elt<E>::to_double(h));
+    if (lo) lo[o + (long long)(l - ls) * KW] = r;
   }
 }
 
@@ -497,16 +524,23 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
   const int lend = ls + ((lmax - ls) / KW + 1) * KW;  // end of the last block
   const long long o = off[mT] - base + (long long)(p & 127) * KW;
   Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
-  constexpr double kS = sizeof(E) == 2 ? kLamScale : 1.0;
+  scale_start<E>(ch);
+  // vectors wholly before the warp's first chain start are zero: no
+  // recurrence there (a tile's warps are whole: the early returns above
+  // take all 128 threads of a tile or none)
+  const int lw = __reduce_min_sync(0xffffffffu, ch.lc);
   for (int lv = ls; lv < lend; lv += V) {
     alignas(16) E h[V];
     alignas(16) E r[V];
+    if (lv + V <= lw) {
 #pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const int l = lv + u;
-      const double mu = (l <= lmax && p < npair) ? kS * ch.step(l) : 0.0;
-      h[u] = Elt<E>::from_double(mu);
-      r[u] = Elt<E>::from_double(mu - Elt<E>::to_double(h[u]));
+      for (int u = 0; u < V; ++u) h[u] = r[u] = Elt<E>::from_float(0.f);
+    } else {
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int l = lv + u;
+        split_value<E>((l <= lmax && p < npair) ? ch.step(l) : 0.0, h[u], r[u]);
+      }
     }
     const int q = lv - ls;
     const long long at = o + (long long)(q / KW) * 128 * KW + (q % KW);
@@ -1330,14 +1364,20 @@ cudaError_t tile_nn(const hpx_plan_s* p, float* out, int b0, int nb, double mfac
   return cudaErrorInvalidValue;
 }
 
-// The tile kernel over all m: one launch on the resident table, or, for an
-// out-of-core plan, one launch per m block with the block's slice of the
-// host table copied into a staging buffer on the plan's copy stream.  Two
-// staging buffers alternate; a copy waits until the launch that last read
-// its buffer is done, and a launch waits for its copy.
+cudaError_t fill_table(hpx_plan_s* p, bool col, int m0, int nm, long long base, void* hi, void* lo,
+                       cudaStream_t s);
+
+// The tile kernel over all m: one launch on the resident table, or one
+// launch per m block with the block's slice of the table in a staging
+// buffer: copied from the host table (out-of-core plans) or filled by the
+// recurrence (streamed plans) on the plan's second stream.  Two staging
+// buffers alternate; a copy or fill waits until the launch that last read
+// its buffer is done, and a launch waits for its copy or fill, so the next
+// block's fill runs beside this block's products.
 template <bool SYN>
 cudaError_t tile_all(hpx_plan_s* p, float* out, int b0, int nb, double mfac, cudaStream_t s) {
-  if (!p->h_tab) {
+  const bool streamed = (p->flags & HPX_PLAN_LAMBDA_STREAM) != 0;
+  if (!p->h_tab && !streamed) {
     const TileRange r{SYN ? p->tm_stab : p->tm_tab, SYN ? p->tm_stablo : p->tm_tablo, 0, p->mmax + 1, 0};
     return tile_nn<SYN>(p, out, b0, nb, mfac, r, s);
   }
@@ -1356,9 +1396,14 @@ cudaError_t tile_all(hpx_plan_s* p, float* out, int b0, int nb, double mfac, cud
     const size_t bytes = (size_t)(bb[j + 1] - bb[j]) * es;
     char* d = static_cast<char*>(p->d_stage[buf]);
     e = cudaStreamWaitEvent(cs, ev[2 + buf], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d, hhi + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && hlo)
-      e = cudaMemcpyAsync(d + p->stage_bytes, hlo + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
+    if (streamed) {
+      if (e == cudaSuccess)
+        e = fill_table(p, SYN, bm[j], bm[j + 1] - bm[j], bb[j], d, p->tc_mode == 2 ? d + p->stage_bytes : nullptr, cs);
+    } else {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d, hhi + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess && hlo)
+        e = cudaMemcpyAsync(d + p->stage_bytes, hlo + (size_t)bb[j] * es, bytes, cudaMemcpyHostToDevice, cs);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev[buf], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[buf], 0);
     if (e == cudaSuccess) {
@@ -1437,9 +1482,11 @@ size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mo
              + es * chunks * nns * kw * parts * groups                       // At, likewise
              + (sizeof(int) + sizeof(long long)) * (size_t)(mmax + 1) * (nptile + ngroup) +
              sizeof(long long) * (mmax + 2) + 2 * sizeof(unsigned) * nbatch;
-  if (host_tables) return b + 2 * parts * (size_t(1) << 30);      // staging buffers at the default size
-  b += es * parts * chunks * nptile * 128 * kw;                    // column table (upper bound)
-  if (mode) b += es * parts * rows * ngroup * kw;                  // 16-bit row table (upper bound)
+  const size_t col = es * chunks * nptile * 128 * kw, row = es * rows * ngroup * kw;  // upper bounds, a part
+  if (host_tables)  // staging buffers at the default size
+    return b + 2 * parts * std::min(size_t(1) << 30, (std::max(col, row) + 127) / 128 * 128);
+  b += parts * col;           // column table
+  if (mode) b += parts * row;  // 16-bit row table
   return b;
 }
 
@@ -1527,6 +1574,7 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   p->tc_mode = mode;
   p->tc_fmt = (p->dtype == HPX_F32_BF16 || p->dtype == HPX_F32_BF16X3) ? 1 : 0;  // FP32 plans: FP16
   const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
+  const bool streamed = (p->flags & HPX_PLAN_LAMBDA_STREAM) != 0;
   const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
   // synthesis channels per CTA: 64 for one 16-bit product (accumulated over
   // all K in tensor memory), else kSynChannels
@@ -1540,9 +1588,9 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   };
   cudaError_t e = cudaSuccess;
   // row table layout: built here for the 16-bit types and for out-of-core
-  // plans (the resident FP32 one comes with the CUDA-core table)
+  // and streamed plans (the resident FP32 one comes with the CUDA-core table)
   std::vector<long long> roff;
-  if (mode || host) {
+  if (mode || host || streamed) {
     const int ng = (p->npair + kw - 1) / kw;
     p->ngroup = ng;
     const long long nent = (long long)(p->mmax + 1) * ng;
@@ -1595,7 +1643,7 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   e = cudaMemcpy(p->d_stab_off, coff.data(), sizeof(long long) * cent, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
 
-  if (!host) {
+  if (!host && !streamed) {
     // resident tables
     if (mode) {
       e = dalloc(&p->d_tab, (size_t)es * p->tab_elems);
@@ -1620,8 +1668,12 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
     }
   } else {
     // out-of-core tables: m blocks that fit a staging buffer, filled block by
-    // block on the device and copied to pinned host memory
-    if (p->stage_bytes == 0) p->stage_bytes = size_t(1) << 30;
+    // block on the device and copied to pinned host memory; streamed plans:
+    // the same blocks, filled anew by every transform
+    if (p->stage_bytes == 0) {  // 1 GiB, or less where the larger table part is smaller
+      const size_t whole = (size_t)es * (size_t)std::max(p->tab_elems, p->stab_elems);
+      p->stage_bytes = std::min(size_t(1) << 30, (whole + 127) / 128 * 128);
+    }
     p->stage_bytes = (p->stage_bytes / 128) * 128;
     const long long cap = (long long)(p->stage_bytes / es);
     std::vector<int> rbm, cbm;
@@ -1643,33 +1695,36 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
     std::copy(cbb.begin(), cbb.end(), p->blk_col_base);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dalloc(&p->d_stage[b], p->stage_bytes * parts);
     if (e != cudaSuccess) return e;
-    auto halloc = [&](void** ptr, size_t bytes) -> cudaError_t {
-      cudaError_t r = cudaHostAlloc(ptr, bytes > 0 ? bytes : 16, cudaHostAllocDefault);
-      if (r == cudaSuccess) p->host_bytes += bytes;
-      return r;
-    };
-    e = halloc(&p->h_tab, (size_t)es * p->tab_elems);
-    if (e == cudaSuccess) e = halloc(&p->h_stab, (size_t)es * p->stab_elems);
-    if (e == cudaSuccess && mode == 2) e = halloc(&p->h_tab_lo, (size_t)es * p->tab_elems);
-    if (e == cudaSuccess && mode == 2) e = halloc(&p->h_stab_lo, (size_t)es * p->stab_elems);
-    if (e != cudaSuccess) return e;
-    char* shi = static_cast<char*>(p->d_stage[0]);
-    char* slo = mode == 2 ? shi + p->stage_bytes : nullptr;
-    for (int col = 0; col < 2 && e == cudaSuccess; ++col) {
-      const std::vector<int>& bm = col ? cbm : rbm;
-      const std::vector<long long>& bb = col ? cbb : rbb;
-      char* hhi = static_cast<char*>(col ? p->h_stab : p->h_tab);
-      char* hlo = static_cast<char*>(col ? p->h_stab_lo : p->h_tab_lo);
-      for (size_t j = 0; j + 1 < bm.size() && e == cudaSuccess; ++j) {
-        const size_t bytes = (size_t)(bb[j + 1] - bb[j]) * es;
-        e = fill_table(p, col != 0, bm[j], bm[j + 1] - bm[j], bb[j], shi, slo, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hhi + (size_t)bb[j] * es, shi, bytes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && slo)
-          e = cudaMemcpyAsync(hlo + (size_t)bb[j] * es, slo, bytes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (host) {
+      auto halloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaHostAlloc(ptr, bytes > 0 ? bytes : 16, cudaHostAllocDefault);
+        if (r == cudaSuccess) p->host_bytes += bytes;
+        return r;
+      };
+      e = halloc(&p->h_tab, (size_t)es * p->tab_elems);
+      if (e == cudaSuccess) e = halloc(&p->h_stab, (size_t)es * p->stab_elems);
+      if (e == cudaSuccess && mode == 2) e = halloc(&p->h_tab_lo, (size_t)es * p->tab_elems);
+      if (e == cudaSuccess && mode == 2) e = halloc(&p->h_stab_lo, (size_t)es * p->stab_elems);
+      if (e != cudaSuccess) return e;
+      char* shi = static_cast<char*>(p->d_stage[0]);
+      char* slo = mode == 2 ? shi + p->stage_bytes : nullptr;
+      for (int col = 0; col < 2 && e == cudaSuccess; ++col) {
+        const std::vector<int>& bm = col ? cbm : rbm;
+        const std::vector<long long>& bb = col ? cbb : rbb;
+        char* hhi = static_cast<char*>(col ? p->h_stab : p->h_tab);
+        char* hlo = static_cast<char*>(col ? p->h_stab_lo : p->h_tab_lo);
+        for (size_t j = 0; j + 1 < bm.size() && e == cudaSuccess; ++j) {
+          const size_t bytes = (size_t)(bb[j + 1] - bb[j]) * es;
+          e = fill_table(p, col != 0, bm[j], bm[j + 1] - bm[j], bb[j], shi, slo, s);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hhi + (size_t)bb[j] * es, shi, bytes, cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess && slo)
+            e = cudaMemcpyAsync(hlo + (size_t)bb[j] * es, slo, bytes, cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
       }
+      if (e != cudaSuccess) return e;
     }
-    if (e != cudaSuccess) return e;
     const unsigned long long srows = (unsigned long long)(p->stage_bytes / 128);
     for (int b = 0; b < 2; ++b) {
       char* base = static_cast<char*>(p->d_stage[b]);

@@ -219,18 +219,22 @@ class GpuExecutor:
     coefficient buffer of the slot's batch capacity.
 
     table_nsides: geometries whose slots hold a plan-time lambda table on the
-    tensor cores (FP16 hi/lo split products, FP32 accuracy); the others
-    recompute lambda with the FP64 recurrence on every call.
+    tensor cores (FP16 hi/lo split products, FP32 accuracy); streamed_nsides:
+    geometries whose slots recompute lambda per call into streamed blocks
+    contracted on the tensor cores (no table held; one FP64 recurrence per
+    batch whatever its channel count); the others recompute lambda on the
+    CUDA cores, once per group of channels of a launch.
     batch_channels: channels per batch by Nside (default 32); one batch runs
     the recurrence, or streams the table, once for all its requests."""
 
     def __init__(self, device=None, keep_outputs: bool = True, lambda_table_nsides=(), batch_channels=None,
-                 tensor_cores: bool = True):
+                 tensor_cores: bool = True, streamed_nsides=()):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.keep = keep_outputs
         self.table_nsides = set(lambda_table_nsides)
+        self.streamed_nsides = set(streamed_nsides) - self.table_nsides
         self.batch_channels = dict(batch_channels or {})
         self.tc = tensor_cores
 
@@ -239,6 +243,8 @@ class GpuExecutor:
 
     def _flags(self, nside) -> int:
         from . import _lib
+        if nside in self.streamed_nsides:
+            return _lib.HPX_PLAN_LAMBDA_TABLE | _lib.HPX_PLAN_TENSOR_CORES | _lib.HPX_PLAN_LAMBDA_STREAM
         if nside not in self.table_nsides:
             return _lib.HPX_PLAN_LAMBDA_RECOMPUTE
         return _lib.HPX_PLAN_LAMBDA_TABLE | (_lib.HPX_PLAN_TENSOR_CORES if self.tc else 0)
@@ -253,8 +259,11 @@ class GpuExecutor:
         from . import Plan
         torch = self.torch
         tab = nside in self.table_nsides
-        plan = Plan(nside, lmax, lmax, max_ch, "f32", lambda_table=tab, tensor_cores=tab and self.tc,
-                    device=self.device)
+        if nside in self.streamed_nsides:
+            plan = Plan(nside, lmax, lmax, max_ch, "f32", streamed=True, device=self.device)
+        else:
+            plan = Plan(nside, lmax, lmax, max_ch, "f32", lambda_table=tab, tensor_cores=tab and self.tc,
+                        device=self.device)
         h = {"plan": plan, "stream": torch.cuda.Stream(self.device), "map": plan.empty_map(),
              "alm": plan.empty_alm(), "event": torch.cuda.Event(), "ys": []}
         h["nbytes"] = plan.device_bytes + h["map"].nbytes + h["alm"].nbytes

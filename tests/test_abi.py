@@ -85,6 +85,27 @@ def test_estimate_counts_the_tensor_core_operands(hpxlib):
     assert tc - table >= 3072 * 64 * 32 * 32 * 4
 
 
+def test_streamed_plan_flags(hpxlib):
+    """Rejected before any device work: extra flags to the streamed
+    constructor, streaming together with host tables, streaming without the
+    tensor-core path."""
+    L = hpxlib.lib()
+    h = ctypes.c_void_p()
+    assert L.hpx_plan_create_stream(16, 47, 47, 1, 1, 1, 0, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert L.hpx_plan_create_ex(16, 47, 47, 1, 1, 1 | 2 | 4 | 16, ctypes.byref(h)) == 1
+    assert L.hpx_plan_create_ex(16, 47, 47, 1, 0, 16, ctypes.byref(h)) == 1
+    assert L.hpx_plan_create_ex(16, 47, 47, 1, 1, 16, ctypes.byref(h)) == 1
+    assert h.value is None
+
+
+def test_estimate_streamed_holds_no_table(hpxlib):
+    L = hpxlib.lib()
+    tc = L.hpx_plan_estimate_bytes(1024, 3071, 3071, 8, 1, 3)
+    st = L.hpx_plan_estimate_bytes(1024, 3071, 3071, 8, 1, 3 | 16)
+    assert st < tc - 20e9  # the FP16 hi/lo tables (about 58 GB) are not held; two staging buffers are
+
+
 def _header_declarations():
     """{name: (return type, [argument types])} of every function declared in
     include/hpx.h (comments and preprocessor lines stripped)."""

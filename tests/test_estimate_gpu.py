@@ -12,6 +12,8 @@ CASES = [  # nside, lmax, nbatch, dtype, Plan keywords, flags
     (128, 383, 8, "f32", dict(lambda_table=True, tensor_cores=True, tf32x3=True), 11),
     (128, 383, 40, "bf16", {}, 0),
     (256, 767, 3, "fp16x3", {}, 0),
+    (256, 767, 8, "f32", dict(streamed=True), 19),
+    (128, 383, 8, "bf16", dict(streamed=True), 16),  # (the estimate assumes the default staging size)
 ]
 
 

@@ -2,9 +2,9 @@
 through every plan kind of the CUDA library: analysis (Eq. 1), synthesis
 (Eq. 2) and both adjoints (Sec. III-F), against the closed forms themselves
 rather than the oracle.  Bars as in the parity tests: relative L2 per
-channel, FP64 1e-12, FP32 (CUDA cores, either tensor-core split scheme, or
-tables streamed from the host) 1e-5, and the mixed-precision bounds for the
-16-bit contractions."""
+channel, FP64 1e-12, FP32 (CUDA cores, either tensor-core split scheme,
+tables streamed from the host, or lambda recomputed into streamed blocks)
+1e-5, and the mixed-precision bounds for the 16-bit contractions."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +21,7 @@ KINDS = {
     "f32-tc-fp16-split": (dict(dtype="f32", lambda_table=True, tensor_cores=True), 1e-5),
     "f32-tc-tf32x3": (dict(dtype="f32", lambda_table=True, tensor_cores=True, tf32x3=True), 1e-5),
     "f32-out-of-core": (dict(dtype="f32", out_of_core=True, stage_bytes=1 << 20), 1e-5),
+    "f32-streamed": (dict(dtype="f32", streamed=True, stage_bytes=1 << 20), 1e-5),
     # 16-bit contractions, at the mixed-precision bounds
     "bf16": (dict(dtype="bf16"), 1e-2),
     "fp16": (dict(dtype="fp16"), 2e-3),
