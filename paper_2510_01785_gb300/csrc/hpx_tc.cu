@@ -556,6 +556,12 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
 // MODE 1: one 16-bit product; MODE 2: 16-bit x3 (stored hi and lo parts).
 __host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : 2 * pow2_at_least((x + 1) / 2); }
 
+// m per CTA of the single-product synthesis of 64 channels (N = 256): 2
+// stages two m's outputs in the 512 tensor-memory columns (one CTA per SM).
+#ifndef HPX_TC_SYN_MQ_256
+#define HPX_TC_SYN_MQ_256 2
+#endif
+
 template <int NN, bool SYN, int MODE>
 struct TcShape {
   static constexpr int kA = kTcTile * 128;  // lambda tile bytes: 128 rows x 128 bytes
@@ -574,7 +580,8 @@ struct TcShape {
   // other modes accumulate each K block alone and add it into FP32 registers
   static constexpr bool kFullK = MODE == 1;
   // synthesis m per CTA (see tc_mq)
-  static constexpr int kMq = (SYN && MODE != 0) ? (kFullK ? (NN <= 64 ? 4 : 2) : (NN == 32 ? 4 : 2)) : 1;
+  static constexpr int kMq =
+      (SYN && MODE != 0) ? (kFullK ? (NN <= 64 ? 4 : NN == 256 ? HPX_TC_SYN_MQ_256 : 2) : (NN == 32 ? 4 : 2)) : 1;
   static constexpr int kTmemCols = kFullK ? pow2_at_least(kMq * NN) : kLoTmem ? 256 : 2 * kBuf;
   static constexpr int kAlloc = (!kFullK && kMq > 1) ? pow2_at_least(kTmemCols + kMq * NN) : kTmemCols;
   // two CTAs per SM where half the tensor memory and half the shared memory
@@ -1095,7 +1102,7 @@ k_legendre_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                   const float oi = has ? __uint_as_float(o[j][2 * cc + 1]) * inv : 0.f;
                   w[j] = side ? make_float2(er - orr, ei - oi) : make_float2(er + orr, ei + oi);
                 }
-                if (nq == MQ && (at % MQ) == 0) {  // whole pieces: 16 or 32 bytes
+                if (MQ % 2 == 0 && nq == MQ && (at % MQ) == 0) {  // whole pieces: 16 or 32 bytes
                   float4* dd = reinterpret_cast<float4*>(F + at);
 #pragma unroll
                   for (int h = 0; h < MQ / 2; ++h)
