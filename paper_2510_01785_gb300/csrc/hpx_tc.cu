@@ -556,10 +556,23 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
 // MODE 1: one 16-bit product; MODE 2: 16-bit x3 (stored hi and lo parts).
 __host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : 2 * pow2_at_least((x + 1) / 2); }
 
-// m per CTA of the single-product synthesis of 64 channels (N = 256): 2
-// stages two m's outputs in the 512 tensor-memory columns (one CTA per SM).
+// m per CTA of the single-product synthesis of 64 channels (N = 256): 2,
+// whose outputs fill the 512 tensor-memory columns (one CTA per SM), F
+// leaving in 16-byte pieces.
 #ifndef HPX_TC_SYN_MQ_256
 #define HPX_TC_SYN_MQ_256 2
+#endif
+// ... and of 32 channels (N = 128): 4, again all 512 columns, so that F
+// leaves in whole 32-byte sectors (at Nside 1024 / lmax 2047 / 64 BF16
+// channels 4.13 ms against 5.77 with 64 channels per CTA and 5.92 with 2 m).
+#ifndef HPX_TC_SYN_MQ_128
+#define HPX_TC_SYN_MQ_128 4
+#endif
+// m per CTA of the split-product synthesis of 16 channels (N = 64): 2 (two
+// CTAs per SM); 4 fills the tensor memory and measured slower (10.5 against
+// 9.0 ms at the same workload in FP32).
+#ifndef HPX_TC_SYN_MQ_X3
+#define HPX_TC_SYN_MQ_X3 2
 #endif
 
 template <int NN, bool SYN, int MODE>
@@ -581,7 +594,10 @@ struct TcShape {
   static constexpr bool kFullK = MODE == 1;
   // synthesis m per CTA (see tc_mq)
   static constexpr int kMq =
-      (SYN && MODE != 0) ? (kFullK ? (NN <= 64 ? 4 : NN == 256 ? HPX_TC_SYN_MQ_256 : 2) : (NN == 32 ? 4 : 2)) : 1;
+      (SYN && MODE != 0)
+          ? (kFullK ? (NN <= 64 ? 4 : NN == 256 ? HPX_TC_SYN_MQ_256 : HPX_TC_SYN_MQ_128)
+                    : (NN == 32 ? 4 : NN == 64 ? HPX_TC_SYN_MQ_X3 : 2))
+          : 1;
   static constexpr int kTmemCols = kFullK ? pow2_at_least(kMq * NN) : kLoTmem ? 256 : 2 * kBuf;
   static constexpr int kAlloc = (!kFullK && kMq > 1) ? pow2_at_least(kTmemCols + kMq * NN) : kTmemCols;
   // two CTAs per SM where half the tensor memory and half the shared memory
@@ -1463,6 +1479,13 @@ constexpr int kSynChannels = HPX_TC_SYN_CHANNELS;
 constexpr int kAnaChannels = HPX_TC_ANA_CHANNELS;
 static_assert(kAnaChannels == 8 || kAnaChannels == 16 || kAnaChannels == 32 || kAnaChannels == 64, "analysis group");
 static_assert(kSynChannels == 8 || kSynChannels == 16 || kSynChannels == 32, "synthesis channel group");
+// Channels per synthesis CTA in the single-product modes (partner CTAs of
+// a wider transform read each lambda block from L2).
+#ifndef HPX_TC_SYN_CHANNELS_FK
+#define HPX_TC_SYN_CHANNELS_FK 32
+#endif
+constexpr int kSynChannelsFK = HPX_TC_SYN_CHANNELS_FK;
+static_assert(kSynChannelsFK == 32 || kSynChannelsFK == 64, "single-product synthesis channel group");
 
 int tc_columns(int nbatch, int cap) {
   int cp = 8;
@@ -1477,7 +1500,7 @@ size_t tc_extra_bytes_estimate(int nside, int lmax, int mmax, int nbatch, int mo
   const size_t es = mode ? 2 : 4, kw = mode ? 64 : 32, parts = mode == 2 ? 2 : 1;
   const size_t npair = 2 * (size_t)nside, ngroup = (npair + kw - 1) / kw, nptile = (npair + 127) / 128;
   const size_t nna = (size_t)tc_columns(nbatch, mode ? kAnaChannels : 32),
-               nns = (size_t)tc_columns(nbatch, mode == 1 ? 64 : kSynChannels);
+               nns = (size_t)tc_columns(nbatch, mode == 1 ? kSynChannelsFK : kSynChannels);
   size_t chunks = 0, rows = 0;
   for (int m = 0; m <= mmax; ++m) {
     chunks += (size_t)((lmax - m) / kw + 1);
@@ -1583,10 +1606,10 @@ cudaError_t build_tc(hpx_plan_s* p, cudaStream_t s) {
   const bool host = (p->flags & HPX_PLAN_LAMBDA_HOST) != 0;
   const bool streamed = (p->flags & HPX_PLAN_LAMBDA_STREAM) != 0;
   const int kw = mode ? 64 : 32, es = mode ? 2 : 4, parts = mode == 2 ? 2 : 1;
-  // synthesis channels per CTA: 64 for one 16-bit product (accumulated over
-  // all K in tensor memory), else kSynChannels
+  // synthesis channels per CTA: kSynChannelsFK for one 16-bit product
+  // (accumulated over all K in tensor memory), else kSynChannels
   const int nna = tc_columns(p->nbatch, mode ? kAnaChannels : 32),
-            nns = tc_columns(p->nbatch, mode == 1 ? 64 : kSynChannels);
+            nns = tc_columns(p->nbatch, mode == 1 ? kSynChannelsFK : kSynChannels);
   const int rba = mode == 2 ? 2 * nna : nna, rbs = mode == 2 ? 2 * nns : nns;
   auto dalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
