@@ -230,3 +230,18 @@ def test_admission_uses_measured_slot_sizes_once_known():
         drain(srv)
     assert srv.evictions == 2  # no more: re-admitting 64 and 128 fits beside 256
     assert len([s for ss in srv.slots.values() for s in ss]) == 3
+
+
+def test_streamed_slots_hold_no_table():
+    """The executor's plan flags per geometry (a geometry in both lists gets
+    the table) and the admission estimate of a streamed slot: no table, so
+    well under the table slot of the same geometry."""
+    from paper_2510_01785_gb300 import _lib
+    from paper_2510_01785_gb300.serve import GpuExecutor
+    ex = GpuExecutor(device="cpu", lambda_table_nsides=(256,), streamed_nsides=(256, 1024))
+    stream = _lib.HPX_PLAN_LAMBDA_TABLE | _lib.HPX_PLAN_TENSOR_CORES | _lib.HPX_PLAN_LAMBDA_STREAM
+    assert ex._flags(1024) == stream
+    assert ex._flags(256) == _lib.HPX_PLAN_LAMBDA_TABLE | _lib.HPX_PLAN_TENSOR_CORES
+    assert ex._flags(64) == _lib.HPX_PLAN_LAMBDA_RECOMPUTE
+    tab = GpuExecutor(device="cpu", lambda_table_nsides=(1024,)).slot_bytes(1024, 3071, 32)
+    assert 0 < ex.slot_bytes(1024, 3071, 32) < tab / 3

@@ -43,11 +43,14 @@ def _rel(got, ref):
     return float(np.max(num / np.maximum(np.linalg.norm(ref.reshape(ref.shape[0], -1), axis=1), 1e-300)))
 
 
-def test_served_results_match_the_oracle_with_tables_and_eviction():
+@pytest.mark.parametrize("tables,streamed", [((32, 128), ()), ((16,), (64, 256))], ids=["tables", "streamed"])
+def test_served_results_match_the_oracle_with_tables_and_eviction(tables, streamed):
     """Every served result against the FP64 oracle (relative L2 per channel
     <= 1e-5, the FP32 bar): geometries up to Nside 256, tensor-core table
-    slots (Nside 32 and 128) beside recomputing ones, batches wider than one
-    request, and an HBM cap small enough that idle slots are evicted."""
+    slots beside CUDA-core recomputing ones, or streamed-lambda tensor-core
+    slots (lambda recomputed per batch into staging blocks) beside a table
+    slot, batches wider than one request, and an HBM cap small enough that
+    idle slots are evicted."""
     import oracle
     from paper_2510_01785_gb300.serve import GpuExecutor, Server, latency_report, make_requests
 
@@ -63,7 +66,7 @@ def test_served_results_match_the_oracle_with_tables_and_eviction():
         else:
             r.x_np = syn.gaussian_alm(4000 + r.rid, r.lmax, r.lmax, r.nch).astype(np.complex64)
             r.x = torch.from_numpy(r.x_np).cuda()
-    ex = GpuExecutor(lambda_table_nsides=(32, 128), batch_channels={ns: 12 for ns in weights})
+    ex = GpuExecutor(lambda_table_nsides=tables, batch_channels={ns: 12 for ns in weights}, streamed_nsides=streamed)
     sizes = sorted(ex.slot_bytes(ns, 3 * ns - 1, 12) for ns in weights)
     cap = sizes[-1] + sizes[-2] + 1  # the two largest slots fit, not all five geometries
     srv = Server(ex, hbm_cap_bytes=cap, max_channels=6, max_slots_per_key=1)
