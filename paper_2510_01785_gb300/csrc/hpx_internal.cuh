@@ -64,6 +64,7 @@ struct hpx_plan_s {
   void* d_tw;          // C2<T> tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1)
   double* d_cmm;       // [mmax+1] lambda_mm / sin^m(theta) (sign included)
   double* d_coef_c;    // [nalm] recurrence coefficient c_l of mu_l = c_l z mu_{l-1} - mu_{l-2}
+  float2* d_coef_cf;   // [nalm] c_l as a double-FP32 pair (hi, lo): the FP32 plans' recurrence
   double* d_coef_p;    // [nalm] P_l, lambda_l = P_l mu_l
   float* d_coef_pf;    // [nalm] P_l rounded to float
   int* d_lc;           // [mmax+1][npair] first significant l of chain (m, pair)
@@ -186,6 +187,97 @@ template <> __device__ __forceinline__ float to_real<float>(double x) {
   unsigned f = __funnelshift_l(lo, ahi, 3) + 0x40000000u + ((lo >> 28) & 1u);
   f = (ahi < (897u << 20)) ? 0u : (f | (hi & 0x80000000u));
   return __uint_as_float(f);
+}
+
+// Double-FP32 numbers (Dekker's double-length arithmetic, 1971): a value is
+// the unevaluated sum hi + lo of two floats, about 48 significant bits, and
+// the arithmetic runs on the FP32 pipe, 64 times the FP64 pipe's rate on
+// this part.  The FP32 plans run the recurrence in it: mu scaled by 2^104
+// (chain starts are at least 2^-200 and |mu| stays below 2^8, so both
+// parts stay normal floats; a power of two scales the linear recurrence
+// exactly).  Explicitly rounded operations keep the compiler from fusing the
+// error terms away.
+struct Df {
+  float hi, lo;
+};
+constexpr double kDfUp = 0x1p104;
+__device__ __forceinline__ Df df_of(double x) {
+  const float h = __double2float_rn(x);
+  return Df{h, __double2float_rn(x - (double)h)};
+}
+// a b as an unnormalised pair: the rounded product, plus its rounding error
+// (one FMA) and the cross terms (the lo lo term, below 2^-44 ab, dropped)
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  return Df{p, __fmaf_rn(a.lo, b.hi, e)};
+}
+// t n1 - n2, renormalised: Knuth's TwoSum of the leading parts, the error
+// terms added, then Dekker's FastTwoSum
+__device__ __forceinline__ Df df_step(Df t, Df n1, Df n2) {
+  const Df q = df_mul(t, n1);
+  const float s = __fsub_rn(q.hi, n2.hi);
+  const float v = __fsub_rn(s, q.hi);
+  const float err = __fadd_rn(__fsub_rn(q.hi, __fsub_rn(s, v)), __fsub_rn(-n2.hi, v));
+  const float f = __fadd_rn(err, __fsub_rn(q.lo, n2.lo));
+  const float h = __fadd_rn(s, f);
+  return Df{h, __fsub_rn(f, __fsub_rn(h, s))};
+}
+// the float value of a scaled pair: hi 2^-104, and 0 below 2^-126 (as to_real)
+__device__ __forceinline__ float df_real(Df x) { return fabsf(x.hi) < 0x1p-22f ? 0.f : __fmul_rn(x.hi, 0x1p-104f); }
+
+// One recurrence chain mu_l = c_l z mu_{l-1} - mu_{l-2} of a plan with real
+// type T, restarted at its first significant l (lc) with the stored
+// (mu_{lc-1}, mu_lc) and zero before: FP64 for FP64 plans, double-FP32 for
+// the others (whose results need FP32 accuracy; the pair's ~2^-46 error per
+// step stays far below it over any chain).  C is the coefficient type the
+// kernels stage (8 bytes either way).  step() returns mu_l as a T; every
+// kernel and table of a plan steps with it, so their values agree bit for
+// bit.
+template <typename T> struct Recur;
+template <> struct Recur<double> {
+  using C = double;
+  double z = 0.0, s0 = 0.0, s1 = 0.0, n1 = 0.0, n2 = 0.0;
+  __device__ __forceinline__ void start(double z_, double s0_, double s1_) {
+    z = z_;
+    s0 = s0_;
+    s1 = s1_;
+  }
+  __device__ __forceinline__ double step(C c, int l, int lc) {
+    double mu = fma(c * z, n1, -n2);
+    if (l == lc) {
+      mu = s1;
+      n1 = s0;
+    }
+    n2 = n1;
+    n1 = mu;
+    return mu;
+  }
+};
+template <> struct Recur<float> {
+  using C = float2;
+  Df z{0.f, 0.f}, s0{0.f, 0.f}, s1{0.f, 0.f}, n1{0.f, 0.f}, n2{0.f, 0.f};
+  __device__ __forceinline__ void start(double z_, double s0_, double s1_) {
+    z = df_of(z_);
+    s0 = df_of(s0_ * kDfUp);
+    s1 = df_of(s1_ * kDfUp);
+  }
+  __device__ __forceinline__ float step(C c, int l, int lc) {
+    Df mu = df_step(df_mul(Df{c.x, c.y}, z), n1, n2);
+    if (l == lc) {
+      mu = s1;
+      n1 = s0;
+    }
+    n2 = n1;
+    n1 = mu;
+    return df_real(mu);
+  }
+};
+template <typename T> using RecCoef = typename Recur<T>::C;
+// the plan's coefficients in the form Recur<T> stages
+template <typename T> inline const RecCoef<T>* rec_coefs(const hpx_plan_s* p) {
+  return reinterpret_cast<const RecCoef<T>*>(sizeof(T) == 4 ? (const void*)p->d_coef_cf : (const void*)p->d_coef_c);
 }
 
 __host__ __device__ inline long long alm_base(int lmax, int m) {  // index(l = 0, m); index(l, m) = alm_base + l

@@ -210,7 +210,7 @@ template <typename T> struct LamTab {
 template <typename T, int CP, bool TAB>
 __global__ void __launch_bounds__(512)
 k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const RingInfo* __restrict__ rings,
-                    const C2<T>* __restrict__ etab, const double* __restrict__ coef_c,
+                    const C2<T>* __restrict__ etab, const RecCoef<T>* __restrict__ coef_c,
                     const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                     const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
                     int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w,
@@ -231,7 +231,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   T* sG = reinterpret_cast<T*>(smem_raw);      // [nthr][2][C2N]  S, A
   T* sMu = sG + (size_t)nthr * 2 * C2N;        // [nthr][MS]; warp w's [LB][C2N] partials at row 32 w
   T* sC = sMu + (size_t)nthr * MS;             // [2][LB][C2N]
-  double* sCz = reinterpret_cast<double*>(sC + 2 * LB * C2N);  // [2][LB] c_l of this and the next block
+  RecCoef<T>* sCz = reinterpret_cast<RecCoef<T>*>(sC + 2 * LB * C2N);  // [2][LB] c_l of this and the next block
 
   double z = 0.0, s0 = 0.0, s1 = 0.0;
   int lc = INT_MAX;
@@ -266,9 +266,10 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   const long long base = alm_base(lmax, m);
   const int lq = lane / NCQ, cq = lane % NCQ;
   const int l0 = lq * LPL, c0 = cq * CPL;
-  double mu1 = 0.0, mu2 = 0.0;
+  Recur<T> rc;
+  rc.start(z, s0, s1);
   int buf = 0;
-  if (t < LB) sCz[t] = (m + t <= lmax) ? coef_c[base + m + t] : 0.0;
+  if (t < LB) sCz[t] = (m + t <= lmax) ? coef_c[base + m + t] : RecCoef<T>{};
   // TAB: this warp's group rows (32 coalesced 128-byte rows per block),
   // loaded one block ahead so the loads are in flight during the contraction
   // and the reductions of the block before
@@ -289,7 +290,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
   }
   __syncthreads();
   for (int lb0 = m; lb0 <= lmax; lb0 += LB) {
-    const double* cz = sCz + buf * LB;
+    const RecCoef<T>* cz = sCz + buf * LB;
     // --- recurrence: LB steps of mu_l = c_l z mu_{l-1} - mu_{l-2} ---
     T* myMu = sMu + (size_t)t * MS;
     if constexpr (TAB) {
@@ -312,17 +313,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
       for (int i4 = 0; i4 < LB; i4 += 4) {
         T v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int l = lb0 + i4 + u;
-          double mu = fma(cz[i4 + u] * z, mu1, -mu2);
-          if (l == lc) {
-            mu = s1;
-            mu1 = s0;
-          }
-          mu2 = mu1;
-          mu1 = mu;
-          v[u] = to_real<T>(mu);
-        }
+        for (int u = 0; u < 4; ++u) v[u] = rc.step(cz[i4 + u], lb0 + i4 + u, lc);
         if constexpr (sizeof(T) == 4) {
           *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
         } else {
@@ -381,7 +372,7 @@ k_legendre_analysis(const C2<T>* __restrict__ spec, T* __restrict__ alm, const R
     // c_l of the next block, into the other half of the double buffer
     if (t < LB) {
       const int l = lb0 + LB + t;
-      sCz[(buf ^ 1) * LB + t] = (l <= lmax) ? coef_c[base + l] : 0.0;
+      sCz[(buf ^ 1) * LB + t] = (l <= lmax) ? coef_c[base + l] : RecCoef<T>{};
     }
     // --- cluster reduction; CTA r writes its share of the block ---
     cluster.sync();
@@ -458,7 +449,7 @@ size_t analysis_ws_smem(int nch) {
 template <int CP>
 __global__ void __launch_bounds__(1024)
 k_legendre_analysis_ws(const float2* __restrict__ spec, float* __restrict__ alm, const RingInfo* __restrict__ rings,
-                       const float2* __restrict__ etab, const double* __restrict__ coef_c,
+                       const float2* __restrict__ etab, const float2* __restrict__ coef_c,
                        const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                        const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
                        int npair, int nring, long long nspec, long long nalm, int b0, int nb, int use_w,
@@ -527,8 +518,9 @@ k_legendre_analysis_ws(const float2* __restrict__ spec, float* __restrict__ alm,
   const int nblk = (lmax - m) / LB + 1;
   if (producer) {
     // ---- the recurrence, block by block into slot b mod 2
-    const double* cl = coef_c + base;
-    double mu1 = 0.0, mu2 = 0.0;
+    const float2* cl = coef_c + base;
+    Recur<float> rc;
+    rc.start(z, s0, s1);
     for (int b = 0; b < nblk; ++b) {
       const int lb0 = m + b * LB, slot = b & 1;
       if (b >= 2) cluster.sync();  // phase b - 2: every consumer is done with block b - 2, which used this slot
@@ -536,22 +528,12 @@ k_legendre_analysis_ws(const float2* __restrict__ spec, float* __restrict__ alm,
       if (__any_sync(0xffffffffu, lc < lb0 + LB)) {
 #pragma unroll
         for (int i4 = 0; i4 < LB; i4 += 4) {
-          double c4[4];
+          float2 c4[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) c4[u] = (lb0 + i4 + u <= lmax) ? cl[lb0 + i4 + u] : 0.0;
+          for (int u = 0; u < 4; ++u) c4[u] = (lb0 + i4 + u <= lmax) ? cl[lb0 + i4 + u] : make_float2(0.f, 0.f);
           T v[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int l = lb0 + i4 + u;
-            double mu = fma(c4[u] * z, mu1, -mu2);
-            if (l == lc) {
-              mu = s1;
-              mu1 = s0;
-            }
-            mu2 = mu1;
-            mu1 = mu;
-            v[u] = to_real<T>(mu);
-          }
+          for (int u = 0; u < 4; ++u) v[u] = rc.step(c4[u], lb0 + i4 + u, lc);
           *reinterpret_cast<float4*>(myMu + i4) = make_float4(v[0], v[1], v[2], v[3]);
         }
       } else {
@@ -644,7 +626,7 @@ k_legendre_analysis_ws(const float2* __restrict__ spec, float* __restrict__ alm,
 template <typename T, int CP, bool TAB>
 __global__ void __launch_bounds__(128)
 k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const RingInfo* __restrict__ rings,
-                     const double* __restrict__ coef_c, const float* __restrict__ coef_pf,
+                     const RecCoef<T>* __restrict__ coef_c, const float* __restrict__ coef_pf,
                      const double* __restrict__ coef_p, const int* __restrict__ lc_tab,
                      const double* __restrict__ mu0_tab, const double* __restrict__ mu1_tab, int lmax,
                      int mmax, int npair, int nring, long long nalm, int b0, int nb, const LamTab<T> tb,
@@ -652,7 +634,7 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
   using V = C2<T>;
   constexpr int C2N = 2 * CP;
   __shared__ __align__(16) T sA[LB][C2N];
-  __shared__ double sCz[LB];
+  __shared__ RecCoef<T> sCz[LB];
   __shared__ int sMinLc;
   const int m = blockIdx.y, t = threadIdx.x, nthr = blockDim.x;
   const int p = blockIdx.x * nthr + t;
@@ -676,7 +658,8 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
 #pragma unroll
   for (int c = 0; c < C2N; ++c) accE[c] = accO[c] = (T)0;
   const long long base = alm_base(lmax, m);
-  double mu1 = 0.0, mu2 = 0.0;
+  Recur<T> rc;
+  rc.start(z, s0, s1);
   if (lstart <= lmax) {
     for (int lb0 = m + ((lstart - m) / LB) * LB; lb0 <= lmax; lb0 += LB) {
       for (int q = t; q < LB * C2N; q += nthr) {
@@ -690,7 +673,7 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
         }
         sA[li][c] = v;
       }
-      if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : 0.0;
+      if (t < LB) sCz[t] = (lb0 + t <= lmax) ? coef_c[base + lb0 + t] : RecCoef<T>{};
       __syncthreads();
       // a warp whose chains all start after this block has nothing to add
       if (TAB && __any_sync(0xffffffffu, lc < lb0 + LB)) {
@@ -718,26 +701,12 @@ k_legendre_synthesis(const T* __restrict__ alm, C2<T>* __restrict__ F, const Rin
 #pragma unroll 4
         for (int i = 0; i < LB; i += 2) {
           {
-            double mu = fma(sCz[i] * z, mu1, -mu2);
-            if (lb0 + i == lc) {
-              mu = s1;
-              mu1 = s0;
-            }
-            mu2 = mu1;
-            mu1 = mu;
-            const T mf = to_real<T>(mu);
+            const T mf = rc.step(sCz[i], lb0 + i, lc);
 #pragma unroll
             for (int c = 0; c < C2N; ++c) accE[c] = fma(mf, sA[i][c], accE[c]);
           }
           {
-            double mu = fma(sCz[i + 1] * z, mu1, -mu2);
-            if (lb0 + i + 1 == lc) {
-              mu = s1;
-              mu1 = s0;
-            }
-            mu2 = mu1;
-            mu1 = mu;
-            const T mf = to_real<T>(mu);
+            const T mf = rc.step(sCz[i + 1], lb0 + i + 1, lc);
 #pragma unroll
             for (int c = 0; c < C2N; ++c) accO[c] = fma(mf, sA[i + 1][c], accO[c]);
           }
@@ -807,7 +776,7 @@ static cudaError_t launch_analysis_cp(const hpx_plan_s* p, T* alm, bool use_w, d
   for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
     e = cudaLaunchKernelEx(&cfg, k_legendre_analysis<T, CP, TAB>, (const V*)p->d_spec, alm,
-                           (const RingInfo*)p->d_ring, (const V*)p->d_etab, (const double*)p->d_coef_c,
+                           (const RingInfo*)p->d_ring, (const V*)p->d_etab, rec_coefs<T>(p),
                            (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
                            (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
                            use_w ? 1 : 0, lam_tab<T>(p), mfac);
@@ -871,7 +840,7 @@ static cudaError_t launch_analysis_ws_cp(const hpx_plan_s* p, float* alm, bool u
   for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
     e = cudaLaunchKernelEx(&cfg, k_legendre_analysis_ws<CP>, (const float2*)p->d_spec, alm,
-                           (const RingInfo*)p->d_ring, (const float2*)p->d_etab, (const double*)p->d_coef_c,
+                           (const RingInfo*)p->d_ring, (const float2*)p->d_etab, (const float2*)p->d_coef_cf,
                            (const double*)p->d_coef_p, (const int*)p->d_lc, (const double*)p->d_mu0,
                            (const double*)p->d_mu1, p->lmax, p->npair, p->nring, p->nspec, p->nalm, b0, nb,
                            use_w ? 1 : 0, mfac, p->d_status);
@@ -943,7 +912,7 @@ static cudaError_t launch_synthesis_cp(const hpx_plan_s* p, const T* alm, double
   for (int b0 = 0; b0 < p->nbatch; b0 += CP) {
     const int nb = (p->nbatch - b0) < CP ? (p->nbatch - b0) : CP;
     k_legendre_synthesis<T, CP, TAB><<<grid, nthr, 0, s>>>(
-        alm, (V*)p->d_F, p->d_ring, p->d_coef_c, p->d_coef_pf, p->d_coef_p, p->d_lc, p->d_mu0, p->d_mu1,
+        alm, (V*)p->d_F, p->d_ring, rec_coefs<T>(p), p->d_coef_pf, p->d_coef_p, p->d_lc, p->d_mu0, p->d_mu1,
         p->lmax, p->mmax, p->npair, p->nring, p->nalm, b0, nb, lam_tab<T>(p), mfac);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -975,10 +944,20 @@ cudaError_t launch_synthesis(const hpx_plan_s* p, const T* alm, double mfac, cud
   }
 }
 
+// c_l as the double-FP32 pairs of the FP32 plans' recurrence
+__global__ void k_coef_pairs(const double* __restrict__ coef_c, float2* __restrict__ coef_cf, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Df d = df_of(coef_c[i]);
+    coef_cf[i] = make_float2(d.hi, d.lo);
+  }
+}
+
 cudaError_t build_recurrence_tables(hpx_plan_s* p, cudaStream_t s) {
   const int mb = (p->mmax + 1 + 127) / 128;
   k_lambda_mm_prefactor<<<mb, 128, 0, s>>>(p->mmax, p->d_cmm);
   k_recurrence_coefs<<<mb, 128, 0, s>>>(p->lmax, p->mmax, p->d_coef_c, p->d_coef_p, p->d_coef_pf);
+  const long long nb = (p->nalm + 255) / 256;
+  k_coef_pairs<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(p->d_coef_c, p->d_coef_cf, p->nalm);
   k_chain_scan<<<dim3((p->npair + 127) / 128, p->mmax + 1), 128, 0, s>>>(
       p->d_ring, p->d_cmm, p->d_coef_c, p->lmax, p->npair, p->d_lc, p->d_mu0, p->d_mu1);
   return cudaGetLastError();
@@ -1010,7 +989,7 @@ __global__ void k_table_groups(const int* __restrict__ lc_tab, int lmax, int npa
 // operations, same conversion), zero before a chain's start and for the
 // padding lanes of a group.
 template <typename T>
-__global__ void k_table_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+__global__ void k_table_fill(const RingInfo* __restrict__ rings, const RecCoef<T>* __restrict__ coef_c,
                              const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                              const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
                              const long long* __restrict__ off, int lmax, int npair, int ngroup, T* tab) {
@@ -1024,22 +1003,12 @@ __global__ void k_table_fill(const RingInfo* __restrict__ rings, const double* _
     for (int l = ls; l <= lmax; ++l) out[(long long)(l - ls) * 32] = (T)0;
     return;
   }
-  const double z = rings[p].z;
   const long long ci = (long long)m * npair + p;
   const int lc = lc_tab[ci];
-  const double s0 = mu0_tab[ci], s1 = mu1_tab[ci];
+  Recur<T> rc;
+  rc.start(rings[p].z, mu0_tab[ci], mu1_tab[ci]);
   const long long base = alm_base(lmax, m);
-  double mu1 = 0.0, mu2 = 0.0;
-  for (int l = ls; l <= lmax; ++l) {
-    double mu = fma(coef_c[base + l] * z, mu1, -mu2);
-    if (l == lc) {
-      mu = s1;
-      mu1 = s0;
-    }
-    mu2 = mu1;
-    mu1 = mu;
-    out[(long long)(l - ls) * 32] = to_real<T>(mu);
-  }
+  for (int l = ls; l <= lmax; ++l) out[(long long)(l - ls) * 32] = rc.step(coef_c[base + l], l, lc);
 }
 
 template <typename T>
@@ -1074,7 +1043,7 @@ cudaError_t build_lambda_table(hpx_plan_s* p, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   p->bytes += sizeof(T) * (acc > 0 ? acc : 1);
   k_table_fill<T><<<dim3((ng * 32 + 127) / 128, p->mmax + 1), 128, 0, s>>>(
-      p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
+      p->d_ring, rec_coefs<T>(p), p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
       ng, static_cast<T*>(p->d_tab));
   return cudaGetLastError();
 }

@@ -137,7 +137,7 @@ static void plan_free(hpx_plan_s* p) {
       if (st[i]) cudaStreamDestroy(st[i]);
     delete[] st;
   }
-  void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_chirp, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_p,
+  void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_chirp, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_cf, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
                   p->d_stab, p->d_stab_off, p->d_stab_lstart, p->d_tab_lo, p->d_stab_lo, p->d_bmax,
@@ -426,6 +426,7 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
             alloc(&p->d_tw, cs * ((size_t)1 << (p->logtw - 1))) &&
             alloc((void**)&p->d_cmm, sizeof(double) * (mmax + 1)) &&
             alloc((void**)&p->d_coef_c, sizeof(double) * p->nalm) &&
+            alloc((void**)&p->d_coef_cf, sizeof(float2) * p->nalm) &&
             alloc((void**)&p->d_coef_p, sizeof(double) * p->nalm) &&
             alloc((void**)&p->d_coef_pf, sizeof(float) * p->nalm) &&
             alloc((void**)&p->d_lc, sizeof(int) * nchain) && alloc((void**)&p->d_mu0, sizeof(double) * nchain) &&
@@ -500,7 +501,7 @@ size_t hpx_plan_estimate_bytes(int nside, int lmax, int mmax, int nbatch, hpx_dt
   }
   size_t b = sizeof(RingInfo) * nring + cs * netab + cs * (nbtab ? nbtab : 1) + cs * ((size_t)1 << (logm_max - 1)) +
              cs * (size_t)nside * (nside - 1) +
-             sizeof(double) * (mmax + 1) + (2 * sizeof(double) + sizeof(float)) * nalm +
+             sizeof(double) * (mmax + 1) + (3 * sizeof(double) + sizeof(float)) * nalm +
              (sizeof(int) + 2 * sizeof(double)) * nchain + cs * (size_t)nbatch * nspec +
              cs * (size_t)nbatch * nring * (mmax + 1);
   const size_t ngroup = (npair + 31) / 32;

@@ -179,22 +179,16 @@ template <> struct Elt<float> {
   static constexpr int kw = 32;
   static __device__ __forceinline__ float from_float(float v) { return v; }
   static __device__ __forceinline__ float to_float(float v) { return v; }
-  static __device__ __forceinline__ float from_double(double v) { return to_real<float>(v); }
-  static __device__ __forceinline__ double to_double(float v) { return (double)v; }
 };
 template <> struct Elt<__nv_bfloat16> {
   static constexpr int kw = 64;
   static __device__ __forceinline__ __nv_bfloat16 from_float(float v) { return __float2bfloat16_rn(v); }
   static __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
-  static __device__ __forceinline__ __nv_bfloat16 from_double(double v) { return __double2bfloat16(v); }
-  static __device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 };
 template <> struct Elt<__half> {
   static constexpr int kw = 64;
   static __device__ __forceinline__ __half from_float(float v) { return __float2half_rn(v); }
   static __device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
-  static __device__ __forceinline__ __half from_double(double v) { return __double2half(v); }
-  static __device__ __forceinline__ double to_double(__half v) { return (double)__half2float(v); }
 };
 
 // Operand value v (already scaled) into row n of a tile column: hi at row n,
@@ -387,56 +381,40 @@ k_pack_at(const float2* __restrict__ alm, const float* __restrict__ coef_pf, con
 // ---------------------------------------------------------------------------
 // plan-time lambda tables of the tensor-core stages
 // ---------------------------------------------------------------------------
-// The recurrence of every table, operation for operation the same as the
-// CUDA-core kernels' (so FP32 tables hold identical values): from l = ls,
-// mu_l = c_l z mu_{l-1} - mu_{l-2}, restarted at the chain start lc with the
-// stored (mu_{lc-1}, mu_lc); zero before lc.
+// The recurrence of every table: the FP32 plans' chain (Recur<float>, the
+// same steps as the CUDA-core kernels', so FP32 tables hold identical
+// values), from l = ls, restarted at the chain start lc with the stored
+// (mu_{lc-1}, mu_lc); zero before lc.  16-bit tables hold kLamScale mu: the
+// restart values scaled by that power of two scale every later value
+// exactly.
 struct Chain {
-  double z, s0, s1, mu1, mu2;
+  Recur<float> rc;
   int lc;
-  const double* c;
-  __device__ __forceinline__ double step(int l) {
-    double mu = fma(c[l] * z, mu1, -mu2);
-    if (l == lc) {
-      mu = s1;
-      mu1 = s0;
-    }
-    mu2 = mu1;
-    mu1 = mu;
-    return mu;
-  }
+  const float2* c;
+  __device__ __forceinline__ float step(int l) { return rc.step(c[l], l, lc); }
 };
-// 16-bit tables hold kLamScale mu: the chain's restart values scaled by
-// that power of two scale every later value exactly.
 template <typename E>
-__device__ __forceinline__ void scale_start(Chain& ch) {
-  if constexpr (sizeof(E) == 2) {
-    ch.s0 *= kLamScale;
-    ch.s1 *= kLamScale;
-  }
-}
-// A table value as a stored element and its remainder: the FP64 value
-// rounded to FP32, then to E, the remainder of the FP32 value (exact in
-// FP32) rounded to E.  hi + lo is within 2^-22 |mu| for 16-bit E; FP32
-// tables store the rounded value alone.
-template <typename E>
-__device__ __forceinline__ void split_value(double mu, E& hi, E& lo) {
-  const float f = to_real<float>(mu);
-  hi = Elt<E>::from_float(f);
-  lo = Elt<E>::from_float(f - Elt<E>::to_float(hi));
-}
-__device__ __forceinline__ Chain chain_at(const RingInfo* rings, const double* coef_c, const int* lc_tab,
+__device__ __forceinline__ Chain chain_at(const RingInfo* rings, const float2* coef_cf, const int* lc_tab,
                                           const double* mu0_tab, const double* mu1_tab, int lmax, int npair, int m,
                                           int p) {
-  Chain ch{0.0, 0.0, 0.0, 0.0, 0.0, INT_MAX, coef_c + alm_base(lmax, m)};
+  Chain ch;
+  ch.lc = INT_MAX;
+  ch.c = coef_cf + alm_base(lmax, m);
   if (p < npair) {
     const long long ci = (long long)m * npair + p;
-    ch.z = rings[p].z;
+    constexpr double kS = sizeof(E) == 2 ? kLamScale : 1.0;
     ch.lc = lc_tab[ci];
-    ch.s0 = mu0_tab[ci];
-    ch.s1 = mu1_tab[ci];
+    ch.rc.start(rings[p].z, kS * mu0_tab[ci], kS * mu1_tab[ci]);
   }
   return ch;
+}
+// A table value as a stored element and its remainder: hi the FP32 value
+// rounded to E, lo the remainder (exact in FP32) rounded to E; hi + lo is
+// within 2^-22 |value| for 16-bit E.  FP32 tables store the value alone.
+template <typename E>
+__device__ __forceinline__ void split_value(float f, E& hi, E& lo) {
+  hi = Elt<E>::from_float(f);
+  lo = Elt<E>::from_float(f - Elt<E>::to_float(hi));
 }
 
 // Row table (analysis) of 16-bit types: per (m, group of KW = 64 pairs), rows
@@ -460,7 +438,7 @@ __global__ void k_rtab_groups(const int* __restrict__ lc_tab, int lmax, int npai
 // Fills m = m0 + blockIdx.y; element e of the table goes to hi[e - base]
 // (base > 0 when the table is built block by block through a staging buffer).
 template <typename E>
-__global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+__global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const float2* __restrict__ coef_c,
                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
                             const long long* __restrict__ off, int lmax, int npair, int ngroup, int m0,
@@ -472,8 +450,7 @@ __global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __
   const long long mg = (long long)m * ngroup + g;
   const int ls = lstart[mg];
   const long long o = off[mg] - base + (p % KW);
-  Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
-  scale_start<E>(ch);
+  Chain ch = chain_at<E>(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
   // rows before the warp's first chain start are zero: no recurrence there
   // (a group's warps are whole, so the early return above left all lanes)
   const int lw = min(__reduce_min_sync(0xffffffffu, ch.lc), lmax + 1);
@@ -484,7 +461,7 @@ __global__ void k_rtab_fill(const RingInfo* __restrict__ rings, const double* __
   }
   for (; l <= lmax; ++l) {
     E h, r;
-    split_value<E>(p < npair ? ch.step(l) : 0.0, h, r);
+    split_value<E>(p < npair ? ch.step(l) : 0.f, h, r);
     hi[o + (long long)(l - ls) * KW] = h;
     if (lo) lo[o + (long long)(l - ls) * KW] = r;
   }
@@ -509,7 +486,7 @@ __global__ void k_ctab_tiles(const int* __restrict__ lc_tab, int lmax, int npair
 }
 
 template <typename E>
-__global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __restrict__ coef_c,
+__global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const float2* __restrict__ coef_c,
                             const int* __restrict__ lc_tab, const double* __restrict__ mu0_tab,
                             const double* __restrict__ mu1_tab, const int* __restrict__ lstart,
                             const long long* __restrict__ off, int lmax, int npair, int nptile, int m0,
@@ -523,8 +500,7 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
   if (ls > lmax) return;
   const int lend = ls + ((lmax - ls) / KW + 1) * KW;  // end of the last block
   const long long o = off[mT] - base + (long long)(p & 127) * KW;
-  Chain ch = chain_at(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
-  scale_start<E>(ch);
+  Chain ch = chain_at<E>(rings, coef_c, lc_tab, mu0_tab, mu1_tab, lmax, npair, m, p);
   // vectors wholly before the warp's first chain start are zero: no
   // recurrence there (a tile's warps are whole: the early returns above
   // take all 128 threads of a tile or none)
@@ -539,7 +515,7 @@ __global__ void k_ctab_fill(const RingInfo* __restrict__ rings, const double* __
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         const int l = lv + u;
-        split_value<E>((l <= lmax && p < npair) ? ch.step(l) : 0.0, h[u], r[u]);
+        split_value<E>((l <= lmax && p < npair) ? ch.step(l) : 0.f, h[u], r[u]);
       }
     }
     const int q = lv - ls;
@@ -1558,13 +1534,13 @@ template <typename E>
 cudaError_t fill_row_table(hpx_plan_s* p, int m0, int nm, long long base, void* hi, void* lo, cudaStream_t s) {
   constexpr int KW = Elt<E>::kw;
   k_rtab_fill<E><<<dim3((p->ngroup * KW + 127) / 128, nm), 128, 0, s>>>(
-      p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
+      p->d_ring, p->d_coef_cf, p->d_lc, p->d_mu0, p->d_mu1, p->d_tab_lstart, p->d_tab_off, p->lmax, p->npair,
       p->ngroup, m0, base, static_cast<E*>(hi), static_cast<E*>(lo));
   return cudaGetLastError();
 }
 template <typename E>
 cudaError_t fill_col_table(hpx_plan_s* p, int m0, int nm, long long base, void* hi, void* lo, cudaStream_t s) {
-  k_ctab_fill<E><<<dim3(p->nptile, nm), 128, 0, s>>>(p->d_ring, p->d_coef_c, p->d_lc, p->d_mu0, p->d_mu1,
+  k_ctab_fill<E><<<dim3(p->nptile, nm), 128, 0, s>>>(p->d_ring, p->d_coef_cf, p->d_lc, p->d_mu0, p->d_mu1,
                                                      p->d_stab_lstart, p->d_stab_off, p->lmax, p->npair,
                                                      p->nptile, m0, base, static_cast<E*>(hi), static_cast<E*>(lo));
   return cudaGetLastError();

@@ -139,12 +139,12 @@ def test_cuda_core_table_and_recompute_rooflines(monkeypatch):
     assert r["kernel"] == "k_legendre_analysis<table>" and r["bound"] == "hbm"
     st = _stages(40.0, 50.0, tc=False)
     r = bench.legendre_roofline(plan, st, table=False)
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["bound"] == "alu" and r["unit"] == "TOP/s"
     assert r["kernel"] == "k_legendre_synthesis"
     active, _ = plan.chain_stats()
-    # 3 FP64 flop per significant triple over the launch
-    assert r["achieved"] == pytest.approx(3.0 * active / 50e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS)
+    # a double-FP32 step (19 FP32 operations) and 2 FMA per channel per significant triple
+    assert r["achieved"] == pytest.approx((19 + 2 * bench.NBATCH) * active / 50e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP32_OPS_PEAK)
     assert "hbm_gbs_algorithmic" not in st["legendre_synthesis"]
 
 

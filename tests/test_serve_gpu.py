@@ -68,7 +68,7 @@ def test_served_results_match_the_oracle_with_tables_and_eviction(tables, stream
             r.x = torch.from_numpy(r.x_np).cuda()
     ex = GpuExecutor(lambda_table_nsides=tables, batch_channels={ns: 12 for ns in weights}, streamed_nsides=streamed)
     sizes = sorted(ex.slot_bytes(ns, 3 * ns - 1, 12) for ns in weights)
-    cap = sizes[-1] + sizes[-2] + 1  # the two largest slots fit, not all five geometries
+    cap = sizes[-1] + 1  # any one slot fits, not all five geometries
     srv = Server(ex, hbm_cap_bytes=cap, max_channels=6, max_slots_per_key=1)
     srv.run(reqs, drain_s=120.0)
     torch.cuda.synchronize()
