@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-drain", type=float, default=15.0)
-    ap.add_argument("--serve-sustainable", type=float, default=200.0,
+    ap.add_argument("--serve-sustainable", type=float, default=120.0,
                     help="offered rate of the second serving stream, one the server keeps up with")
     ap.add_argument("--record", default=os.path.join("gpurun_out", "bench_record.json"),
                     help="file for the full record (every plan, stage, config); stdout gets the headline only")
@@ -693,7 +693,7 @@ def _serve_stream(dev, pools, rate, duration, drain_s, seed):
     return reqs, srv, wall
 
 
-def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_rate: float = 200.0) -> dict:
+def run_serving(dev, rate: float, duration: float, drain_s: float, sustainable_rate: float = 120.0) -> dict:
     """Config 5: a seeded Poisson stream of map2alm/alm2map requests (50/50),
     Nside from SERVE_MIX, lmax = 3 Nside - 1, 1-32 FP32 channels, served by
     the continuously batching server under a 120 GB cap (requests still
