@@ -3,7 +3,7 @@
 
 Workload (one step): map2alm followed by alm2map of one batch of 8 FP32
 channels at Nside 1024 (12,582,912 pixels, 4095 rings), lmax = mmax = 3071,
-lambda_lm from the FP64 recurrence.  Channels 0-3 are band-limited fields
+lambda_lm from the three-term recurrence (double-FP32 in the FP32 plans).  Channels 0-3 are band-limited fields
 (a_lm ~ N(0, (l+1)^-2), synthesised), channels 4-7 white noise; all inputs
 are seeded and synthetic and already resident in HBM when timing starts
 (maps 403 MB, coefficients 302 MB: larger than the 129 MB L2, so no flush).
@@ -423,8 +423,8 @@ def run_ours(args):
     rec["accuracy"] = plan_accuracy(plan_r, maps, alm_in, ref64)
     plan_r.close()
 
-    # plan-resident lambda table (built by the same FP64 recurrence at plan
-    # time), Legendre analysis on the CUDA cores
+    # plan-resident lambda table (built by the same double-FP32 recurrence at
+    # plan time), Legendre analysis on the CUDA cores
     plan_c = hpx.Plan(NSIDE, LMAX, MMAX, NBATCH, "f32", lambda_table=True, device=dev)
     cc = timed_steps(plan_c, maps, alm_in, args, dist, dev, world, gpu_index)
     cc["roofline"] = legendre_roofline(plan_c, cc["stages"], table=True)
@@ -498,7 +498,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "precision": "FP32 I/O; lambda from the FP64 recurrence (plan-time table); contraction on "
+                "precision": "FP32 I/O; lambda from the double-FP32 recurrence (plan-time table); contraction on "
                              "tcgen05 as FP16 hi/lo split products (hi*hi + hi*lo + lo*hi, FP32 sums): "
                              f"{acc['map2alm_max_rel_l2_vs_f64']:.1e} / {acc['alm2map_max_rel_l2_vs_f64']:.1e} "
                              "rel. L2 vs FP64",
@@ -650,7 +650,7 @@ def legendre_roofline(plan, stages, table: bool, value_bytes: int = 4):
 SERVE_MIX = {64: 0.30, 128: 0.25, 256: 0.20, 512: 0.15, 1024: 0.07, 2048: 0.03}
 # slots with a plan-time lambda table on the tensor cores, and slots that
 # recompute lambda per batch into streamed blocks contracted on the tensor
-# cores (one FP64 recurrence per batch, whatever its channels); channels per
+# cores (one recurrence per batch, whatever its channels); channels per
 # batch: one table stream or one recurrence serves every request of a batch
 SERVE_TABLE_NSIDES = (64, 128, 256)
 SERVE_STREAMED_NSIDES = (512, 1024, 2048)
@@ -966,7 +966,7 @@ def run_small_configs(dev) -> dict:
         diff[f"nside{ns}_lmax{lmax}_b{nb}"] = {
             "loss1_forward_backward_ms": _event_ms(loss1, dev, reps, 1),
             "loss2_forward_backward_ms": _event_ms(loss2, dev, reps, 1),
-            "dtype": "f32", "lambda": "recomputed by the FP64 recurrence in forward and backward"}
+            "dtype": "f32", "lambda": "recomputed by the double-FP32 recurrence in forward and backward"}
         del maps, alm, target, ell, wl
         hpx.clear_plans()
         torch.cuda.empty_cache()
