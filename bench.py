@@ -372,18 +372,24 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def tile_source_sha() -> str:
+    """Hash of the sources the tensor-core tile kernels are compiled from
+    (their translation unit, the internal header and the C ABI header)."""
+    h = hashlib.sha256()
+    for f in (os.path.join("paper_2510_01785_gb300", "csrc", "hpx_tc.cu"),
+              os.path.join("paper_2510_01785_gb300", "csrc", "hpx_internal.cuh"),
+              os.path.join("include", "hpx.h")):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured from the current source (else None)."""
+    was captured from the current source of the tile kernels (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2510_01785_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    sha = h.hexdigest()[:16]
+    sha = tile_source_sha()
     for line in open(path):
         kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
         if kv.get("kernel") == kernel and kv.get("source_sha") == sha and "dram_bytes_per_launch" in kv:

@@ -11,17 +11,24 @@
 // channel); the whole transform stays in shared memory, so each stage reads
 // its input from HBM once and writes its output once.  Belt rings (all of
 // length 4 nside) and cap rings are launched separately, each launch with the
-// shared memory its longest transform needs.
+// shared memory its longest transform needs, the belt launch on a second
+// stream so that the two run side by side; a ring's channels are adjacent
+// CTAs, so its chirp and kernel spectrum are read from HBM once.
 //
 // The power-of-two FFT is a Stockham (self-sorting) transform: radix-16
 // passes, then one radix-8, -4 or -2 pass if log2 M is not a multiple of 4,
 // natural order in and out.  Each pass reads its butterflies' inputs into
 // registers, synchronises, and writes the outputs.  Shared-memory element i
-// lives at i XOR ((i / 16) mod 16) -- each 128-byte row of 16 elements
-// permuted by its row number -- so that reads along i and the passes' writes
-// at power-of-two strides spread over all banks.  One twiddle per butterfly
-// comes from the table; its powers are formed by multiplication, at most four
-// deep.
+// lives at i + i / 16 (one unused slot after every 16): the pass reads
+// j + r M/R and writes (j - k) R + k + r Ns, with the thread index j
+// contiguous across a warp, so every access of a half-warp falls on distinct
+// bank pairs, and for every stride a multiple of 16 the R addresses of a
+// thread are one base plus multiples of one stride (no per-element index
+// arithmetic: the kernels are bound by instruction issue, and this layout
+// took the ring transforms from 0.73 / 1.52 to 0.52 / 0.88 ms at Nside 1024,
+// 8 FP32 channels, against a row-wise XOR swizzle).  One twiddle per
+// butterfly comes from the table; its powers are formed by multiplication,
+// at most four deep.
 //
 // Chirp and phase angles pi r / N are reduced exactly in integers before the
 // FP64 sincospi that fills the tables.
@@ -33,10 +40,10 @@ __device__ __forceinline__ int brev(int k, int logm) {
   return (int)(__brev((unsigned)k) >> (32 - logm));
 }
 
-// shared-memory position of FFT element i (a permutation within each row of
-// 16 elements)
-__device__ __forceinline__ int spos(int i) { return i ^ ((i >> 4) & 15); }
-__host__ __device__ inline size_t padded_len(size_t n) { return n + 16; }  // one more row: the c2r fold writes element n
+// shared-memory position of FFT element i: one unused element after every
+// 16, so that element i + 16 t sits t bank pairs further on
+__device__ __forceinline__ int spos(int i) { return i + (i >> 4); }
+__host__ __device__ inline size_t padded_len(size_t n) { return n + (n >> 4) + 1; }  // the c2r fold writes element n
 
 // Radix-2 decimation in frequency (natural order in, bit-reversed order out),
 // used once per plan to transform the Bluestein kernels in FP64.
@@ -145,6 +152,13 @@ template <int R, int Q, bool INV, typename V>
 __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw,
                                               const V* __restrict__ pre = nullptr) {
   const int nb = (1 << logm) / R;
+  // with nb a multiple of 16 the inputs j + r nb sit at spos(j) + r istr; the
+  // outputs base + r Ns at spos(base) + r ostr when Ns >= 16 or (radix 16,
+  // Ns = 1) base = 16 j
+  const bool lin_in = (nb & 15) == 0;
+  const int istr = nb + (nb >> 4);
+  const bool lin_out = Ns >= 16 || (Ns == 1 && R == 16);
+  const int ostr = Ns >= 16 ? Ns + (Ns >> 4) : 1;
   V v[Q][R], wq[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -153,10 +167,17 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
       // the butterfly's twiddle W^k, k = j mod Ns (k / (Ns R) < 1/2: inside
       // the stored half of the table), fetched before the barrier
       if (Ns > 1) wq[q] = tw[(j & (Ns - 1)) << (logtw - __ffs(Ns * R) + 1)];
+      if (lin_in) {
+        const V* src = buf + spos(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        v[q][r] = buf[spos(j + r * nb)];
-        if (pre) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
+        for (int r = 0; r < R; ++r) v[q][r] = src[r * istr];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = buf[spos(j + r * nb)];
+      }
+      if (pre) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
       }
     }
   }
@@ -190,8 +211,14 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
       }
       dft_small<R, INV>(v[q]);
       const int base = (j - k) * R + k;
+      if (lin_out) {
+        V* dst = buf + spos(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[spos(base + r * Ns)] = v[q][r];
+        for (int r = 0; r < R; ++r) dst[r * ostr] = v[q][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[spos(base + r * Ns)] = v[q][r];
+      }
     }
   }
   __syncthreads();
@@ -247,8 +274,17 @@ __device__ __forceinline__ int slot_ring(int q, int caps, int nside) {
 // ---------------------------------------------------------------------------
 // analysis: real ring -> half spectrum X_y[k], k = 0..N/2 (Eq. 13)
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM the ring kernels are compiled for: two of 512
+// threads (64 registers a thread) in FP32, 512 threads in FP64; the synthesis
+// kernel's build for launches of at most 256 threads takes five (48
+// registers: c2r 0.86 -> 0.80 ms at Nside 1024, 8 channels; the analysis
+// kernel measured no faster there).
+template <typename T, int MAXT> constexpr int ring_min_blocks() {
+  return sizeof(T) == 8 ? 512 / MAXT : (MAXT <= 256 ? 5 : 1024 / MAXT);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, (ring_min_blocks<T, 512>()))
 k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* __restrict__ rings,
            const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab, const C2<T>* __restrict__ chirp,
            const C2<T>* __restrict__ tw, int logtw, long long npix, long long nspec, int caps, int nside,
@@ -256,7 +292,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int y = slot_ring(blockIdx.x, caps, nside), b = blockIdx.y;
+  const int y = slot_ring(blockIdx.y, caps, nside), b = blockIdx.x;
   const RingInfo R = rings[y];
   const int H = R.nphi >> 1, logm = R.logm;
   const bool blue = R.btab >= 0;
@@ -280,8 +316,9 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = x2[j + r * nb];
       dft_small<16, false>(v);
+      const int b0 = spos(16 * j);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) buf[spos(16 * j + r)] = v[r];
+      for (int r = 0; r < 16; ++r) buf[b0 + r] = v[r];
     }
     __syncthreads();
     fft_pow2<false>(buf, logm, tw, logtw, static_cast<const V*>(nullptr), 1);
@@ -323,8 +360,8 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
 // The ring's values are p_x = sum_{k<N} D[k] exp(2 pi i k x / N) with
 // D[k] = sum_{m = k mod N} F_m e^{i m phi0} + sum_{m = -k mod N, m >= 1}
 // conj(F_m e^{i m phi0}) (the aliasing fold; m = 0 contributes Re F_0).
-template <typename T>
-__global__ void __launch_bounds__(512)
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, (ring_min_blocks<T, MAXT>()))
 k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __restrict__ rings,
            const C2<T>* __restrict__ etab, const C2<T>* __restrict__ btab, const C2<T>* __restrict__ chirp,
            const C2<T>* __restrict__ tw, int logtw, long long npix, int nring, int mmax,
@@ -332,7 +369,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int y = slot_ring(blockIdx.x, caps, nside), b = blockIdx.y;
+  const int y = slot_ring(blockIdx.y, caps, nside), b = blockIdx.x;
   const RingInfo R = rings[y];
   const int N = R.nphi, H = N >> 1, logm = R.logm, sig = R.sigma;
   const unsigned twoN = 2u * (unsigned)N;  // sigma m < 2^15: 32-bit arithmetic is exact
@@ -373,6 +410,33 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   // the ring is then z = IDFT_H(Z) with p[2n] = Re z[n], p[2n+1] = Im z[n].
   // Computed as conj(DFT_H(conj Z)), so conj Z (Bluestein: times the chirp,
   // zero-padded to 2^logm) is stored.
+  if (!blue && logm >= 4 && (H >> 4) <= (int)blockDim.x) {
+    // power-of-two rings: conj Z is formed as the first radix-16 pass
+    // (Ns = 1) reads its inputs j + r H/16 -- no separate pass over the
+    // buffer -- and that pass writes elements 16 j + r
+    const int nb = H >> 4, j = threadIdx.x;
+    V v[16];
+    if (j < nb) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int k = j + r * nb;
+        const V dk = buf[spos(k)], dc = buf[spos(H - k)];
+        const V s1 = cadd(dk, cconj(dc)), d1 = csub(dk, cconj(dc));
+        const V t1 = cmul(cconj(E[2 * k]), d1);
+        v[r] = cmk<V>(s1.x - t1.y, -(s1.y + t1.x));
+      }
+    }
+    __syncthreads();
+    if (j < nb) {
+      dft_small<16, false>(v);
+      const int b0 = spos(16 * j);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) buf[b0 + r] = v[r];
+    }
+    __syncthreads();
+    fft_pow2<false>(buf, logm, tw, logtw, static_cast<const V*>(nullptr), 1);
+  } else
+  {
   for (int k = threadIdx.x; k <= H / 2; k += blockDim.x) {
     const int kc = H - k;
     const V dk = buf[spos(k)], dc = buf[spos(kc)];
@@ -393,6 +457,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
     for (int n = H + threadIdx.x; n < (1 << logm); n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
   __syncthreads();
   ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
+  }
   const T sc = scale_by_weight ? (T)R.w : (T)1;
   V* out = reinterpret_cast<V*>(map + (long long)b * npix + R.start);
   for (int n = threadIdx.x; n < H; n += blockDim.x) {
@@ -521,6 +586,37 @@ static RingLaunch caps_launch(const hpx_plan_s* p) {
   return {1, 2 * (p->nside - 1), p->logm_max, fft_threads(p->logm_max)};
 }
 
+static dim3 grid_of(const RingLaunch& L, int nbatch) {
+  return dim3(nbatch, L.nslots);  // a ring's channels adjacent: its tables are read once from HBM
+}
+
+// The belt-ring launch runs on the plan's second stream, beside the cap-ring
+// launch on the caller's stream: forked from the caller's stream before the
+// launches and joined back after them, so the call stays ordered on the
+// caller's stream (and captures into a graph as a fork and a join).  `which`
+// picks the stream and events of the analysis (0) or the synthesis (1).
+struct Fork {
+  cudaStream_t s, side;
+  cudaEvent_t join_ev = nullptr;
+  Fork(const hpx_plan_s* p, int which, cudaStream_t s_, cudaError_t& e) : s(s_), side(s_) {
+    if (!p->fft_streams || p->nside < 2 || e != cudaSuccess) return;
+    cudaStream_t st = static_cast<cudaStream_t*>(p->fft_streams)[which];
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->fft_events) + 2 * which;
+    e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[0], 0);
+    if (e == cudaSuccess) {
+      side = st;
+      join_ev = ev[1];
+    }
+  }
+  cudaError_t join(cudaError_t e) {
+    if (!join_ev) return e;
+    cudaError_t e2 = cudaEventRecord(join_ev, side);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, join_ev, 0);
+    return e != cudaSuccess ? e : e2;
+  }
+};
+
 template <typename T>
 cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   using V = C2<T>;
@@ -529,28 +625,33 @@ cudaError_t launch_r2c(const hpx_plan_s* p, const T* map, cudaStream_t s) {
   // spectrum component here (zeroed first)
   unsigned* bmax = (sizeof(T) == 4 && p->tc_mode > 0) ? p->d_bmax : nullptr;
   if (e == cudaSuccess && bmax) e = cudaMemsetAsync(bmax, 0, sizeof(unsigned) * p->nbatch, s);
+  Fork f(p, 0, s, e);
   for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
     if (e != cudaSuccess || L.nslots <= 0) continue;
-    k_ring_r2c<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
+    k_ring_r2c<T><<<grid_of(L, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V),
+                    L.caps ? s : f.side>>>(
         map, (V*)p->d_spec, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_chirp,
         (const V*)p->d_tw, p->logtw, p->npix, p->nspec, L.caps, p->nside, bmax);
     e = cudaGetLastError();
   }
-  return e;
+  return f.join(e);
 }
 
 template <typename T>
 cudaError_t launch_c2r(const hpx_plan_s* p, T* map, bool scale_by_weight, cudaStream_t s) {
   using V = C2<T>;
-  cudaError_t e = allow_max_smem(k_ring_c2r<T>);
+  cudaError_t e = allow_max_smem(k_ring_c2r<T, 256>);
+  if (e == cudaSuccess) e = allow_max_smem(k_ring_c2r<T, 512>);
+  Fork f(p, 1, s, e);
   for (const RingLaunch L : {belt_launch(p), caps_launch(p)}) {
     if (e != cudaSuccess || L.nslots <= 0) continue;
-    k_ring_c2r<T><<<dim3(L.nslots, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), s>>>(
+    auto kern = L.threads <= 256 ? k_ring_c2r<T, 256> : k_ring_c2r<T, 512>;
+    kern<<<grid_of(L, p->nbatch), L.threads, padded_len(size_t(1) << L.logm) * sizeof(V), L.caps ? s : f.side>>>(
         (const V*)p->d_F, map, p->d_ring, (const V*)p->d_etab, (const V*)p->d_btab, (const V*)p->d_chirp,
         (const V*)p->d_tw, p->logtw, p->npix, p->nring, p->mmax, scale_by_weight ? 1 : 0, L.caps, p->nside);
     e = cudaGetLastError();
   }
-  return e;
+  return f.join(e);
 }
 
 template cudaError_t build_fft_tables<float>(hpx_plan_s*, cudaStream_t);

@@ -136,6 +136,9 @@ struct hpx_plan_s {
   alignas(64) unsigned char tm_stage[2][128];
   alignas(64) unsigned char tm_stagelo[2][128];
   void* copy_stream;   // cudaStream_t
+  void* fft_streams;   // cudaStream_t[2]: the belt-ring launches of the analysis / synthesis ring
+                       // transforms, beside the cap-ring launch on the caller's stream
+  void* fft_events;    // cudaEvent_t[4]: fork / join of the analysis, then of the synthesis
   void* stage_events;  // cudaEvent_t[4]: copied[2], free[2]
   int* d_status;       // device-side wait status (HPX_OK or HPX_ERR_TIMEOUT)
   int test_withhold;   // test support: tile kernels issue no copies (hpx_plan_test_withhold_copies)

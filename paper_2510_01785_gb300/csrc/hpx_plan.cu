@@ -137,6 +137,18 @@ static void plan_free(hpx_plan_s* p) {
       if (st[i]) cudaStreamDestroy(st[i]);
     delete[] st;
   }
+  if (p->fft_events) {
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->fft_events);
+    for (int i = 0; i < 4; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+    delete[] ev;
+  }
+  if (p->fft_streams) {
+    cudaStream_t* st = static_cast<cudaStream_t*>(p->fft_streams);
+    for (int i = 0; i < 2; ++i)
+      if (st[i]) cudaStreamDestroy(st[i]);
+    delete[] st;
+  }
   void* ptrs[] = {p->d_ring, p->d_etab, p->d_btab, p->d_chirp, p->d_tw, p->d_cmm, p->d_coef_c, p->d_coef_cf, p->d_coef_p,
                   p->d_coef_pf, p->d_lc, p->d_mu0, p->d_mu1, p->d_spec, p->d_F, p->d_io_map, p->d_io_alm,
                   p->d_tab, p->d_tab_off, p->d_tab_lstart, p->d_gt, p->d_status, p->d_at, p->d_achunk,
@@ -443,6 +455,21 @@ static hpx_status create_plan(int nside, int lmax, int mmax, int nbatch, hpx_dty
   if (e != cudaSuccess) {
     plan_free(p);
     return cuda_fail(e, "cudaStreamCreate");
+  }
+  {
+    // the ring transforms' second stream (belt rings beside the cap rings)
+    // and its fork / join events; kept by the plan once all of them exist
+    cudaStream_t* fs = new cudaStream_t[2]();
+    cudaEvent_t* fe = new cudaEvent_t[4]();
+    p->fft_streams = fs;
+    p->fft_events = fe;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&fs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&fe[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(s);
+      plan_free(p);
+      return cuda_fail(e, "ring-transform streams");
+    }
   }
   e = cudaMemsetAsync(p->d_status, 0, sizeof(int), s);
   if (e == cudaSuccess) {

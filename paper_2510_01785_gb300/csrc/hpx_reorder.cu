@@ -18,8 +18,15 @@
 // the ring's pixel count over four and s the belt rings' half-pixel shift
 // ((jr - nside) mod 2; 0 on the caps).
 //
-// The reorder kernels gather: thread t computes the xyf of target pixel t
-// and reads the source pixel with that xyf, so writes are coalesced.
+// The reorder kernel walks the faces in tiles of (x, y): one CTA per face
+// and T x T tile (T = min(32, nside)), so no pixel index has to be inverted.
+// Each pixel's source and target index follow from its xyf directly; the
+// tile's pixels are taken in the order of the target layout (Morton order
+// for NESTED, rows for FLAT, the tile's diagonals x + y = const by
+// increasing x for RING, each of which is a run of consecutive ring
+// pixels), so that a warp's writes are contiguous, and its reads stay within
+// the tile, whose source pixels the cache then holds.  All index arithmetic
+// is 32-bit (Npix < 2^31 for nside <= 8192).
 #include "hpx_internal.cuh"
 
 namespace hpx {
@@ -133,20 +140,88 @@ __device__ __forceinline__ long long from_xyf(int layout, long long nside, Xyf q
   return q.f * n2 + (long long)q.y * nside + q.x;  // FLAT
 }
 
-// out[b][t] = in[b][source(t)], elements of E bytes
-template <typename E>
-__global__ void k_reorder(const E* __restrict__ in, E* __restrict__ out, int nside, int nbatch, int from, int to,
-                          int* __restrict__ bad) {
-  const long long npix = 12LL * nside * nside;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < npix;
-       t += (long long)gridDim.x * blockDim.x) {
-    const Xyf q = to_xyf(to, nside, t);
-    if (q.f < 0) {  // no face found: cannot happen for a valid index
-      atomicExch(bad, 1);
-      continue;
+// index of pixel q in `layout`, 32-bit (Npix < 2^31)
+__device__ __forceinline__ int index_of(int layout, int nside, Xyf q) {
+  const int n2 = nside * nside;
+  if (layout == HPX_NESTED) return q.f * n2 + (int)(spread_bits((unsigned)q.x) | (spread_bits((unsigned)q.y) << 1));
+  if (layout == HPX_FLAT) return q.f * n2 + q.y * nside + q.x;
+  // RING: ring jr (1-based) of the face's pixel, then its position around it
+  const int jr = kJr[q.f] * nside - q.x - q.y - 1;
+  int nr, start, shift = 0;
+  if (jr < nside) {
+    nr = jr;
+    start = 2 * jr * (jr - 1);
+  } else if (jr > 3 * nside) {
+    nr = 4 * nside - jr;
+    start = 12 * n2 - 2 * nr * (nr + 1);
+  } else {
+    nr = nside;
+    start = 2 * nside * (nside - 1) + (jr - nside) * 4 * nside;
+    shift = (jr - nside) & 1;
+  }
+  int jp = (kJp[q.f] * nr + q.x - q.y + 1 + shift) / 2;
+  if (jp > 4 * nr) jp -= 4 * nr;
+  if (jp < 1) jp += 4 * nr;
+  return start + jp - 1;
+}
+
+// (x, y) within a T x T tile of the i-th pixel in the target layout's order
+__device__ __forceinline__ void tile_pixel(int to, int i, int T, int logT, int& lx, int& ly) {
+  if (to == HPX_NESTED) {
+    lx = (int)pack_bits((unsigned)i);
+    ly = (int)pack_bits((unsigned)i >> 1);
+  } else if (to == HPX_FLAT) {
+    lx = i & (T - 1);
+    ly = i >> logT;
+  } else {
+    // diagonals c = x + y = 0 .. 2T-2 (lengths 1 .. T .. 1), x increasing
+    // along each; the second half is the first mirrored through the centre
+    const int half = T * (T + 1) / 2;
+    const bool second = i >= half;
+    const int k = second ? T * T - 1 - i : i;
+    int c = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
+    while (c * (c + 1) / 2 > k) --c;
+    while ((c + 1) * (c + 2) / 2 <= k) ++c;
+    const int pos = k - c * (c + 1) / 2;  // 0 .. c
+    if (!second) {
+      lx = pos;
+      ly = c - pos;
+    } else {
+      lx = T - 1 - pos;
+      ly = T - 1 - (c - pos);
     }
-    const long long src = from_xyf(from, nside, q);
-    for (int b = 0; b < nbatch; ++b) out[(long long)b * npix + t] = in[(long long)b * npix + src];
+  }
+}
+
+// out[b][index_to(q)] = in[b][index_from(q)] for every pixel q, elements of
+// E bytes.  Grid: ((nside / T)^2 tiles in Morton order, 12 faces), 256 threads.
+template <typename E>
+__global__ void __launch_bounds__(256)
+k_reorder(const E* __restrict__ in, E* __restrict__ out, int nside, int nbatch, int from, int to, int logT) {
+  const int T = 1 << logT, f = blockIdx.y;
+  const int x0 = (int)pack_bits(blockIdx.x) << logT, y0 = (int)pack_bits(blockIdx.x >> 1) << logT;
+  const long long npix = 12LL * nside * nside;
+  for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+    int lx, ly;
+    tile_pixel(to, i, T, logT, lx, ly);
+    const Xyf q{x0 + lx, y0 + ly, f};
+    const E* src = in + index_of(from, nside, q);
+    E* dst = out + index_of(to, nside, q);
+    int b = 0;
+    for (; b + 4 <= nbatch; b += 4) {  // four loads in flight
+      const E v0 = src[0], v1 = src[npix], v2 = src[2 * npix], v3 = src[3 * npix];
+      dst[0] = v0;
+      dst[npix] = v1;
+      dst[2 * npix] = v2;
+      dst[3 * npix] = v3;
+      src += 4 * npix;
+      dst += 4 * npix;
+    }
+    for (; b < nbatch; ++b) {
+      *dst = *src;
+      src += npix;
+      dst += npix;
+    }
   }
 }
 
@@ -204,28 +279,26 @@ hpx_status hpx_reorder(int nside, int nbatch, size_t elem_bytes, hpx_layout from
     set_error("hpx_reorder: buffers must be aligned to the element size");
     return HPX_ERR_INVALID;
   }
-  int* bad = nullptr;
-  cudaError_t e = cudaGetSymbolAddress((void**)&bad, g_layout_bad);
-  if (e != cudaSuccess) return cuda_fail(e, "hpx_reorder");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const long long npix = 12LL * nside * nside;
+  int logT = 0;
+  while ((1 << logT) < nside && logT < 5) ++logT;  // T = min(32, nside)
+  const int per_side = nside >> logT;
+  const dim3 grid(per_side * per_side, 12);
   switch (elem_bytes) {
     case 4:
-      k_reorder<float><<<grid_for(npix), 256, 0, s>>>((const float*)in, (float*)out, nside, nbatch, from, to, bad);
+      k_reorder<float><<<grid, 256, 0, s>>>((const float*)in, (float*)out, nside, nbatch, from, to, logT);
       break;
     case 8:
-      k_reorder<double><<<grid_for(npix), 256, 0, s>>>((const double*)in, (double*)out, nside, nbatch, from, to,
-                                                       bad);
+      k_reorder<double><<<grid, 256, 0, s>>>((const double*)in, (double*)out, nside, nbatch, from, to, logT);
       break;
     case 16:
-      k_reorder<double2><<<grid_for(npix), 256, 0, s>>>((const double2*)in, (double2*)out, nside, nbatch, from, to,
-                                                        bad);
+      k_reorder<double2><<<grid, 256, 0, s>>>((const double2*)in, (double2*)out, nside, nbatch, from, to, logT);
       break;
     default:
       set_error("hpx_reorder: elem_bytes must be 4, 8 or 16, got %zu", elem_bytes);
       return HPX_ERR_INVALID;
   }
-  e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HPX_OK : cuda_fail(e, "hpx_reorder");
 }
 

@@ -16,20 +16,25 @@ import bench  # noqa: E402
 
 
 def _tree(tmp_path, sources):
+    """A stand-in source tree; returns the hash of the tile kernels' sources
+    (hpx_tc.cu, hpx_internal.cuh, include/hpx.h, in that order)."""
     src = tmp_path / "paper_2510_01785_gb300" / "csrc"
     src.mkdir(parents=True)
+    (tmp_path / "include").mkdir()
     for name, text in sources.items():
-        (src / name).write_text(text)
+        (tmp_path / name).write_text(text)
     (tmp_path / "profiles").mkdir()
     h = hashlib.sha256()
-    for name in sorted(sources):
-        if name.endswith((".cu", ".cuh")):
-            h.update(sources[name].encode())
+    for name in ("paper_2510_01785_gb300/csrc/hpx_tc.cu", "paper_2510_01785_gb300/csrc/hpx_internal.cuh",
+                 "include/hpx.h"):
+        h.update(sources[name].encode())
     return h.hexdigest()[:16]
 
 
 def test_kernel_traffic_matches_source_hash(tmp_path, monkeypatch):
-    sha = _tree(tmp_path, {"a.cu": "x", "b.cuh": "y", "notes.txt": "ignored"})
+    C = "paper_2510_01785_gb300/csrc/"
+    sha = _tree(tmp_path, {C + "hpx_tc.cu": "x", C + "hpx_internal.cuh": "y", "include/hpx.h": "z",
+                           C + "hpx_fft.cu": "w"})
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.kernel_traffic("k_legendre_tc<analysis>") is None  # no summary file
     (tmp_path / "profiles" / "dram_traffic.txt").write_text(
@@ -40,10 +45,11 @@ def test_kernel_traffic_matches_source_hash(tmp_path, monkeypatch):
     # captured from another source: stale, so no figure
     assert bench.kernel_traffic("k_legendre_tc<synthesis>") is None
     assert bench.kernel_traffic("k_unknown") is None
-    # a change to any .cu/.cuh file makes every line stale; other files do not count
-    (tmp_path / "paper_2510_01785_gb300" / "csrc" / "notes.txt").write_text("changed")
+    # a change to a source the tiles are not built from does not count; one
+    # to any of theirs makes every line stale
+    (tmp_path / C / "hpx_fft.cu").write_text("changed")
     assert bench.kernel_traffic("k_legendre_tc<analysis>") == 123.5
-    (tmp_path / "paper_2510_01785_gb300" / "csrc" / "b.cuh").write_text("y2")
+    (tmp_path / C / "hpx_internal.cuh").write_text("y2")
     assert bench.kernel_traffic("k_legendre_tc<analysis>") is None
 
 
