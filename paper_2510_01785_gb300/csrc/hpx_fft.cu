@@ -323,25 +323,33 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
     __syncthreads();
     fft_pow2<false>(buf, logm, tw, logtw, static_cast<const V*>(nullptr), 1);
   } else {
-    for (int n = threadIdx.x; n < M; n += blockDim.x)
-      buf[spos(n)] = n < H ? (blue ? cmul(x2[n], C[n]) : x2[n]) : cmk<V>(0, 0);
+#pragma unroll 4
+    for (int n = threadIdx.x; n < H; n += blockDim.x) buf[spos(n)] = blue ? cmul(x2[n], C[n]) : x2[n];
+    for (int n = H + threadIdx.x; n < M; n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
     __syncthreads();
     ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   }
-  // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i)
+  // X[k] = (Z[k] + conj Z[H-k]) / 2 + exp(-2 pi i k / N) (Z[k] - conj Z[H-k]) / (2 i),
+  // indices of Z mod H.  One thread forms X[k] and X[H-k], k <= H/2, from the
+  // same two values: with e, d the two halves and P = E[2k] d / i, X[k] = e + P
+  // and, as E[2(H-k)] = E[N-2k] = -conj E[2k], X[H-k] = (e.x - P.x, P.y - e.y).
   V* out = spec + (long long)b * nspec + R.specoff;
   T amax = 0;  // largest |component| written by this thread
-  for (int k = threadIdx.x; k <= H; k += blockDim.x) {
-    const int k1 = (k == H) ? 0 : k;
-    const int k2 = (k == 0) ? 0 : H - k;
-    const V zk = blue ? cmul(buf[spos(k1)], C[k1]) : buf[spos(k1)];
-    const V zc = cconj(blue ? cmul(buf[spos(k2)], C[k2]) : buf[spos(k2)]);
+  for (int k = threadIdx.x; k <= (H >> 1); k += blockDim.x) {
+    const int kc = (k == 0) ? 0 : H - k;
+    V zk = buf[spos(k)], zc = buf[spos(kc)];
+    if (blue) {
+      zk = cmul(zk, C[k]);
+      zc = cmul(zc, C[kc]);
+    }
+    zc = cconj(zc);
     const V e = cscale(cadd(zk, zc), (T)0.5);
     const V d = cscale(csub(zk, zc), (T)0.5);
-    const V o = cmk<V>(d.y, -d.x);
-    const V X = cadd(e, cmul(E[2 * k], o));
+    const V P = cmul(E[2 * k], cmk<V>(d.y, -d.x));
+    const V X = cadd(e, P), Xc = cmk<V>(e.x - P.x, P.y - e.y);
     out[k] = X;
-    amax = fmax(amax, fmax(fabs(X.x), fabs(X.y)));
+    if (H - k != k) out[H - k] = Xc;
+    amax = fmax(amax, fmax(fmax(fabs(X.x), fabs(X.y)), fmax(fabs(Xc.x), fabs(Xc.y))));
   }
   // the channel's largest spectrum component, for the 16-bit operand scale
   // of the tensor-core analysis (float plans only; blockDim is a multiple of 32)
@@ -378,18 +386,30 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   const V* C = blue ? chirp + chirp_offset(N) : nullptr;
   const V* Fy = F + ((long long)b * nring + y) * (mmax + 1);
 
-  auto term = [&](int m) -> V {  // F_m exp(+i pi sigma m / N)
+  // F_m exp(+i pi sigma m / N) = F_m conj E[ip], ip = sigma m mod 2N.  The
+  // aliases of bin k are m = k + t N and m = t N - k; their phase indices
+  // advance by step = sigma N mod 2N (0 or N) per alias, so one reduction per
+  // bin gives all of them.
+  auto term = [&](int m, unsigned ip) -> V {
     V f = Fy[m];
     if (m == 0) f.y = 0;
-    return cmul(f, cconj(E[((unsigned)sig * (unsigned)m) % twoN]));
+    return cmul(f, cconj(E[ip]));
   };
+  auto wrap = [&](unsigned i) { return i >= twoN ? i - twoN : i; };  // i < 4N
+  const unsigned step = ((unsigned)sig * (unsigned)N) % twoN;
   const int per_bin = (mmax + N) / N;
   if (per_bin > 8) {  // few bins, many aliases: one warp per bin
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // lane l takes the aliases t = l, l + 32, ...: its phase index is the
+    // same for all of them (32 step = 0 mod 2N)
+    const unsigned lstep = (unsigned)(((unsigned long long)lane * step) % twoN);
     for (int k = warp; k <= H; k += nw) {
+      const unsigned ip0 = ((unsigned)sig * (unsigned)k) % twoN;
+      const unsigned ia = wrap(ip0 + lstep), ib = wrap(wrap(step + lstep) + (twoN - ip0));
       V acc = cmk<V>(0, 0);
-      for (long long m = k + (long long)lane * N; m <= mmax; m += 32LL * N) acc = cadd(acc, term((int)m));
-      for (long long m = N - k + (long long)lane * N; m <= mmax; m += 32LL * N) acc = cadd(acc, cconj(term((int)m)));
+      for (long long m = k + (long long)lane * N; m <= mmax; m += 32LL * N) acc = cadd(acc, term((int)m, ia));
+      for (long long m = N - k + (long long)lane * N; m <= mmax; m += 32LL * N)
+        acc = cadd(acc, cconj(term((int)m, ib)));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -397,11 +417,26 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
       }
       if (lane == 0) buf[spos(k)] = acc;
     }
+  } else if (mmax < N) {
+    // at most one alias of each kind per bin (m = k and m = N - k): loads of
+    // several bins in flight at once
+#pragma unroll 4
+    for (int k = threadIdx.x; k <= H; k += blockDim.x) {
+      unsigned ip = (unsigned)sig * (unsigned)k;
+      if (ip >= twoN) ip %= twoN;
+      V acc = cmk<V>(0, 0);
+      if (k <= mmax) acc = term(k, ip);
+      if (N - k <= mmax) acc = cadd(acc, cconj(term(N - k, wrap(step + (twoN - ip)))));
+      buf[spos(k)] = acc;
+    }
   } else {
     for (int k = threadIdx.x; k <= H; k += blockDim.x) {
+      unsigned ip = (unsigned)sig * (unsigned)k;
+      if (ip >= twoN) ip %= twoN;
+      unsigned iq = wrap(step + (twoN - ip));  // alias m = N - k
       V acc = cmk<V>(0, 0);
-      for (int m = k; m <= mmax; m += N) acc = cadd(acc, term(m));
-      for (int m = N - k; m <= mmax; m += N) acc = cadd(acc, cconj(term(m)));
+      for (int m = k; m <= mmax; m += N, ip = wrap(ip + step)) acc = cadd(acc, term(m, ip));
+      for (int m = N - k; m <= mmax; m += N, iq = wrap(iq + step)) acc = cadd(acc, cconj(term(m, iq)));
       buf[spos(k)] = acc;
     }
   }
@@ -416,14 +451,22 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
     // buffer -- and that pass writes elements 16 j + r
     const int nb = H >> 4, j = threadIdx.x;
     V v[16];
-    if (j < nb) {
+    auto conj_z = [&](V dk, V dc, V e) {
+      const V s1 = cadd(dk, cconj(dc)), d1 = csub(dk, cconj(dc));
+      const V t1 = cmul(cconj(e), d1);
+      return cmk<V>(s1.x - t1.y, -(s1.y + t1.x));
+    };
+    if (j < nb && (nb & 15) == 0) {
+      // k = j + r nb and H - k sit at spos(j) + r istr and spos(H - j) - r istr
+      const int istr = nb + (nb >> 4);
+      const V *pa = buf + spos(j), *pb = buf + spos(H - j), *ek = E + 2 * j;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = conj_z(pa[r * istr], pb[-r * istr], ek[2 * r * nb]);
+    } else if (j < nb) {
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int k = j + r * nb;
-        const V dk = buf[spos(k)], dc = buf[spos(H - k)];
-        const V s1 = cadd(dk, cconj(dc)), d1 = csub(dk, cconj(dc));
-        const V t1 = cmul(cconj(E[2 * k]), d1);
-        v[r] = cmk<V>(s1.x - t1.y, -(s1.y + t1.x));
+        v[r] = conj_z(buf[spos(k)], buf[spos(H - k)], E[2 * k]);
       }
     }
     __syncthreads();
@@ -460,6 +503,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   }
   const T sc = scale_by_weight ? (T)R.w : (T)1;
   V* out = reinterpret_cast<V*>(map + (long long)b * npix + R.start);
+#pragma unroll 4
   for (int n = threadIdx.x; n < H; n += blockDim.x) {
     const V r = blue ? cmul(buf[spos(n)], C[n]) : buf[spos(n)];
     out[n] = cmk<V>(r.x * sc, -r.y * sc);
