@@ -388,35 +388,41 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   const V* Fy = F + ((long long)b * nring + y) * (mmax + 1);
 
   // F_m exp(+i pi sigma m / N) = F_m conj E[ip], ip = sigma m mod 2N.  The
-  // aliases of bin k are m = k + t N and m = t N - k; their phase indices
-  // advance by step = sigma N mod 2N (0 or N) per alias, so one reduction per
-  // bin gives all of them.
-  auto term = [&](int m, unsigned ip) -> V {
-    V f = Fy[m];
-    if (m == 0) f.y = 0;
-    return cmul(f, cconj(E[ip]));
-  };
+  // aliases of bin k are m = k + t N and m = (t+1) N - k, t >= 0; their phase
+  // indices differ from the first one's by t sigma N mod 2N = t step, step =
+  // sigma N mod 2N (0 or N), and E[i + N] = -E[i].  So each kind of alias is
+  // summed as F (signs alternating in t where step = N), and the sum takes
+  // the first alias's phase once: D[k] = phA SA + conj(phB SB).
   auto wrap = [&](unsigned i) { return i >= twoN ? i - twoN : i; };  // i < 4N
   const unsigned step = ((unsigned)sig * (unsigned)N) % twoN;
+  const bool alt = step != 0;
+  auto fval = [&](int m) {  // F_m, with Im F_0 dropped (real maps)
+    V f = Fy[m];
+    if (m == 0) f.y = 0;
+    return f;
+  };
   const int per_bin = (mmax + N) / N;
   if (per_bin > 8) {  // few bins, many aliases: one warp per bin
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // lane l takes the aliases t = l, l + 32, ...: its phase index is the
-    // same for all of them (32 step = 0 mod 2N)
-    const unsigned lstep = (unsigned)(((unsigned long long)lane * step) % twoN);
+    // lane l takes the aliases t = l, l + 32, ...: all of one sign
+    const T sgn = (alt && (lane & 1)) ? (T)-1 : (T)1;
     for (int k = warp; k <= H; k += nw) {
-      const unsigned ip0 = ((unsigned)sig * (unsigned)k) % twoN;
-      const unsigned ia = wrap(ip0 + lstep), ib = wrap(wrap(step + lstep) + (twoN - ip0));
-      V acc = cmk<V>(0, 0);
-      for (long long m = k + (long long)lane * N; m <= mmax; m += 32LL * N) acc = cadd(acc, term((int)m, ia));
-      for (long long m = N - k + (long long)lane * N; m <= mmax; m += 32LL * N)
-        acc = cadd(acc, cconj(term((int)m, ib)));
+      V sa = cmk<V>(0, 0), sb = cmk<V>(0, 0);
+      for (int m = k + lane * N; m <= mmax; m += 32 * N) sa = cadd(sa, fval(m));
+      for (int m = (lane + 1) * N - k; m <= mmax; m += 32 * N) sb = cadd(sb, Fy[m]);
+      sa = cscale(sa, sgn);
+      sb = cscale(sb, sgn);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        sa.x += __shfl_xor_sync(0xffffffffu, sa.x, off);
+        sa.y += __shfl_xor_sync(0xffffffffu, sa.y, off);
+        sb.x += __shfl_xor_sync(0xffffffffu, sb.x, off);
+        sb.y += __shfl_xor_sync(0xffffffffu, sb.y, off);
       }
-      if (lane == 0) buf[spos(k)] = acc;
+      if (lane == 0) {
+        const unsigned ip = ((unsigned)sig * (unsigned)k) % twoN;
+        buf[spos(k)] = cadd(cmul(sa, cconj(E[ip])), cconj(cmul(sb, cconj(E[wrap(step + (twoN - ip))]))));
+      }
     }
   } else if (mmax < N) {
     // at most one alias of each kind per bin (m = k and m = N - k): loads of
@@ -426,19 +432,26 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
       unsigned ip = (unsigned)sig * (unsigned)k;
       if (ip >= twoN) ip %= twoN;
       V acc = cmk<V>(0, 0);
-      if (k <= mmax) acc = term(k, ip);
-      if (N - k <= mmax) acc = cadd(acc, cconj(term(N - k, wrap(step + (twoN - ip)))));
+      if (k <= mmax) acc = cmul(fval(k), cconj(E[ip]));
+      if (N - k <= mmax) acc = cadd(acc, cconj(cmul(Fy[N - k], cconj(E[wrap(step + (twoN - ip))]))));
       buf[spos(k)] = acc;
     }
   } else {
     for (int k = threadIdx.x; k <= H; k += blockDim.x) {
       unsigned ip = (unsigned)sig * (unsigned)k;
       if (ip >= twoN) ip %= twoN;
-      unsigned iq = wrap(step + (twoN - ip));  // alias m = N - k
-      V acc = cmk<V>(0, 0);
-      for (int m = k; m <= mmax; m += N, ip = wrap(ip + step)) acc = cadd(acc, term(m, ip));
-      for (int m = N - k; m <= mmax; m += N, iq = wrap(iq + step)) acc = cadd(acc, cconj(term(m, iq)));
-      buf[spos(k)] = acc;
+      // even and odd t apart, then combined with the sign of odd t
+      V a0 = cmk<V>(0, 0), a1 = a0, b0 = a0, b1 = a0;
+      for (int m = k; m <= mmax; m += 2 * N) {
+        a0 = cadd(a0, fval(m));
+        if (m + N <= mmax) a1 = cadd(a1, Fy[m + N]);
+      }
+      for (int m = N - k; m <= mmax; m += 2 * N) {
+        b0 = cadd(b0, Fy[m]);
+        if (m + N <= mmax) b1 = cadd(b1, Fy[m + N]);
+      }
+      const V sa = alt ? csub(a0, a1) : cadd(a0, a1), sb = alt ? csub(b0, b1) : cadd(b0, b1);
+      buf[spos(k)] = cadd(cmul(sa, cconj(E[ip])), cconj(cmul(sb, cconj(E[wrap(step + (twoN - ip))]))));
     }
   }
   __syncthreads();
@@ -663,6 +676,11 @@ static int ring_launches(const hpx_plan_s* p, RingLaunch* out) {
     hi = lo;
   }
   return k;
+}
+
+int ring_launch_count(const hpx_plan_s* p) {
+  RingLaunch ls[4];
+  return ring_launches(p, ls);
 }
 
 static dim3 grid_of(const RingLaunch& L, int nbatch) {

@@ -203,11 +203,14 @@ static cudaError_t staged(hpx_plan_s* p, int stage, cudaStream_t s, F&& f) {
   return e != cudaSuccess ? e : e2;
 }
 
+// kernel launches of one ring-transform stage (hpx_fft.cu)
+int ring_launch_count(const hpx_plan_s* p);
+
 template <typename T>
 static cudaError_t run_analysis(hpx_plan_s* p, const void* map, void* alm, bool weighted, double mfac,
                                 cudaStream_t s) {
   cudaError_t e = staged(p, 0, s, [&](int* n) {
-    *n = p->nside > 1 ? 2 : 1;  // belt and cap rings
+    *n = ring_launch_count(p);  // belt and cap rings
     return launch_r2c<T>(p, static_cast<const T*>(map), s);
   });
   if (e != cudaSuccess) return e;
@@ -259,7 +262,7 @@ static cudaError_t run_synthesis(hpx_plan_s* p, const void* alm, void* map, bool
   }
   if (e == cudaSuccess)
     e = staged(p, 3, s, [&](int* n) {
-      *n = p->nside > 1 ? 2 : 1;
+      *n = ring_launch_count(p);
       return launch_c2r<T>(p, static_cast<T*>(map), weighted, s);
     });
   return e;
