@@ -653,15 +653,26 @@ static int cap_logm(int i) {  // log2 of the transform length of cap ring i (as 
   while ((1LL << L) < M) ++L;
   return L;
 }
+// Below this Nside the transforms are small enough to be bound by launch
+// latency (Nside 32: 131 us for an FP64 analysis + synthesis as two launches
+// a stage on one stream, 197 us as four on two), and every cap ring fits 64
+// threads anyway: one cap launch, no second stream.
+constexpr int kSplitNside = 512;
+
 static int ring_launches(const hpx_plan_s* p, RingLaunch* out) {
   const int ns = p->nside;
   int logh = 0;
   while ((1 << logh) < 2 * ns) ++logh;
   int k = 0;
-  out[k++] = {0, 0, 0, 2 * ns + 1, logh, fft_threads(logh), 1};
+  const bool split = ns >= kSplitNside;
+  out[k++] = {0, 0, 0, 2 * ns + 1, logh, fft_threads(logh), split ? 1 : 0};
   if (ns < 2) return k;
   int lc = 0;
   for (int i = 1; i < ns; ++i) lc = cap_logm(i) > lc ? cap_logm(i) : lc;
+  if (!split) {  // one launch for all cap rings, everything on the caller's stream
+    out[k++] = {1, 1, ns - 1, 2 * (ns - 1), lc, fft_threads(lc), 0};
+    return k;
+  }
   // i ranges (lo, hi]: (2^(lc-3), ns-1], (2^(lc-4), 2^(lc-3)], (0, 2^(lc-4)]
   int hi = ns - 1;
   for (int c = 0; c < 3 && hi >= 1; ++c) {
@@ -696,7 +707,7 @@ struct Fork {
   cudaStream_t s, side;
   cudaEvent_t join_ev = nullptr;
   Fork(const hpx_plan_s* p, int which, cudaStream_t s_, cudaError_t& e) : s(s_), side(s_) {
-    if (!p->fft_streams || p->nside < 2 || e != cudaSuccess) return;
+    if (!p->fft_streams || p->nside < kSplitNside || e != cudaSuccess) return;
     cudaStream_t st = static_cast<cudaStream_t*>(p->fft_streams)[which];
     cudaEvent_t* ev = static_cast<cudaEvent_t*>(p->fft_events) + 2 * which;
     e = cudaEventRecord(ev[0], s);
