@@ -31,7 +31,11 @@
  * Pointers must be 16-byte aligned; map and alm must not overlap.
  *
  * Calls are asynchronous and ordered on the stream passed in (NULL = the
- * legacy default stream).  A plan owns device workspace: one part for its
+ * legacy default stream).  From Nside 512 a ring-transform stage forks part
+ * of its kernels onto a plan-owned second stream (one for analyses, one for
+ * syntheses) and joins it back before the call's next work on the caller's
+ * stream, so the call stays ordered there and a stream capture records the
+ * fork and the join.  A plan owns device workspace: one part for its
  * analyses (hpx_map2alm, hpx_alm2map_adjoint, hpx_map2alm_n) and one for
  * its syntheses (hpx_alm2map, hpx_map2alm_adjoint, hpx_alm2map_n).  So one
  * analysis and one synthesis may run at the same time on two streams
