@@ -626,8 +626,8 @@ cudaError_t build_fft_tables(hpx_plan_s* p, cudaStream_t s) {
 }
 
 // Launch shapes.  The belt rings (2 nside + 1 of them, H = 2 nside) are one
-// launch.  The cap rings (H = 2i, i < nside; Bluestein length 2^L with
-// 4i - 1 <= 2^L < 8i - 2 unless 2i is a power of two) are three, by size:
+// launch.  From Nside 512 the cap rings (H = 2i, i < nside; Bluestein length
+// 2^L with 4i - 1 <= 2^L < 8i - 2 unless 2i is a power of two) are three, by size:
 // the rings of the longest length 2^Lc (i > 2^(Lc-3)), of half that length
 // (i > 2^(Lc-4)), and the rest, each launch with the threads and shared
 // memory of its own longest transform, so that no CTA carries idle threads
@@ -700,9 +700,9 @@ static dim3 grid_of(const RingLaunch& L, int nbatch) {
 
 // The launches of the second stream run beside those on the caller's
 // stream: forked from the caller's stream before the launches and joined
-// back after them, so the call stays ordered on the
-// caller's stream (and captures into a graph as a fork and a join).  `which`
-// picks the stream and events of the analysis (0) or the synthesis (1).
+// back after them, so the call stays ordered on the caller's stream (and
+// captures into a graph as a fork and a join).  `which` picks the stream and
+// events of the analysis (0) or the synthesis (1).
 struct Fork {
   cudaStream_t s, side;
   cudaEvent_t join_ev = nullptr;

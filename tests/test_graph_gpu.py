@@ -1,6 +1,8 @@
 """Stream capture: the device-buffer transforms of a resident plan allocate
 nothing and never wait on the host, so a CUDA graph can record them; its
-replays give the eager calls' results bit for bit."""
+replays give the eager calls' results bit for bit.  From Nside 512 the ring
+stages fork onto the plan's second stream and join back, which the capture
+records too."""
 import numpy as np
 import pytest
 import torch
@@ -12,8 +14,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("case", [(32, 95, 1, "f64", {}), (64, 191, 8, "f32", {}),
                                   (64, 191, 8, "f32", dict(lambda_table=True, tensor_cores=True)),
-                                  (64, 191, 9, "bf16x3", {})],
-                         ids=["f64", "f32-recompute", "f32-tensor-cores", "bf16x3"])
+                                  (64, 191, 9, "bf16x3", {}), (512, 127, 2, "f32", {})],
+                         ids=["f64", "f32-recompute", "f32-tensor-cores", "bf16x3",
+                              "f32-nside512-forked-ring-stages"])
 def test_transforms_replay_from_a_cuda_graph(case):
     import paper_2510_01785_gb300 as hpx
     nside, lmax, nb, dtype, kw = case
