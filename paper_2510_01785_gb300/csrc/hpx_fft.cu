@@ -73,9 +73,12 @@ template <bool INV, typename V> __device__ __forceinline__ V rot90(V x) {
 
 // In-register DFT of length R in {2, 4, 8, 16} (8: decimation in frequency
 // down to length 2; 16: two levels of length 4), sign -1 (forward) or +1
-// (INV).  Natural order in and out.
-template <int R, bool INV, typename V>
+// (INV).  Natural order in and out.  For R = 16, NZ = 8 says inputs 8..15
+// are zero and NO = 8 that only outputs 0..7 are wanted (the others are then
+// left unset).
+template <int R, bool INV, int NZ = R, int NO = R, typename V>
 __device__ __forceinline__ void dft_small(V (&v)[R]) {
+  static_assert((NZ == R && NO == R) || R == 16, "pruning is for radix 16");
   using T = decltype(V::x);
   if constexpr (R == 2) {
     const V a = v[0], b = v[1];
@@ -95,9 +98,17 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
     V y[4][4];
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) {
+      if constexpr (NZ == 8) {  // inputs 4 n1 + n2 with n1 >= 2 are zero
+        const V a = v[n2], b = v[4 + n2], rb = rot90<INV>(b);
+        y[n2][0] = cadd(a, b);
+        y[n2][1] = cadd(a, rb);
+        y[n2][2] = csub(a, b);
+        y[n2][3] = csub(a, rb);
+      } else {
 #pragma unroll
-      for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
-      dft_small<4, INV>(y[n2]);
+        for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+        dft_small<4, INV>(y[n2]);
+      }
     }
     // W16^e = (cos, -+sin)(pi e / 8) for e = n2 k1 in {1, 2, 3, 4, 6, 9}
     auto tw16 = [&](V x, T c, T s) { return INV ? cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c)
@@ -114,9 +125,16 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
       V z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-      dft_small<4, INV>(z);
+      if constexpr (NO == 8) {  // outputs k1 + 4 k2 with k2 < 2 only
+        const V u0 = cadd(z[0], z[2]), u1 = cadd(z[1], z[3]);
+        const V w0 = csub(z[0], z[2]), w1 = rot90<INV>(csub(z[1], z[3]));
+        v[k1] = cadd(u0, u1);
+        v[k1 + 4] = cadd(w0, w1);
+      } else {
+        dft_small<4, INV>(z);
 #pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+      }
     }
   } else {
     const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
@@ -148,7 +166,9 @@ __device__ __forceinline__ void dft_small(V (&v)[R]) {
 // length-R DFT and writes element r to (j - k) R + k + r Ns.  Each thread
 // handles butterflies threadIdx.x + q blockDim.x, q < Q (blockDim.x * Q * R
 // >= M).  tw[j] = exp(-2 pi i j / 2^logtw), j < 2^(logtw-1).
-template <int R, int Q, bool INV, typename V>
+// NZ < R: elements j + r M/R with r >= NZ are zero and not read; NO < R:
+// only outputs r < NO are written (radix 16, see dft_small).
+template <int R, int Q, bool INV, int NZ = R, int NO = R, typename V>
 __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V* __restrict__ tw, int logtw,
                                               const V* __restrict__ pre = nullptr) {
   const int nb = (1 << logm) / R;
@@ -167,17 +187,19 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
       // the butterfly's twiddle W^k, k = j mod Ns (k / (Ns R) < 1/2: inside
       // the stored half of the table), fetched before the barrier
       if (Ns > 1) wq[q] = tw[(j & (Ns - 1)) << (logtw - __ffs(Ns * R) + 1)];
+#pragma unroll
+      for (int r = NZ; r < R; ++r) v[q][r] = cmk<V>(0, 0);
       if (lin_in) {
         const V* src = buf + spos(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = src[r * istr];
+        for (int r = 0; r < NZ; ++r) v[q][r] = src[r * istr];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = buf[spos(j + r * nb)];
+        for (int r = 0; r < NZ; ++r) v[q][r] = buf[spos(j + r * nb)];
       }
       if (pre) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
+        for (int r = 0; r < NZ; ++r) v[q][r] = cmul(v[q][r], pre[j + r * nb]);  // pointwise product fused into the read
       }
     }
   }
@@ -209,15 +231,15 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
           }
         }
       }
-      dft_small<R, INV>(v[q]);
+      dft_small<R, INV, NZ, NO>(v[q]);
       const int base = (j - k) * R + k;
       if (lin_out) {
         V* dst = buf + spos(base);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[r * ostr] = v[q][r];
+        for (int r = 0; r < NO; ++r) dst[r * ostr] = v[q][r];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[spos(base + r * Ns)] = v[q][r];
+        for (int r = 0; r < NO; ++r) buf[spos(base + r * Ns)] = v[q][r];
       }
     }
   }
@@ -230,12 +252,25 @@ __device__ __forceinline__ void stockham_pass(V* buf, int logm, int Ns, const V*
 // are contiguous.
 // `pre`, if given, multiplies the input pointwise as the first pass reads it.
 // `first` passes are done already (the caller's own first pass).
+// `half_in`: the upper half of the input is zero (the first pass, radix 16,
+// neither reads nor transforms it); `half_out`: only the lower half of the
+// output is wanted (a last pass of radix 16 writes no other).
 template <bool INV, typename V>
 __device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, const V* __restrict__ pre = nullptr,
-                         int first = 0) {
-  int Ns = 1 << (4 * first);
-  for (int rest = logm - 4 * first; rest >= 4; rest -= 4) {
+                         int first = 0, bool half_in = false, bool half_out = false) {
+  int Ns = 1 << (4 * first), rest = logm - 4 * first;
+  if (half_in && Ns == 1 && rest >= 4) {
+    stockham_pass<16, 1, INV, 8, 16>(buf, logm, Ns, tw, logtw, pre);
+    Ns <<= 4;
+    rest -= 4;
+  }
+  const bool cut = half_out && (logm & 3) == 0 && rest >= 8;
+  for (; rest >= (cut ? 8 : 4); rest -= 4) {
     stockham_pass<16, 1, INV>(buf, logm, Ns, tw, logtw, Ns == 1 ? pre : nullptr);
+    Ns <<= 4;
+  }
+  if (cut) {
+    stockham_pass<16, 1, INV, 16, 8>(buf, logm, Ns, tw, logtw, static_cast<const V*>(nullptr));
     Ns <<= 4;
   }
   switch (logm & 3) {
@@ -247,15 +282,19 @@ __device__ void fft_pow2(V* buf, int logm, const V* __restrict__ tw, int logtw, 
 
 // DFT of length H of buf[0..H) (positions spos) in place, natural order: the
 // power-of-two FFT when H = 2^logm; otherwise Bluestein's convolution with the
-// kernel spectrum Bk (length 2^logm, natural order, scaled 1/2^logm), where
-// the caller has already multiplied buf[n] by the chirp C[n] = exp(-pi i n^2 /
-// H) and zero-filled [H, 2^logm), and multiplies output k by C[k] as it
-// reads it.  Caller has synchronised after filling buf.
+// kernel spectrum Bk (length M = 2^logm >= 2H, natural order, scaled 1/M),
+// where the caller has already multiplied buf[n] by the chirp C[n] =
+// exp(-pi i n^2 / H) and zero-filled [H, M/2), and multiplies output k < H by
+// C[k] as it reads it.  The convolution's input is zero in [M/2, M) and only
+// its outputs below H <= M/2 are used, so the first pass of the forward
+// transform reads half its inputs and the last pass of the inverse (when it
+// is of radix 16) writes half its outputs; [M/2, M) is left undefined.
+// Caller has synchronised after filling buf.
 template <typename V>
 __device__ void ring_dft(V* buf, int logm, bool bluestein, const V* __restrict__ Bk, const V* __restrict__ tw,
                          int logtw) {
-  fft_pow2<false>(buf, logm, tw, logtw);
-  if (bluestein) fft_pow2<true>(buf, logm, tw, logtw, Bk);
+  fft_pow2<false>(buf, logm, tw, logtw, static_cast<const V*>(nullptr), 0, bluestein);
+  if (bluestein) fft_pow2<true>(buf, logm, tw, logtw, Bk, 0, false, true);
 }
 
 // Offset of the chirp table of the cap ring of length N = 4i: i (i - 1).
@@ -326,7 +365,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   } else {
 #pragma unroll 4
     for (int n = threadIdx.x; n < H; n += blockDim.x) buf[spos(n)] = blue ? cmul(x2[n], C[n]) : x2[n];
-    for (int n = H + threadIdx.x; n < M; n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
+    for (int n = H + threadIdx.x; n < (blue ? M >> 1 : M); n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
     __syncthreads();
     ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   }
@@ -511,7 +550,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   // zero padding; position H (read above as D[H] for k = 0) is cleared by
   // thread 0 after its own read
   if (blue)
-    for (int n = H + threadIdx.x; n < (1 << logm); n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
+    for (int n = H + threadIdx.x; n < (1 << (logm - 1)); n += blockDim.x) buf[spos(n)] = cmk<V>(0, 0);
   __syncthreads();
   ring_dft(buf, logm, blue, blue ? btab + R.btab : nullptr, tw, logtw);
   }
