@@ -339,7 +339,7 @@ k_ring_r2c(const T* __restrict__ map, C2<T>* __restrict__ spec, const RingInfo* 
   const V* E = etab + R.etab;
   const V* C = blue ? chirp + chirp_offset(R.nphi) : nullptr;
   // (x[2n], x[2n+1]) as one complex sample z[n]; Bluestein: times the chirp,
-  // zero-padded to 2^logm
+  // zero-padded to 2^(logm-1) (the pruned first pass reads no further)
   const V* x2 = reinterpret_cast<const V*>(map + (long long)b * npix + R.start);
   const int M = blue ? 1 << logm : H;
   if (!blue && logm >= 4) {
@@ -497,7 +497,7 @@ k_ring_c2r(const C2<T>* __restrict__ F, T* __restrict__ map, const RingInfo* __r
   // Z[k] = (D[k] + conj D[H-k]) + i exp(2 pi i k / N) (D[k] - conj D[H-k]), k < H;
   // the ring is then z = IDFT_H(Z) with p[2n] = Re z[n], p[2n+1] = Im z[n].
   // Computed as conj(DFT_H(conj Z)), so conj Z (Bluestein: times the chirp,
-  // zero-padded to 2^logm) is stored.
+  // zero-padded to 2^(logm-1)) is stored.
   if (!blue && logm >= 4 && (H >> 4) <= (int)blockDim.x) {
     // power-of-two rings: conj Z is formed as the first radix-16 pass
     // (Ns = 1) reads its inputs j + r H/16 -- no separate pass over the
