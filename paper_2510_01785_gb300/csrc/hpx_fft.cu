@@ -11,9 +11,13 @@
 // channel); the whole transform stays in shared memory, so each stage reads
 // its input from HBM once and writes its output once.  Belt rings (all of
 // length 4 nside) and cap rings are launched separately, each launch with the
-// shared memory its longest transform needs, the belt launch on a second
-// stream so that the two run side by side; a ring's channels are adjacent
-// CTAs, so its chirp and kernel spectrum are read from HBM once.
+// shared memory its longest transform needs; from Nside 512 the cap rings are
+// three launches by transform length and the belt launch runs on a second
+// stream beside them (see ring_launches); a ring's channels are adjacent
+// CTAs, so its chirp and kernel spectrum are read from HBM once.  Bluestein's
+// convolution input is zero in its upper half and only its lower half of
+// outputs is used, so the first forward pass and the last inverse pass are
+// pruned to those halves.
 //
 // The power-of-two FFT is a Stockham (self-sorting) transform: radix-16
 // passes, then one radix-8, -4 or -2 pass if log2 M is not a multiple of 4,
